@@ -1,0 +1,321 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself:
+hand-derived kernel values, a quadrature, finite differences, closed forms of
+one and two particles, an explicit infinite-lattice sum, brute force, the
+paper's pair-efficiency statistics (Section 1 and Section 2), symmetries, and
+finite differences of the loss for the adjoint.
+"""
+import math
+from fractions import Fraction
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_1804_06231_gb300 import inputs as I
+
+GOLDEN = Path(__file__).parent / "golden"
+G = 1.825742
+C8PI = 8.0 / math.pi
+
+
+def _golden_kernel():
+    rows = []
+    for line in (GOLDEN / "kernel_values.txt").read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        rows.append([float(Fraction(t)) for t in line.split()])
+    return rows
+
+
+# --------------------------------------------------------------------------- kernel
+
+def test_kernel_hand_values(oracle_lib):
+    O = oracle_lib
+    for q, w, dw, d2w in _golden_kernel():
+        assert O.w(q) == pytest.approx(C8PI * w, rel=1e-15, abs=1e-15)
+        assert O.dw(q) == pytest.approx(C8PI * dw, rel=1e-15, abs=1e-15)
+        if q < 1.0:
+            assert O.d2w(q) == pytest.approx(C8PI * d2w, rel=1e-15, abs=1e-15)
+    assert O.w(1.3) == 0.0 and O.dw(1.3) == 0.0 and O.d2w(1.3) == 0.0
+
+
+def test_kernel_normalised(oracle_lib):
+    """int W dV = 1 over the support (quadrature of the oracle's W)."""
+    from scipy.integrate import quad
+    O = oracle_lib
+    for H in (0.01, 0.3, 1.0):
+        val, err = quad(lambda r: 4 * math.pi * r * r * O.W(r, H), 0, H, points=[H / 2],
+                        epsabs=1e-14, epsrel=1e-13)
+        assert val == pytest.approx(1.0, abs=1e-12)
+
+
+def test_kernel_c2_continuity(oracle_lib):
+    O = oracle_lib
+    e = 1e-9
+    for f in (O.w, O.dw, O.d2w):
+        assert f(0.5 - e) == pytest.approx(f(0.5 + e), abs=1e-6)
+    assert O.w(1 - e) == pytest.approx(0, abs=1e-12)
+    assert O.dw(1 - e) == pytest.approx(0, abs=1e-12)
+    assert O.d2w(1 - e) == pytest.approx(0, abs=1e-6)
+
+
+@pytest.mark.parametrize("q", [0.13, 0.37, 0.61, 0.88])
+def test_kernel_derivatives_fd(oracle_lib, q):
+    """dW/dh, d2W/dh2, dW/dr, d2W/dhdr against central differences of W."""
+    O = oracle_lib
+    h = 0.03
+    H = G * h
+    r = q * H
+    eps_h, eps_r = 1e-7 * h, 1e-7 * H
+    fd_h = (O.W(r, G * (h + eps_h)) - O.W(r, G * (h - eps_h))) / (2 * eps_h)
+    assert O.W_h(r, h) == pytest.approx(fd_h, rel=1e-6)
+    fd_hh = (O.W_h(r, h + eps_h) - O.W_h(r, h - eps_h)) / (2 * eps_h)
+    assert O.W_hh(r, h) == pytest.approx(fd_hh, rel=1e-6)
+    fd_r = (O.W(r + eps_r, H) - O.W(r - eps_r, H)) / (2 * eps_r)
+    assert O.W_r(r, H) == pytest.approx(fd_r, rel=1e-6)
+    fd_hr = (O.W_h(r + eps_r, h) - O.W_h(r - eps_r, h)) / (2 * eps_r)
+    assert O.W_hr(r, h) == pytest.approx(fd_hr, rel=1e-6)
+
+
+# --------------------------------------------------------------------------- closed forms
+
+ROUTES = ("brute", "cells", "pv")
+
+
+def _run(O, route, pos, h, m, nc, L=1.0):
+    if route == "brute":
+        return O.density_brute(pos, h, m, L)
+    if route == "cells":
+        return O.density_cells(pos, h, m, L, nc)
+    return O.density_pv(pos, h, m, L, nc)
+
+
+@pytest.mark.parametrize("route", ROUTES)
+def test_single_particle(oracle_lib, route):
+    """One particle: rho = m W(0,H) = m (8/pi)/H^3, drho/dh = -3 rho/h, n = 0."""
+    O = oracle_lib
+    pos = np.array([[0.31, 0.52, 0.93]])
+    h = np.array([0.1])
+    m = np.array([2.5])
+    r = _run(O, route, pos, h, m, nc=4)
+    H = G * 0.1
+    assert r.rho[0] == pytest.approx(2.5 * C8PI / H ** 3, rel=1e-14)
+    assert r.drho_dh[0] == pytest.approx(-3 * r.rho[0] / 0.1, rel=1e-14)
+    assert r.n_ngb[0] == 0
+
+
+@pytest.mark.parametrize("route", ROUTES)
+@pytest.mark.parametrize("qn,w_hand", [(Fraction(1, 4), Fraction(23, 32)),
+                                       (Fraction(3, 4), Fraction(1, 32))])
+def test_two_particles(oracle_lib, route, qn, w_hand):
+    """Two particles at r = q H_i across a periodic face, hand values of w."""
+    O = oracle_lib
+    h0 = 0.08
+    H = G * h0
+    r = float(qn) * H
+    pos = np.array([[0.99, 0.5, 0.5], [0.99 + r - 1.0, 0.5, 0.5]])   # wraps through x = 1
+    h = np.array([h0, h0 * 0.5])
+    m = np.array([1.0, 3.0])
+    res = _run(O, route, pos, h, m, nc=5)
+    expect_rho0 = (1.0 * C8PI + 3.0 * C8PI * float(w_hand)) / H ** 3
+    assert res.rho[0] == pytest.approx(expect_rho0, rel=1e-12)
+    assert res.n_ngb[0] == 1
+    # particle 1 has half the support: q = 2 qn >= 1/2 -> only the self term when q >= 1
+    q1 = 2 * float(qn)
+    assert res.n_ngb[1] == (1 if q1 < 1 else 0)
+
+
+def test_duplicate_positions(oracle_lib):
+    """Coincident particles j != i are neighbours (r = 0 < H) and add W(0)."""
+    O = oracle_lib
+    pos = np.array([[0.4, 0.4, 0.4]] * 3)
+    h = np.full(3, 0.05)
+    m = np.ones(3)
+    for route in ROUTES:
+        r = _run(O, route, pos, h, m, nc=6)
+        assert list(r.n_ngb) == [2, 2, 2]
+        assert r.rho[0] == pytest.approx(3 * C8PI / (G * 0.05) ** 3, rel=1e-14)
+
+
+# --------------------------------------------------------------------------- lattice
+
+def _lattice_sum(a, h, m):
+    """Explicit sum over the infinite simple-cubic lattice Z^3 a (no cells, no wrap)."""
+    H = G * h
+    k = int(math.ceil(H / a)) + 1
+    rng = np.arange(-k, k + 1)
+    n = np.stack(np.meshgrid(rng, rng, rng, indexing="ij"), -1).reshape(-1, 3)
+    r = np.sqrt((n.astype(float) ** 2).sum(1)) * a
+    inside = r < H
+    rho = m * sum(oracle_W(x, H) for x in r[inside])
+    D = m * sum(oracle_W_h(x, h) for x in r[inside])
+    nn = int(inside.sum()) - 1
+    return rho, D, nn
+
+
+def oracle_W(r, H):
+    import oracle
+    return oracle.W(float(r), H)
+
+
+def oracle_W_h(r, h):
+    import oracle
+    return oracle.W_h(float(r), h)
+
+
+@pytest.mark.parametrize("route", ["cells", "pv"])
+def test_lattice(oracle_lib, route):
+    O = oracle_lib
+    box = I.lattice(18, nc=6)
+    a = 1.0 / 18
+    h = float(box.h[0])            # float32-rounded 1.2348 a
+    res = _run(O, route, box.pos, box.h, box.m, box.nc)
+    rho, D, nn = _lattice_sum(a, h, float(box.m[0]))
+    # 56 lattice vectors with |n|^2 in {1,2,3,4,5}: 6 + 12 + 8 + 6 + 24
+    assert nn == 56
+    assert np.all(res.n_ngb == 56)
+    np.testing.assert_allclose(res.rho, rho, rtol=1e-12)
+    np.testing.assert_allclose(res.drho_dh, D, rtol=1e-11)
+    # N m / V = 1: the lattice reproduces it to kernel-discretisation accuracy
+    assert abs(res.rho.mean() - 1.0) < 5e-3
+
+
+# --------------------------------------------------------------------------- routes agree
+
+@pytest.mark.parametrize("kind,n,nc", [("uniform", 3000, 3), ("uniform", 3000, 5),
+                                       ("uniform", 6000, None), ("clustered", 5000, None),
+                                       ("test27cells", 0, 3)])
+def test_routes_agree(oracle_lib, kind, n, nc):
+    O = oracle_lib
+    if kind == "uniform":
+        b = I.uniform(n, 7, nc=nc)
+    elif kind == "clustered":
+        b = I.clustered(n, 8, nc=nc)
+    else:
+        b = I.test27cells(per_cell=64)
+    ref = O.density_brute(b.pos, b.h, b.m)
+    for route in ("cells", "pv"):
+        r = _run(O, route, b.pos, b.h, b.m, b.nc)
+        np.testing.assert_allclose(r.rho, ref.rho, rtol=1e-13)
+        np.testing.assert_allclose(r.drho_dh, ref.drho_dh, rtol=0, atol=1e-13 * ref.S.max())
+        np.testing.assert_array_equal(r.n_ngb, ref.n_ngb)
+        np.testing.assert_array_equal(r.band, ref.band)
+
+
+def test_empty_and_tiny(oracle_lib):
+    O = oracle_lib
+    e = np.zeros((0, 3))
+    r = O.density_pv(e, np.zeros(0), np.zeros(0), 1.0, 4)
+    assert r.rho.size == 0 and r.counters.sum() == 0
+    # most cells empty
+    b = I.uniform(20, 3, nc=3)
+    b.h = (b.h * 0.3).astype(np.float32)
+    ref = O.density_brute(b.pos, b.h, b.m)
+    r = O.density_pv(b.pos, b.h, b.m, 1.0, 3)
+    np.testing.assert_allclose(r.rho, ref.rho, rtol=1e-13)
+
+
+def test_rejects_small_cells(oracle_lib):
+    O = oracle_lib
+    b = I.uniform(500, 1, nc=3)
+    with pytest.raises(ValueError):
+        O.density_pv(b.pos, b.h, b.m, 1.0, 2)
+    with pytest.raises(ValueError):   # H_max above the edge
+        O.density_pv(b.pos, b.h * 4, b.m, 1.0, 3)
+
+
+# --------------------------------------------------------------------------- symmetries
+
+def test_translation_and_axis_symmetry(oracle_lib):
+    O = oracle_lib
+    b = I.uniform(8000, 12, nc=7)
+    ref = O.density_pv(b.pos, b.h, b.m, 1.0, b.nc)
+    shifted = np.mod(b.pos + np.array([0.3141, 0.777, 0.05]), 1.0)
+    r1 = O.density_pv(shifted, b.h, b.m, 1.0, b.nc)
+    rot = np.ascontiguousarray(b.pos[:, [1, 2, 0]])
+    r2 = O.density_pv(rot, b.h, b.m, 1.0, b.nc)
+    for r in (r1, r2):
+        np.testing.assert_allclose(r.rho, ref.rho, rtol=1e-12)
+        ok = ref.band == 0
+        np.testing.assert_array_equal(r.n_ngb[ok], ref.n_ngb[ok])
+
+
+def test_grid_invariance(oracle_lib):
+    O = oracle_lib
+    b = I.uniform(8000, 13, nc=None)
+    ref = O.density_pv(b.pos, b.h, b.m, 1.0, 3)
+    for nc in (4, b.nc):
+        r = O.density_pv(b.pos, b.h, b.m, 1.0, nc)
+        np.testing.assert_allclose(r.rho, ref.rho, rtol=1e-13)
+        np.testing.assert_array_equal(r.n_ngb, ref.n_ngb)
+
+
+# --------------------------------------------------------------------------- statistics
+
+def test_mean_neighbour_count(oracle_lib):
+    """E[n] = (4 pi/3) (gamma eta)^3 E[U^3], U ~ U(0.9, 1.1): 48.475 for the uniform rule."""
+    O = oracle_lib
+    b = I.cfg0()
+    r = O.density_pv(b.pos, b.h, b.m, 1.0, b.nc)
+    eu3 = (1.1 ** 4 - 0.9 ** 4) / (4 * 0.2)
+    expect = 4 * math.pi / 3 * (G * I.ETA) ** 3 * eu3
+    assert expect == pytest.approx(48.475, abs=1e-3)
+    assert r.n_ngb.mean() == pytest.approx(expect, abs=0.3)
+
+
+def test_pair_efficiency_matches_paper(oracle_lib):
+    """Cell edge = support, uniform particles.
+
+    Section 2: about 68 % of the pairs inspected by the sorted sweep are in
+    range (face-sharing cells); Section 1: a plain cell list finds at most 16 %
+    of the inspected pairs in range (4 pi/81 = 15.5 % over the 27-cell stencil).
+    """
+    O = oracle_lib
+    nc = 8
+    rng = np.random.default_rng(11)
+    n = 40000
+    pos = rng.random((n, 3))
+    h = np.full(n, (1.0 / nc) * (1 - 3e-6) / G)
+    m = np.full(n, 1.0 / n)
+    c = O.density_pv(pos, h, m, 1.0, nc).counters
+    face = c[1, 1] / c[1, 0]
+    assert face == pytest.approx(0.68, abs=0.02)
+    stencil = c[:, 1].sum() / (27 * (n / nc ** 3) * n)
+    assert stencil == pytest.approx(4 * math.pi / 81, abs=0.005)
+    assert stencil <= 0.16
+
+
+# --------------------------------------------------------------------------- adjoint
+
+def test_adjoint_brute_equals_cells(oracle_lib):
+    O = oracle_lib
+    b = I.uniform(3000, 21, nc=None)
+    w, v = I.loss_weights(b.n, 21)
+    d = O.density_cells(b.pos, b.h, b.m, 1.0, b.nc)
+    g, k = O.loss_upstream(d.rho, w, v)
+    gp0, gh0 = O.backward_brute(b.pos, b.h, b.m, g, k)
+    gp1, gh1 = O.backward_cells(b.pos, b.h, b.m, g, k, 1.0, b.nc)
+    np.testing.assert_allclose(gp1, gp0, rtol=0, atol=1e-12 * np.abs(gp0).max())
+    np.testing.assert_allclose(gh1, gh0, rtol=0, atol=1e-12 * np.abs(gh0).max())
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clustered"])
+def test_adjoint_matches_finite_differences(oracle_lib, kind):
+    """dL/dx and dL/dh of L = sum w (rho-1)^2 + sum v drho/dh, central FD step 1e-6."""
+    O = oracle_lib
+    b = I.uniform(4096, 31, nc=None) if kind == "uniform" else I.clustered(4096, 32)
+    w, v = I.loss_weights(b.n, 31)
+    d = O.density_cells(b.pos, b.h, b.m, 1.0, b.nc)
+    g, k = O.loss_upstream(d.rho, w, v)
+    gp, gh = O.backward_cells(b.pos, b.h, b.m, g, k, 1.0, b.nc)
+    rng = np.random.default_rng(5)
+    scale_x = np.abs(gp).max()
+    scale_h = np.abs(gh).max()
+    for p in rng.choice(b.n, 12, replace=False):
+        for comp in range(3):
+            fd = O.fd_loss_grad(b.pos, b.h, b.m, w, v, p, comp, 1e-6)
+            assert fd == pytest.approx(gp[p, comp], abs=1e-6 * scale_x, rel=1e-5)
+        fd = O.fd_loss_grad(b.pos, b.h, b.m, w, v, p, 3, 1e-6)
+        assert fd == pytest.approx(gh[p], abs=1e-6 * scale_h, rel=1e-5)
