@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the pseudo-Verlet SPH density loop on GB300.
+
+One step = one pass of the whole hot path over one synthetic particle set:
+pv_sort_cells (cell grid + 13 sorted projections), pv_density (rho, drho/dh,
+n) and pv_density_backward (dL/dx, dL/dh).  The workload is N = 1,048,576
+uniform random particles in a periodic unit cube, h_i = 1.2348 N^(-1/3)
+U(0.9, 1.1), 15^3 cells (about 311 per cell).  The metric is density-loop
+pair interactions per second: sum_i n_i of the step divided by its time.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (the only other place this script runs it).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "density-loop pair interactions/s"
+UNIT = "interactions/s"
+WORKLOAD = "uniform N=1048576, 15^3 cells, h=1.2348 N^-1/3 U(0.9,1.1), sort+density+backward"
+# algorithmic FP32 work: flops per window candidate and per
+# in-range pair of the forward sweep, per candidate and per pair of the adjoint
+FWD_FLOP_CAND, FWD_FLOP_PAIR = 9, 23
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="pv", choices=["pv", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.uuid = uuid
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workloads
+
+def workload(seed: int):
+    from paper_1804_06231_gb300 import inputs as I
+    return I.cfg1(seed)
+
+
+def cpu_sample(seed: int):
+    """Bounded sample of the workload for the CPU oracle: a periodic sub-box of
+    7^3 cells of the same edge (1/15), number density and h rule -- 106,572
+    particles (1/9.8 of the volume)."""
+    from paper_1804_06231_gb300 import inputs as I
+    L = 7.0 / 15.0
+    n = int(round((1 << 20) * L ** 3))
+    b = I.uniform(n, seed + 777, nc=7, L=L)
+    b.name = f"uniform sub-box N={n}, L=7/15, 7^3 cells"
+    return b
+
+
+def time_oracle(box, steps: int, warmup: int, threads: int):
+    """Times oracle density (pseudo-Verlet sweep) + oracle adjoint per step."""
+    import oracle
+    from paper_1804_06231_gb300 import inputs as I
+    w, v = I.loss_weights(box.n, 0)
+    times, inter = [], 0
+    for s in range(warmup + steps):
+        t0 = time.perf_counter()
+        d = oracle.density_pv(box.pos, box.h, box.m, box.L, box.nc, threads=threads)
+        g, k = oracle.loss_upstream(d.rho, w, v)
+        oracle.backward_cells(box.pos, box.h, box.m, g, k, box.L, box.nc, threads=threads)
+        t1 = time.perf_counter()
+        if s >= warmup:
+            times.append(t1 - t0)
+        inter = int(d.n_ngb.sum())
+    return inter, times
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cores = host_cores()
+    box = cpu_sample(0)
+    steps, warmup = max(1, args.steps), max(0, args.warmup)
+    # bound the total: each step is ~1-3 s on 16 cores; cap the count
+    steps = min(steps, 20)
+    warmup = min(warmup, 2)
+    inter, times = time_oracle(box, steps, warmup, cores)
+    t = statistics.mean(times)
+    value = inter / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": len(times), "warmup": warmup, "ms_per_step": 1e3 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": box.name},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": box.name + "; FP64 pseudo-Verlet density + cell-list adjoint"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1804_06231_gb300 import build as B
+    B.build_library()
+    from paper_1804_06231_gb300.pv import Grid
+
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    stream = torch.cuda.current_stream()
+
+    box = workload(1 + rank)  # independent box per rank (weak scaling)
+    n = box.n
+    pos = torch.from_numpy(box.pos).to(dev)
+    h = torch.from_numpy(box.h).to(dev)
+    rng = np.random.default_rng(100 + rank)
+    g_rho = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
+    g_d = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
+    rho = torch.empty(n, dtype=torch.float32, device=dev)
+    drho = torch.empty_like(rho)
+    nngb = torch.empty(n, dtype=torch.int32, device=dev)
+    gpos = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    gh = torch.empty_like(rho)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+    grid = Grid((n, 1.0, box.nc))
+    m_uniform = float(box.m[0])
+
+    def step():
+        grid.sort(pos, h, None, m_uniform)
+        grid.density(rho, drho, nngb)
+        grid.backward(g_rho, g_d, gpos, gh)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    grid.sync()
+    st0 = grid.stats()
+    interactions = st0.interactions
+    candidates = grid.count_candidates()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(props.uuid) if not str(props.uuid).startswith("GPU") else str(props.uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid) if rank == 0 else None
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.4)
+    launches0 = grid.stats().kernel_launches
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()  # evict the previous step's data from L2 (outside the events)
+        e = ev[k]
+        e[0].record(stream)
+        grid.sort(pos, h, None, m_uniform)
+        e[1].record(stream)
+        grid.density(rho, drho, nngb)
+        e[2].record(stream)
+        grid.backward(g_rho, g_d, gpos, gh)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    launches = grid.stats().kernel_launches - launches0
+    t_sort = sum(e[0].elapsed_time(e[1]) for e in ev) / K
+    t_dens = sum(e[1].elapsed_time(e[2]) for e in ev) / K
+    t_bwd = sum(e[2].elapsed_time(e[3]) for e in ev) / K
+    t_step = sum(e[0].elapsed_time(e[3]) for e in ev) / K  # ms
+    st = grid.stats()
+    assert st.device_flags == 0
+
+    t_max = t_step
+    tot_inter = interactions
+    if ws > 1:
+        t = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        c = torch.tensor([interactions], device=dev, dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        tot_inter = int(c.item())
+    value = tot_inter / (t_max * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.from_numpy(box.pos).pin_memory()
+        hh = torch.from_numpy(box.h).pin_memory()
+        hg = g_rho.cpu().pin_memory()
+        hd = g_d.cpu().pin_memory()
+        o_rho = torch.empty(n, dtype=torch.float32).pin_memory()
+        o_d = torch.empty(n, dtype=torch.float32).pin_memory()
+        o_n = torch.empty(n, dtype=torch.int32).pin_memory()
+        o_gp = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+        o_gh = torch.empty(n, dtype=torch.float32).pin_memory()
+        bi = sum(t.numel() * t.element_size() for t in (hp, hh, hg, hd))
+        bo = sum(t.numel() * t.element_size() for t in (o_rho, o_d, o_n, o_gp, o_gh))
+        times = []
+        for k in range(K + 2):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pos.copy_(hp, non_blocking=True)
+            h.copy_(hh, non_blocking=True)
+            g_rho.copy_(hg, non_blocking=True)
+            g_d.copy_(hd, non_blocking=True)
+            step()
+            o_rho.copy_(rho, non_blocking=True)
+            o_d.copy_(drho, non_blocking=True)
+            o_n.copy_(nngb, non_blocking=True)
+            o_gp.copy_(gpos, non_blocking=True)
+            o_gh.copy_(gh, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            if k >= 2:
+                times.append(a.elapsed_time(b))
+        t_e2e = statistics.mean(times)
+        if ws > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": tot_inter / (t_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "ms_per_step": t_e2e}
+
+    # ---- roofline of the forward density sweep (FP32 ALU bound)
+    peaks = measured_peaks()
+    sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    pairs = interactions + n  # in-range pairs evaluated, including j = i
+    fwd_flops = FWD_FLOP_CAND * candidates + FWD_FLOP_PAIR * pairs
+    achieved = fwd_flops / (t_dens * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "pv_density (plan + sweep + finalize)",
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                               f"{sm_max:.0f} MHz"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        cores = host_cores()
+        cbox = cpu_sample(0)
+        c_inter, c_times = time_oracle(cbox, 2, 0, cores)
+        cpu = {"value": c_inter / statistics.mean(c_times), "unit": UNIT, "cores": cores,
+               "kind": "oracle",
+               "sample": cbox.name + "; FP64 pseudo-Verlet density + cell-list adjoint, "
+                                     f"{len(c_times)} runs"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_particles_per_gpu": n, "cells": box.nc ** 3,
+                       "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "breakdown_ms": {"sort": t_sort, "density": t_dens, "backward": t_bwd},
+            "density_interactions_per_s": interactions / (t_dens * 1e-3),
+            "fwd_bwd_over_fwd": (t_dens + t_bwd) / t_dens,
+            "candidates": candidates, "interactions": interactions,
+            "candidates_per_interaction": candidates / max(interactions, 1),
+            "guard_pairs": st.guard_pairs, "wall_s_timed_loop": wall,
+        }
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

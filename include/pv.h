@@ -1,0 +1,162 @@
+/*
+ * pv.h -- C ABI of the GB300 pseudo-Verlet SPH density loop.
+ *
+ * The operation (Willis et al., arXiv:1804.06231, Section 1 and Section 2):
+ * particles in a periodic cube are binned into cells whose edge is at least
+ * the largest interaction radius; for every pair of neighbouring cells the
+ * particles of both cells are sorted by their projection on the axis joining
+ * the cell centres (13 distinct axes by symmetry, Section 2), and each
+ * particle i of cell a only computes distances to the particles j of cell b
+ * whose projected distance is below its own radius (Section 2, Section 3.1).
+ * The interaction gathered over those pairs is the SPH density of the 3D
+ * cubic spline with support H = gamma h:
+ *
+ *   rho_i     = sum_j m_j W(r_ij, H_i)              (j = i included)
+ *   drho_dh_i = sum_j m_j dW/dh(r_ij, h_i)
+ *   n_i       = #{ j != i : r_ij < H_i }
+ *   W(r, H)   = 8/(pi H^3) * { 1 - 6q^2 + 6q^3 (q < 1/2) | 2 (1-q)^3 (q < 1) | 0 },  q = r/H
+ *
+ * r_ij is the minimum-image distance in the periodic cube of the particle's
+ * box.  All device pointers below are CUDA device (or managed) memory; "host"
+ * pointers are ordinary host memory.  Every call is asynchronous on the given
+ * stream (a cudaStream_t passed as void*, NULL = the legacy default stream)
+ * unless stated otherwise; argument errors are returned synchronously and
+ * nothing is launched.  Errors found by the kernels (a support larger than
+ * the cell edge, a non-finite position, a cell above PV_MAX_CELL_COUNT) are
+ * latched in a device status word and returned by the next call that
+ * synchronises (pv_grid_stats, pv_grid_sync) as PV_ERR_DEVICE.
+ *
+ * Thread safety: a pv_grid may be used by one host thread at a time.
+ */
+#ifndef PV_H
+#define PV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PV_OK = 0,
+  PV_ERR_INVALID_ARGUMENT = 1, /* NULL pointer, negative size, bad box layout */
+  PV_ERR_CELL_TOO_SMALL = 2,   /* nc < 3 (returned by pv_grid_create) */
+  PV_ERR_OUT_OF_MEMORY = 3,    /* device or host allocation failed */
+  PV_ERR_CUDA = 4,             /* a CUDA runtime call failed (see pv_last_cuda_error) */
+  PV_ERR_NOT_SORTED = 5,       /* pv_density / pv_density_backward before pv_sort_cells */
+  PV_ERR_DEVICE = 6,           /* a kernel latched an error; see pv_stats.device_flags */
+  PV_ERR_TOO_LARGE = 7         /* more than 2^31 - 1 particles or cells */
+} pv_status;
+
+/* Bits of pv_stats.device_flags (set by the kernels of pv_sort_cells). */
+#define PV_FLAG_SUPPORT_EXCEEDS_CELL 1u /* gamma h_i > L/nc for some particle */
+#define PV_FLAG_BAD_POSITION 2u         /* non-finite position coordinate */
+#define PV_FLAG_BAD_SMOOTHING 4u        /* h_i not finite or not > 0, or m_i not finite */
+#define PV_FLAG_CELL_OVERFLOW 8u        /* a cell holds more than PV_MAX_CELL_COUNT particles */
+
+/* Largest number of particles one cell may hold (cell-local indices are 16-bit). */
+#define PV_MAX_CELL_COUNT 65535
+
+/* One periodic box.  Boxes are independent: particles of different boxes
+   never interact.  The particles of box b are the contiguous index range
+   [first, first + n) of the arrays passed to pv_sort_cells. */
+typedef struct {
+  int64_t first; /* index of the box's first particle */
+  int64_t n;     /* particles in the box (may be 0) */
+  double L;      /* edge of the periodic cube [0, L)^3, > 0; positions are wrapped into it */
+  int32_t nc;    /* cells per dimension, >= 3; the cell edge L/nc must be >= gamma * max h */
+} pv_box_desc;
+
+typedef struct {
+  int32_t n_boxes;          /* >= 1 */
+  const pv_box_desc* boxes; /* host array [n_boxes]; copied, the caller keeps ownership */
+  double gamma;             /* H = gamma h; <= 0 selects 1.825742 */
+  uint32_t flags;           /* must be 0 */
+} pv_grid_desc;
+
+typedef struct pv_grid pv_grid; /* opaque; owns all scratch device memory */
+
+typedef struct {
+  int64_t n_particles;      /* sum of the boxes' n */
+  int64_t n_cells;          /* sum of nc^3 */
+  int32_t max_cell_count;   /* largest cell occupancy seen by the last pv_sort_cells */
+  uint32_t device_flags;    /* PV_FLAG_* bits latched since the last pv_sort_cells */
+  int64_t interactions;     /* sum_i n_i of the last pv_density */
+  int64_t guard_pairs;      /* pairs re-decided in FP64 near r = H_i by the last pv_density */
+  int64_t candidates;       /* distance tests inside the sorted windows (pv_count_candidates) */
+  int64_t device_bytes;     /* scratch device memory owned by the grid */
+  int64_t kernel_launches;  /* kernels this grid has launched since it was created */
+} pv_stats;
+
+/* Allocates a grid for the given boxes (cudaMalloc on the current device).
+   Host-synchronous.  On success *out owns the grid; free it with
+   pv_grid_destroy.  Returns PV_ERR_CELL_TOO_SMALL if a box has nc < 3. */
+pv_status pv_grid_create(const pv_grid_desc* desc, pv_grid** out);
+
+/* Frees the grid and its device memory (synchronises the device first).
+   NULL is accepted. */
+pv_status pv_grid_destroy(pv_grid* g);
+
+/* Cell grid and sorted projections (Section 2; the dist/index arrays of the
+   13 axes), built from the caller's particles:
+     pos  device double [N][3]  positions (wrapped into [0, L) of their box)
+     h    device float  [N]     smoothing lengths, > 0; support H = gamma h
+     m    device float  [N]     masses, or NULL to use m_uniform for every particle
+   N = sum of the boxes' n.  The grid copies what it needs: the caller may
+   reuse pos, h and m once the work queued on `stream` has run.  Kernel-side
+   input errors are latched (see PV_FLAG_*). */
+pv_status pv_sort_cells(pv_grid* g, const double* pos, const float* h, const float* m,
+                        float m_uniform, void* stream);
+
+/* Density gather over the self cell and the 26 neighbour cells of every cell
+   (Section 2 and Section 3: sorted sweep with early exit, trimmed to the
+   particles that can reach the other cell), results in the caller's particle
+   order:
+     rho      device float   [N]
+     drho_dh  device float   [N]   (NULL: not written)
+     n_ngb    device int32_t [N]   (NULL: not written)
+   Requires a prior pv_sort_cells on the same grid (else PV_ERR_NOT_SORTED).
+   Deterministic: the result does not depend on scheduling. */
+pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, void* stream);
+
+/* Adjoint of pv_density (not in the paper).  Given the upstream gradients
+     g_rho      device float [N]   dL/drho_i
+     g_drho_dh  device float [N]   dL/d(drho_dh)_i   (NULL: zero)
+   writes
+     g_pos      device float [N][3]  dL/dx_i
+     g_h        device float [N]     dL/dh_i         (NULL: not written)
+   with
+     dL/dh_i = g_i drho_dh_i + k_i sum_j m_j d2W/dh2(r_ij, h_i)
+     dL/dx_i = sum_{j != i} (x_i - x_j)/r_ij [ m_j (g_i dW/dr(r,H_i) + k_i d2W/dhdr(r,h_i)) [r < H_i]
+                                             + m_i (g_j dW/dr(r,H_j) + k_j d2W/dhdr(r,h_j)) [r < H_j] ]
+   (g = g_rho, k = g_drho_dh), computed by re-sweeping the same sorted cell
+   pairs as a gather (the transposed term is a second gather, no atomics on
+   the outputs).  Requires a prior pv_sort_cells.  Masses are constants. */
+pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drho_dh,
+                              float* g_pos, float* g_h, void* stream);
+
+/* Counts the distance tests of the sorted windows of the method (the
+   "candidates": self-cell two-sided windows plus the pair windows of
+   Section 2) for the particles sorted by the last pv_sort_cells, into
+   pv_stats.candidates.  A diagnostic pass; not needed for pv_density. */
+pv_status pv_count_candidates(pv_grid* g, void* stream);
+
+/* Waits for the grid's work on `stream` and returns PV_ERR_DEVICE if a kernel
+   latched an error flag, else PV_OK.  Host-synchronous. */
+pv_status pv_grid_sync(pv_grid* g, void* stream);
+
+/* Fills *out (host pointer).  Synchronises the device.  Returns
+   PV_ERR_DEVICE when device_flags is non-zero (out is still filled). */
+pv_status pv_grid_stats(pv_grid* g, pv_stats* out);
+
+/* Static description of a status code (never NULL). */
+const char* pv_status_str(pv_status s);
+
+/* Text of the last CUDA error seen by this library on the calling thread. */
+const char* pv_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PV_H */

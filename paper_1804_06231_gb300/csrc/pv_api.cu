@@ -1,0 +1,300 @@
+// pv_api.cu -- host side of the C ABI declared in include/pv.h: argument
+// checks, scratch allocation, and the launch sequence of each call.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pv_internal.cuh"
+
+using pv::GridDev;
+
+struct pv_grid {
+  GridDev d{};
+  std::vector<pv_box_desc> boxes;
+  std::vector<void*> allocs;
+  int64_t n = 0, ncell = 0;
+  int device = 0, num_sms = 0;
+  bool sorted = false;
+  size_t bytes = 0;
+  int64_t launches = 0;  // kernels launched by this grid so far
+};
+
+namespace {
+
+thread_local char g_cuda_err[256] = "no error";
+
+pv_status cuda_fail(cudaError_t e, const char* what) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? PV_ERR_OUT_OF_MEMORY : PV_ERR_CUDA;
+}
+
+#define PV_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <typename T>
+pv_status dev_alloc(pv_grid* g, T** p, size_t count) {
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = 16;
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  g->allocs.push_back(ptr);
+  g->bytes += bytes;
+  *p = static_cast<T*>(ptr);
+  return PV_OK;
+}
+
+#define PV_TRY(x)                   \
+  do {                              \
+    pv_status s_ = (x);             \
+    if (s_ != PV_OK) return s_;     \
+  } while (0)
+
+void free_all(pv_grid* g) {
+  for (void* p : g->allocs) cudaFree(p);
+  g->allocs.clear();
+}
+
+pv_status build(pv_grid* g, const pv_grid_desc* desc) {
+  const double gamma = desc->gamma > 0 ? desc->gamma : 1.825742;
+  std::vector<pv::BoxDev> hb(desc->n_boxes);
+  std::vector<int64_t> hfirst(desc->n_boxes);
+  int64_t n = 0, ncell = 0;
+  for (int b = 0; b < desc->n_boxes; b++) {
+    const pv_box_desc& bd = desc->boxes[b];
+    if (bd.n < 0 || !(bd.L > 0) || !std::isfinite(bd.L)) return PV_ERR_INVALID_ARGUMENT;
+    if (bd.first != n) return PV_ERR_INVALID_ARGUMENT;  // contiguous, in order
+    if (bd.nc < 3) return PV_ERR_CELL_TOO_SMALL;
+    if (bd.nc > 1290) return PV_ERR_TOO_LARGE;  // nc^3 fits in int32
+    pv::BoxDev& B = hb[b];
+    B.L = bd.L;
+    B.inv_L = 1.0 / bd.L;
+    B.edge = bd.L / bd.nc;
+    B.inv_edge = bd.nc / bd.L;
+    B.edge_f = (float)B.edge;
+    // projections of FP32 offsets carry < 2^-21 edge of rounding each; the
+    // window pad covers two of them plus the FP32 cell shift
+    B.pad = (float)(std::ldexp(B.edge, -18));
+    B.guard = 0.0f;
+    B.nc = bd.nc;
+    B.cell_base = (int32_t)ncell;
+    B.first = bd.first;
+    B.n = bd.n;
+    hfirst[b] = bd.first;
+    n += bd.n;
+    ncell += (int64_t)bd.nc * bd.nc * bd.nc;
+    // thread indices over (cell, slot) pairs and task counts stay in int32
+    if (n > 0x7fffffffLL / 32 * 32 - 64 || ncell * pv::kNSlot > 0x7fffffffLL)
+      return PV_ERR_TOO_LARGE;
+  }
+  g->n = n;
+  g->ncell = ncell;
+  g->boxes.assign(desc->boxes, desc->boxes + desc->n_boxes);
+  PV_CUDA(cudaGetDevice(&g->device));
+  PV_CUDA(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+
+  GridDev& d = g->d;
+  d.n_boxes = desc->n_boxes;
+  d.n = (int32_t)n;
+  d.ncell = (int32_t)ncell;
+  d.gamma = (float)gamma;
+  d.gamma_d = gamma;
+  const size_t N = (size_t)n, C = (size_t)ncell;
+  pv::BoxDev* boxes_d;
+  int64_t* first_d;
+  PV_TRY(dev_alloc(g, &boxes_d, hb.size()));
+  PV_TRY(dev_alloc(g, &first_d, hfirst.size()));
+  PV_CUDA(cudaMemcpy(boxes_d, hb.data(), hb.size() * sizeof(pv::BoxDev), cudaMemcpyHostToDevice));
+  PV_CUDA(cudaMemcpy(first_d, hfirst.data(), hfirst.size() * sizeof(int64_t),
+                     cudaMemcpyHostToDevice));
+  d.boxes = boxes_d;
+  d.box_first = first_d;
+  PV_TRY(dev_alloc(g, &d.cell_count, C));
+  PV_TRY(dev_alloc(g, &d.cell_start, C + 1));
+  PV_TRY(dev_alloc(g, &d.cell_box, C));
+  PV_TRY(dev_alloc(g, &d.cell_Hmax, C));
+  PV_TRY(dev_alloc(g, &d.big_cells, C));
+  PV_TRY(dev_alloc(g, &d.pcell, N));
+  PV_TRY(dev_alloc(g, &d.prank, N));
+  PV_TRY(dev_alloc(g, &d.xm, N));
+  PV_TRY(dev_alloc(g, &d.hs, N));
+  PV_TRY(dev_alloc(g, &d.orig, N));
+  PV_TRY(dev_alloc(g, &d.pos64, 3 * N));
+  PV_TRY(dev_alloc(g, &d.perm, pv::kNDir * N));
+  PV_TRY(dev_alloc(g, &d.dist, pv::kNDir * N));
+  PV_TRY(dev_alloc(g, &d.skey, N));
+  PV_TRY(dev_alloc(g, &d.sbuf, N));
+  PV_TRY(dev_alloc(g, &d.sbucket, 2 * N));
+  PV_TRY(dev_alloc(g, &d.acc, 3 * N));
+  PV_TRY(dev_alloc(g, &d.gacc, 5 * N));
+  PV_TRY(dev_alloc(g, &d.gk, N));
+  PV_TRY(dev_alloc(g, &d.ghh, N));
+  const int64_t mt = pv::max_tasks_for(n, ncell);
+  if (mt > 0x7fffffffLL) return PV_ERR_TOO_LARGE;
+  d.max_tasks = (int32_t)mt;
+  PV_TRY(dev_alloc(g, &d.tasks, (size_t)d.max_tasks));
+  // scalars in one allocation
+  int32_t* sc;
+  PV_TRY(dev_alloc(g, &sc, 16));
+  d.flags = reinterpret_cast<uint32_t*>(sc + 0);
+  d.m_max = reinterpret_cast<float*>(sc + 1);
+  d.max_count = sc + 2;
+  d.n_big = sc + 3;
+  d.ntask = sc + 4;
+  d.task_next = sc + 5;
+  unsigned long long* cnt;
+  PV_TRY(dev_alloc(g, &cnt, 4));
+  d.counters = cnt;
+  PV_CUDA(cudaMemset(sc, 0, 16 * sizeof(int32_t)));
+  PV_CUDA(cudaMemset(cnt, 0, 4 * sizeof(unsigned long long)));
+  if (N) {
+    PV_CUDA(cudaMemset(d.acc, 0, 3 * N * sizeof(long long)));
+    PV_CUDA(cudaMemset(d.gacc, 0, 5 * N * sizeof(long long)));
+  }
+  // cell -> box map
+  std::vector<int32_t> cbox(C);
+  for (int b = 0; b < desc->n_boxes; b++) {
+    const int64_t c0 = hb[b].cell_base, c1 = c0 + (int64_t)hb[b].nc * hb[b].nc * hb[b].nc;
+    for (int64_t c = c0; c < c1; c++) cbox[c] = b;
+  }
+  if (C) PV_CUDA(cudaMemcpy(d.cell_box, cbox.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return PV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pv_status_str(pv_status s) {
+  switch (s) {
+    case PV_OK: return "ok";
+    case PV_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case PV_ERR_CELL_TOO_SMALL: return "cell grid too coarse (nc < 3)";
+    case PV_ERR_OUT_OF_MEMORY: return "out of memory";
+    case PV_ERR_CUDA: return "CUDA error";
+    case PV_ERR_NOT_SORTED: return "pv_sort_cells has not been called on this grid";
+    case PV_ERR_DEVICE: return "a kernel latched an input error (see device_flags)";
+    case PV_ERR_TOO_LARGE: return "too many particles or cells";
+  }
+  return "unknown status";
+}
+
+const char* pv_last_cuda_error(void) { return g_cuda_err; }
+
+pv_status pv_grid_create(const pv_grid_desc* desc, pv_grid** out) {
+  if (!desc || !out || desc->n_boxes < 1 || !desc->boxes || desc->flags != 0)
+    return PV_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  pv_grid* g = new (std::nothrow) pv_grid();
+  if (!g) return PV_ERR_OUT_OF_MEMORY;
+  pv_status s = build(g, desc);
+  if (s != PV_OK) {
+    free_all(g);
+    delete g;
+    return s;
+  }
+  *out = g;
+  return PV_OK;
+}
+
+pv_status pv_grid_destroy(pv_grid* g) {
+  if (!g) return PV_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  free_all(g);
+  delete g;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  return PV_OK;
+}
+
+pv_status pv_sort_cells(pv_grid* g, const double* pos, const float* h, const float* m,
+                        float m_uniform, void* stream) {
+  if (!g) return PV_ERR_INVALID_ARGUMENT;
+  if (g->n > 0 && (!pos || !h)) return PV_ERR_INVALID_ARGUMENT;
+  if (!m && !(m_uniform >= 0.0f && std::isfinite(m_uniform))) return PV_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GridDev& d = g->d;
+  const size_t C = (size_t)g->ncell;
+  PV_CUDA(cudaMemsetAsync(d.cell_count, 0, C * sizeof(int32_t), st));
+  PV_CUDA(cudaMemsetAsync(d.cell_Hmax, 0, C * sizeof(float), st));
+  PV_CUDA(cudaMemsetAsync(d.flags, 0, 4 * sizeof(int32_t), st));  // flags, m_max, max_count, n_big
+  PV_CUDA(pv::launch_bin(d, pos, h, m, m_uniform, st));
+  PV_CUDA(pv::launch_scan(d, st));
+  PV_CUDA(pv::launch_scatter(d, pos, h, m, m_uniform, st));
+  PV_CUDA(pv::launch_sort(d, st));
+  g->launches += g->n > 0 ? 5 : 1;
+  g->sorted = true;
+  return PV_OK;
+}
+
+pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, void* stream) {
+  if (!g) return PV_ERR_INVALID_ARGUMENT;
+  if (g->n > 0 && !rho) return PV_ERR_INVALID_ARGUMENT;
+  if (!g->sorted) return PV_ERR_NOT_SORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GridDev& d = g->d;
+  PV_CUDA(cudaMemsetAsync(d.ntask, 0, 2 * sizeof(int32_t), st));  // ntask, task_next
+  PV_CUDA(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned long long), st));
+  PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, st));
+  g->launches += g->n > 0 ? 3 : 1;
+  return PV_OK;
+}
+
+pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drho_dh,
+                              float* g_pos, float* g_h, void* stream) {
+  if (!g) return PV_ERR_INVALID_ARGUMENT;
+  if (g->n > 0 && (!g_rho || !g_pos)) return PV_ERR_INVALID_ARGUMENT;
+  if (!g->sorted) return PV_ERR_NOT_SORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GridDev& d = g->d;
+  PV_CUDA(cudaMemsetAsync(d.ntask, 0, 2 * sizeof(int32_t), st));
+  PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, st));
+  g->launches += g->n > 0 ? 4 : 0;
+  return PV_OK;
+}
+
+pv_status pv_count_candidates(pv_grid* g, void* stream) {
+  if (!g) return PV_ERR_INVALID_ARGUMENT;
+  if (!g->sorted) return PV_ERR_NOT_SORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PV_CUDA(cudaMemsetAsync(g->d.counters + 2, 0, sizeof(unsigned long long), st));
+  PV_CUDA(pv::launch_count_candidates(g->d, st));
+  g->launches += 1;
+  return PV_OK;
+}
+
+pv_status pv_grid_sync(pv_grid* g, void* stream) {
+  if (!g) return PV_ERR_INVALID_ARGUMENT;
+  PV_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  uint32_t flags = 0;
+  PV_CUDA(cudaMemcpy(&flags, g->d.flags, sizeof(flags), cudaMemcpyDeviceToHost));
+  return flags ? PV_ERR_DEVICE : PV_OK;
+}
+
+pv_status pv_grid_stats(pv_grid* g, pv_stats* out) {
+  if (!g || !out) return PV_ERR_INVALID_ARGUMENT;
+  PV_CUDA(cudaDeviceSynchronize());
+  int32_t sc[4];
+  unsigned long long cnt[4];
+  PV_CUDA(cudaMemcpy(sc, g->d.flags, sizeof(sc), cudaMemcpyDeviceToHost));
+  PV_CUDA(cudaMemcpy(cnt, g->d.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+  std::memset(out, 0, sizeof(*out));
+  out->n_particles = g->n;
+  out->n_cells = g->ncell;
+  out->max_cell_count = g->sorted ? sc[2] : 0;
+  out->device_flags = (uint32_t)sc[0];
+  out->interactions = (int64_t)cnt[0];
+  out->guard_pairs = (int64_t)cnt[1];
+  out->candidates = (int64_t)cnt[2];
+  out->device_bytes = (int64_t)g->bytes;
+  out->kernel_launches = g->launches;
+  return out->device_flags ? PV_ERR_DEVICE : PV_OK;
+}
+
+}  // extern "C"

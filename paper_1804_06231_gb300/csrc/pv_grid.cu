@@ -1,0 +1,349 @@
+// pv_grid.cu -- cell grid and the 13 sorted projections per cell.
+//
+// Section 2 of the paper: the domain is split into cells of edge C_l >= the
+// largest interaction radius and the particles of a cell are stored
+// together; for each of the 13 axes joining a cell centre to its neighbours'
+// centres the particles are sorted by their projection on the axis ("dist"
+// and "index" arrays).  Section 3.2: positions are shifted to a cell-local
+// frame in double precision and only then converted to single precision.
+//
+// Kernels (all HBM-bound except the sort, which is shared-memory bound):
+//   k_bin      particle -> cell id, occupancy histogram, cell H_max, m_max,
+//              input checks (latched flags)
+//   k_scan     exclusive scan of the occupancies, list of big cells
+//   k_scatter  cell-order copies: FP32 offsets + normalised mass, h, caller
+//              index, wrapped FP64 position
+//   k_sort_small  one CTA per cell of <= 512 particles, one warp per axis:
+//              bucket (counting) sort in shared memory, exact order inside a
+//              bucket by (projection, caller index)
+//   k_sort_big    one CTA per larger cell, axes in turn, same algorithm with
+//              the buckets in global scratch
+#include <cuda_runtime.h>
+
+#include "pv_internal.cuh"
+
+namespace pv {
+
+namespace {
+
+constexpr int kSortSmallMax = 512;
+constexpr int kSortThreads = kNDir * 32;
+
+__device__ __forceinline__ int box_of_particle(const GridDev& g, int p) {
+  // last box whose first index is <= p (boxes are contiguous and ordered)
+  int lo = 0, hi = g.n_boxes - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.box_first[mid] <= (int64_t)p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+  double y = x - L * floor(x / L);
+  if (y >= L) y = 0.0;
+  if (y < 0.0) y = 0.0;
+  return y;
+}
+
+__global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
+                      const float* __restrict__ m, float m_uniform) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  const BoxDev B = g.boxes[box_of_particle(g, p)];
+  uint32_t flags = 0;
+  int c3[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double x = pos[3 * (size_t)p + c];
+    if (!isfinite(x)) { flags |= PV_FLAG_BAD_POSITION; x = 0.0; }
+    x = wrap_coord(x, B.L);
+    int ci = (int)floor(x / B.edge);
+    c3[c] = ci < 0 ? 0 : (ci >= B.nc ? B.nc - 1 : ci);
+  }
+  int cell = B.cell_base + (c3[0] * B.nc + c3[1]) * B.nc + c3[2];
+  float hv = h[p];
+  float mv = m ? m[p] : m_uniform;
+  if (!(hv > 0.0f) || !isfinite(hv) || !(mv >= 0.0f) || !isfinite(mv)) {
+    flags |= PV_FLAG_BAD_SMOOTHING;
+    hv = 0.0f;
+  }
+  if (g.gamma_d * (double)hv > B.edge) flags |= PV_FLAG_SUPPORT_EXCEEDS_CELL;
+  if (flags) atomicOr(g.flags, flags);
+  g.pcell[p] = cell;
+  g.prank[p] = atomicAdd(&g.cell_count[cell], 1);
+  atomic_max_nonneg(&g.cell_Hmax[cell], g.gamma * hv);
+  if (mv > 0.0f) atomic_max_nonneg(g.m_max, mv);
+}
+
+// Single-CTA exclusive scan of the cell occupancies (C is at most a few
+// million; each thread scans a contiguous chunk).
+__global__ void __launch_bounds__(1024) k_scan(GridDev g) {
+  __shared__ int s_part[1024];
+  __shared__ int s_max[32];
+  const int C = g.ncell, T = blockDim.x, t = threadIdx.x;
+  const int per = (C + T - 1) / T;
+  const int c0 = min(C, t * per), c1 = min(C, c0 + per);
+  int sum = 0, mx = 0;
+  for (int c = c0; c < c1; c++) {
+    int v = g.cell_count[c];
+    sum += v;
+    mx = max(mx, v);
+  }
+  s_part[t] = sum;
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) s_max[t >> 5] = mx;
+  __syncthreads();
+  // Hillis-Steele inclusive scan of the chunk sums
+  for (int o = 1; o < T; o <<= 1) {
+    int v = t >= o ? s_part[t - o] : 0;
+    __syncthreads();
+    s_part[t] += v;
+    __syncthreads();
+  }
+  int run = s_part[t] - sum;
+  for (int c = c0; c < c1; c++) {
+    int v = g.cell_count[c];
+    g.cell_start[c] = run;
+    run += v;
+    if (v > kSortSmallMax) g.big_cells[atomicAdd(g.n_big, 1)] = c;
+  }
+  if (t == T - 1) g.cell_start[C] = s_part[T - 1];
+  if (t == 0) {
+    int m = 0;
+    for (int w = 0; w < T / 32; w++) m = max(m, s_max[w]);
+    *g.max_count = m;
+    if (m > PV_MAX_CELL_COUNT) atomicOr(g.flags, PV_FLAG_CELL_OVERFLOW);
+  }
+}
+
+__global__ void k_scatter(GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
+                          const float* __restrict__ m, float m_uniform) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= g.n) return;
+  const int cell = g.pcell[p];
+  const BoxDev B = g.boxes[g.cell_box[cell]];
+  const int s = g.cell_start[cell] + g.prank[p];
+  const int loc = cell - B.cell_base;
+  const int c3[3] = {loc / (B.nc * B.nc), (loc / B.nc) % B.nc, loc % B.nc};
+  double xw[3];
+  float off[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double x = pos[3 * (size_t)p + c];
+    if (!isfinite(x)) x = 0.0;
+    xw[c] = wrap_coord(x, B.L);
+    off[c] = (float)(xw[c] - (c3[c] + 0.5) * B.edge);  // shift first, then round
+    g.pos64[3 * (size_t)s + c] = xw[c];
+  }
+  float mmax = *g.m_max;
+  float mv = m ? m[p] : m_uniform;
+  float mn = mmax > 0.0f ? mv / mmax : 0.0f;
+  g.xm[s] = make_float4(off[0], off[1], off[2], mn);
+  g.hs[s] = h[p];
+  g.orig[s] = p;
+}
+
+__device__ __forceinline__ bool key_less(float ka, int oa, float kb, int ob) {
+  return ka < kb || (ka == kb && oa < ob);
+}
+
+template <bool kBlock>
+__device__ __forceinline__ void group_sync() {
+  if (kBlock) __syncthreads(); else __syncwarp();
+}
+
+// Sorts the cnt particles of one cell by key.  `grp` threads (a warp, or the
+// whole block when kBlock) with ranks 0..grp-1 cooperate.  Arrays:
+//   orig[cnt] (tie break), key[cnt], out[cnt] (sorted cell-local indices),
+//   bucket[B], chunk[grp] (scratch for the scan).
+template <bool kBlock>
+__device__ void sort_axis(int cnt, const int* orig, const float* key, int* out, int* bucket,
+                          int* chunk, int B, int rank, int grp, float kmin, float kmax) {
+  const float scale = kmax > kmin ? (float)B / (kmax - kmin) : 0.0f;
+  for (int b = rank; b < B; b += grp) bucket[b] = 0;
+  group_sync<kBlock>();
+  for (int t = rank; t < cnt; t += grp) {
+    int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
+    atomicAdd(&bucket[b], 1);
+  }
+  group_sync<kBlock>();
+  // exclusive scan of bucket[0..B): contiguous chunks, then a serial pass
+  // over the chunk totals by the group (B / grp is small)
+  const int per = (B + grp - 1) / grp;
+  const int b0 = min(B, rank * per), b1 = min(B, b0 + per);
+  int sum = 0;
+  for (int b = b0; b < b1; b++) sum += bucket[b];
+  chunk[rank] = sum;
+  group_sync<kBlock>();
+  if (rank == 0) {
+    int run = 0;
+    for (int r = 0; r < grp; r++) { int v = chunk[r]; chunk[r] = run; run += v; }
+  }
+  group_sync<kBlock>();
+  int run = chunk[rank];
+  for (int b = b0; b < b1; b++) { int v = bucket[b]; bucket[b] = run; run += v; }
+  group_sync<kBlock>();
+  // scatter (order inside a bucket is fixed below)
+  for (int t = rank; t < cnt; t += grp) {
+    int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
+    out[atomicAdd(&bucket[b], 1)] = t;
+  }
+  group_sync<kBlock>();
+  // bucket[b] is now the end of bucket b: insertion sort by (key, orig)
+  for (int b = rank; b < B; b += grp) {
+    int s0 = b ? bucket[b - 1] : 0, s1 = bucket[b];
+    for (int i = s0 + 1; i < s1; i++) {
+      int v = out[i];
+      float kv = key[v];
+      int ov = orig[v];
+      int j = i - 1;
+      while (j >= s0 && key_less(kv, ov, key[out[j]], orig[out[j]])) {
+        out[j + 1] = out[j];
+        j--;
+      }
+      out[j + 1] = v;
+    }
+  }
+  group_sync<kBlock>();
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
+  extern __shared__ float4 smem4[];
+  float4* s_x = smem4;                                            // [512]
+  int* s_orig = reinterpret_cast<int*>(s_x + kSortSmallMax);       // [512]
+  float* s_key = reinterpret_cast<float*>(s_orig + kSortSmallMax); // [13][512]
+  int* s_out = reinterpret_cast<int*>(s_key + kNDir * kSortSmallMax);  // [13][512]
+  int* s_bkt = s_out + kNDir * kSortSmallMax;                      // [13][512 + 32]
+  // per warp: buckets [512], then 32 ints of scan scratch
+  const int c = blockIdx.x;
+  const int cnt = g.cell_count[c];
+  if (cnt == 0 || cnt > kSortSmallMax) return;
+  const int cs = g.cell_start[c];
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    s_x[t] = g.xm[cs + t];
+    s_orig[t] = g.orig[cs + t];
+  }
+  __syncthreads();
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float ux, uy, uz;
+  axis_u(k, ux, uy, uz);
+  float* key = s_key + k * kSortSmallMax;
+  int* out = s_out + k * kSortSmallMax;
+  int* bkt = s_bkt + k * (kSortSmallMax + 32);
+  float kmin = 3.0e38f, kmax = -3.0e38f;
+  for (int t = lane; t < cnt; t += 32) {
+    float d = project(s_x[t], ux, uy, uz);
+    key[t] = d;
+    kmin = fminf(kmin, d);
+    kmax = fmaxf(kmax, d);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  }
+  int B = 32;
+  while (B < cnt) B <<= 1;
+  sort_axis<false>(cnt, s_orig, key, out, bkt, bkt + kSortSmallMax, B, lane, 32, kmin, kmax);
+  const size_t base = (size_t)k * g.n + cs;
+  for (int t = lane; t < cnt; t += 32) {
+    int v = out[t];
+    g.perm[base + t] = (uint16_t)v;
+    g.dist[base + t] = key[v];
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_sort_big(GridDev g) {
+  __shared__ float s_red[2][32];
+  __shared__ int s_chunk[1024];
+  const int nbig = *g.n_big;
+  for (int idx = blockIdx.x; idx < nbig; idx += gridDim.x) {
+    const int c = g.big_cells[idx];
+    const int cnt = min(g.cell_count[c], PV_MAX_CELL_COUNT);
+    const int cs = g.cell_start[c];
+    int B = 32;
+    while (B < cnt) B <<= 1;
+    float* key = g.skey + cs;
+    int* out = g.sbuf + cs;
+    // buckets: B <= 2 cnt slots of the cell's own range [2 cs, 2 cs + 2 cnt)
+    int* bkt = g.sbucket + 2 * (size_t)cs;
+    for (int k = 0; k < kNDir; k++) {
+      float ux, uy, uz;
+      axis_u(k, ux, uy, uz);
+      float kmin = 3.0e38f, kmax = -3.0e38f;
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        float d = project(g.xm[cs + t], ux, uy, uz);
+        key[t] = d;
+        kmin = fminf(kmin, d);
+        kmax = fmaxf(kmax, d);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        s_red[0][threadIdx.x >> 5] = kmin;
+        s_red[1][threadIdx.x >> 5] = kmax;
+      }
+      __syncthreads();
+      kmin = s_red[0][0];
+      kmax = s_red[1][0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+        kmin = fminf(kmin, s_red[0][w]);
+        kmax = fmaxf(kmax, s_red[1][w]);
+      }
+      __syncthreads();
+      sort_axis<true>(cnt, g.orig + cs, key, out, bkt, s_chunk, B, threadIdx.x, blockDim.x, kmin,
+                      kmax);
+      const size_t base = (size_t)k * g.n + cs;
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        int v = out[t];
+        g.perm[base + t] = (uint16_t)v;
+        g.dist[base + t] = key[v];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const GridDev& g, const double* pos, const float* h, const float* m,
+                       float m_uniform, cudaStream_t st) {
+  if (g.n == 0) return cudaSuccess;
+  k_bin<<<(g.n + 255) / 256, 256, 0, st>>>(g, pos, h, m, m_uniform);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const GridDev& g, cudaStream_t st) {
+  k_scan<<<1, 1024, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const GridDev& g, const double* pos, const float* h, const float* m,
+                           float m_uniform, cudaStream_t st) {
+  if (g.n == 0) return cudaSuccess;
+  k_scatter<<<(g.n + 255) / 256, 256, 0, st>>>(g, pos, h, m, m_uniform);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const GridDev& g, cudaStream_t st) {
+  if (g.n == 0) return cudaSuccess;
+  const size_t smem = kSortSmallMax * (sizeof(float4) + sizeof(int)) +
+                      kNDir * kSortSmallMax * (sizeof(float) + sizeof(int)) +
+                      kNDir * (kSortSmallMax + 32) * sizeof(int);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_sort_small<<<g.ncell, kSortThreads, smem, st>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sort_big<<<256, 1024, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace pv

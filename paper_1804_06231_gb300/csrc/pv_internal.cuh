@@ -1,0 +1,236 @@
+// pv_internal.cuh -- device-side data layout and helpers shared by the CUDA
+// translation units of the pseudo-Verlet density library (sm_103a).
+//
+// Layout in HBM (all particle arrays are in "cell order": the particles of a
+// cell are contiguous, cells in global cell-id order, boxes one after the
+// other):
+//   xm    float4 [N]       {x', y', z', m/m_max}: FP32 offset of the particle
+//                          from its cell centre (Section 3.2: shift, then
+//                          convert to single precision) and normalised mass
+//   hs    float  [N]       smoothing length h (support H = gamma h)
+//   orig  int32  [N]       index of the particle in the caller's arrays
+//   pos64 double [N][3]    wrapped FP64 position (only read to re-decide
+//                          pairs whose FP32 distance is within rounding of H)
+//   perm  uint16 [13][N]   per cell and axis k: cell-local index of the t-th
+//                          particle in ascending projection on u_k
+//   dist  float  [13][N]   the projection itself (the "dist"/"index" arrays
+//                          of Section 2)
+//   cell_start int32 [C+1], cell_Hmax float [C]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pv.h"
+
+namespace pv {
+
+constexpr int kNDir = 13;   // distinct axes joining neighbouring cell centres
+constexpr int kNSlot = 27;  // neighbour offsets (ox,oy,oz) in {-1,0,1}^3
+constexpr int kSelfSlot = 13;
+constexpr int kFixShift = 36;                       // fixed-point scale 2^36
+constexpr double kFixScale = 68719476736.0;         // 2^36
+constexpr double kFixInv = 1.0 / 68719476736.0;
+constexpr float kPiF = 3.14159265358979f;
+
+struct BoxDev {
+  double L, inv_L, edge, inv_edge;
+  float edge_f;    // FP32 cell edge
+  float pad;       // window pad covering FP32 rounding of projections
+  float guard;     // guard half-width factor for r^2 (see guard_band())
+  int32_t nc;
+  int32_t cell_base;  // first global cell id of the box
+  int64_t first, n;
+};
+
+// Everything a kernel needs, passed by value.
+struct GridDev {
+  int32_t n_boxes, n, ncell;
+  float gamma;
+  double gamma_d;
+  const BoxDev* boxes;
+  const int64_t* box_first;  // [n_boxes] (for particle -> box lookup)
+  // per cell
+  int32_t* cell_count;  // [C]
+  int32_t* cell_start;  // [C+1]
+  int32_t* cell_box;    // [C]
+  float* cell_Hmax;     // [C]
+  int32_t* big_cells;   // [C] list of cells sorted by the big-cell path
+  int32_t* n_big;       // [1]
+  // per particle, caller order
+  int32_t* pcell;
+  int32_t* prank;
+  // per particle, cell order
+  float4* xm;
+  float* hs;
+  int32_t* orig;
+  double* pos64;
+  uint16_t* perm;  // [13][N]
+  float* dist;     // [13][N]
+  // sort scratch for big cells (cell order)
+  float* skey;
+  int32_t* sbuf;
+  int32_t* sbucket;  // [2N]
+  // density accumulators (cell order), fixed point
+  long long* acc;    // [3][N]: rho, drho/dh (2^36 scale), n
+  // backward accumulators (cell order), FP64 [5][N]: sum m th, sum m uh, gx, gy, gz
+  long long* gacc;
+  float4* gk;        // [N] backward: {g/H^5, k/(h H^5), H^2+guard, H^2-guard}, cell order
+  float2* ghh;       // [N] backward: {1/H, H}
+  // tasks
+  int4* tasks;
+  int32_t* ntask;
+  int32_t* task_next;
+  int32_t max_tasks;
+  // scalars
+  uint32_t* flags;
+  float* m_max;
+  int32_t* max_count;
+  unsigned long long* counters;  // [0] interactions, [1] guard pairs, [2] candidates
+};
+
+// ---- direction slots ------------------------------------------------------
+// Slot o = (ox+1)*9 + (oy+1)*3 + (oz+1) for the neighbour offset (ox,oy,oz).
+// The slot number orders offsets lexicographically, so the 13 axes v_k (the
+// lexicographically positive offsets, Section 2) are the slots 14..26 with
+// k = o - 14, and slot o < 13 is -v_k with k = 12 - o.  The self slot is 13.
+struct Slot {
+  int ox, oy, oz;  // offset of the neighbour cell
+  int k, s;        // axis index and sign: (ox,oy,oz) = s v_k
+  int v2;          // |v|^2: 1 face, 2 edge, 3 corner (0 for the self slot)
+};
+
+__host__ __device__ __forceinline__ Slot slot_info(int o) {
+  Slot r;
+  r.ox = o / 9 - 1;
+  r.oy = (o / 3) % 3 - 1;
+  r.oz = o % 3 - 1;
+  r.v2 = r.ox * r.ox + r.oy * r.oy + r.oz * r.oz;
+  if (o > kSelfSlot) { r.k = o - 14; r.s = 1; }
+  else if (o < kSelfSlot) { r.k = 12 - o; r.s = -1; }
+  else { r.k = 0; r.s = 1; }  // the self sweep uses axis (0,0,1)
+  return r;
+}
+
+// |v|^-1 for |v|^2 = 1, 2, 3 (FP32-rounded 1, 1/sqrt2, 1/sqrt3)
+__host__ __device__ __forceinline__ float inv_norm(int v2) {
+  return v2 == 1 ? 1.0f : (v2 == 2 ? 0.70710678f : 0.57735027f);
+}
+__host__ __device__ __forceinline__ float vnorm(int v2) {
+  return v2 == 1 ? 1.0f : (v2 == 2 ? 1.41421356f : 1.73205081f);
+}
+
+// unit axis u_k
+__host__ __device__ __forceinline__ void axis_u(int k, float& ux, float& uy, float& uz) {
+  Slot sl = slot_info(14 + k);
+  float in = inv_norm(sl.v2);
+  ux = sl.ox * in; uy = sl.oy * in; uz = sl.oz * in;
+}
+
+// projection of an FP32 offset on u_k (the sort key and the stored dist)
+__device__ __forceinline__ float project(float4 x, float ux, float uy, float uz) {
+  return fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz));
+}
+
+// neighbour cell of global cell a at slot o (periodic wrap inside the box)
+__device__ __forceinline__ int neighbour_cell(const GridDev& g, int a, int o) {
+  const BoxDev& B = g.boxes[g.cell_box[a]];
+  int nc = B.nc, loc = a - B.cell_base;
+  int cx = loc / (nc * nc), cy = (loc / nc) % nc, cz = loc % nc;
+  const Slot si = slot_info(o);
+  cx += si.ox; cy += si.oy; cz += si.oz;
+  cx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
+  cy = cy < 0 ? cy + nc : (cy >= nc ? cy - nc : cy);
+  cz = cz < 0 ? cz + nc : (cz >= nc ? cz - nc : cz);
+  return B.cell_base + (cx * nc + cy) * nc + cz;
+}
+
+// ---- float <-> orderable int for atomicMax on non-negative floats ---------
+__device__ __forceinline__ void atomic_max_nonneg(float* p, float v) {
+  atomicMax(reinterpret_cast<int*>(p), __float_as_int(v));
+}
+
+// first index t in [0, n) with a[t] >= x (a ascending), n if none
+__device__ __forceinline__ int lower_bound_f(const float* a, int n, float x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// first index t in [0, n) with a[t] > x, n if none
+__device__ __forceinline__ int upper_bound_f(const float* a, int n, float x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Projection of particle p of cell c on axis k, in the frame of cell a,
+// along u = s u_k, in ascending order t = 0 .. cnt-1:
+//   stored order for s = +1, reversed for s = -1; d = s dist + offset.
+__host__ __device__ __forceinline__ int order_pos(int s, int t, int cnt) { return s > 0 ? t : cnt - 1 - t; }
+
+// ---- cubic spline, half-scaled ---------------------------------------------
+// With w(q) the shape function of the workload (8/pi factor included),
+// wh(q) = w(q) / (16/pi) and th(q) = (3 w(q) + q w'(q)) / (16/pi):
+//   q < 1/2 : wh = 1/2 + q^2 (3q - 3),  th = 3/2 + q^2 (18q - 15)
+//   q < 1   : wh = s^3,                  th = s^2 (3 - 6q),   s = 1 - q
+// so rho_i = (16/pi) H_i^-3 sum_j m_j wh(q_ij) and
+//    drho/dh_i = -(16/pi) / (h_i H_i^3) sum_j m_j th(q_ij).
+__device__ __forceinline__ void spline_half(float q, float q2, float& wh, float& th) {
+  float win = fmaf(q2, fmaf(3.0f, q, -3.0f), 0.5f);
+  float tin = fmaf(q2, fmaf(18.0f, q, -15.0f), 1.5f);
+  float s = fmaxf(1.0f - q, 0.0f);
+  float s2 = s * s;
+  float wout = s2 * s;
+  float tout = s2 * fmaf(-6.0f, q, 3.0f);
+  bool inner = q < 0.5f;
+  wh = inner ? win : wout;
+  th = inner ? tin : tout;
+}
+
+// Guard band of the FP32 distance test.  The FP32 r^2 of a pair differs from
+// the exact one by less than
+//   2 r |d(dx)| sqrt(3) + 3 ulp(r^2)  with |d(dx)| <= 2^-22 edge
+// (offsets rounded to 2^-24 edge, the shifted i position to 2^-23 edge, the
+// difference to 2^-24 H), i.e. < 1.2e-6 H edge + 3.6e-7 H^2 for r ~ H.
+// Pairs whose FP32 r^2 lies within twice that of H^2 are re-decided in FP64.
+__device__ __forceinline__ float guard_band(float H, float edge) {
+  return 2.4e-6f * H * edge + 8.0e-7f * H * H;
+}
+
+// FP64 re-decision of r_ij < H_i for a pair in the guard band, from the
+// wrapped FP64 positions with the minimum-image convention.
+static __device__ __noinline__ bool guard_inside(const double* __restrict__ pos64, int si,
+                                                 int sj, double L, double inv_L, double Hd) {
+  double r2 = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    double d = pos64[3 * (size_t)si + c] - pos64[3 * (size_t)sj + c];
+    d -= L * rint(d * inv_L);
+    r2 = fma(d, d, r2);
+  }
+  return r2 < Hd * Hd;
+}
+
+// ---- host-side launchers (defined in the .cu files) ------------------------
+cudaError_t launch_bin(const GridDev& g, const double* pos, const float* h, const float* m,
+                       float m_uniform, cudaStream_t st);
+cudaError_t launch_scan(const GridDev& g, cudaStream_t st);
+cudaError_t launch_scatter(const GridDev& g, const double* pos, const float* h, const float* m,
+                           float m_uniform, cudaStream_t st);
+cudaError_t launch_sort(const GridDev& g, cudaStream_t st);
+cudaError_t launch_plan(const GridDev& g, int wide, cudaStream_t st);
+int64_t max_tasks_for(int64_t n, int64_t ncell);
+cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t* n_ngb,
+                           int num_sms, cudaStream_t st);
+cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g_drho_dh,
+                            float* g_pos, float* g_h, int num_sms, cudaStream_t st);
+cudaError_t launch_count_candidates(const GridDev& g, cudaStream_t st);
+
+}  // namespace pv

@@ -1,0 +1,271 @@
+"""Python binding of the C ABI in ``include/pv.h`` (argument marshalling only).
+
+The functions named ``pv_*`` mirror the C entry points one to one: they take
+device pointers as Python ints (e.g. ``tensor.data_ptr()``) and a CUDA stream
+handle (``torch.cuda.current_stream().cuda_stream``), and raise ``PvError`` on
+any status other than ``PV_OK``.  ``Grid`` wraps a ``pv_grid*`` for torch
+tensors.  All computation happens in ``libpv.so``; if the library is missing
+this module raises on import of the library, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpv.so")
+
+PV_OK = 0
+STATUS = {0: "PV_OK", 1: "PV_ERR_INVALID_ARGUMENT", 2: "PV_ERR_CELL_TOO_SMALL",
+          3: "PV_ERR_OUT_OF_MEMORY", 4: "PV_ERR_CUDA", 5: "PV_ERR_NOT_SORTED",
+          6: "PV_ERR_DEVICE", 7: "PV_ERR_TOO_LARGE"}
+FLAG_SUPPORT_EXCEEDS_CELL = 1
+FLAG_BAD_POSITION = 2
+FLAG_BAD_SMOOTHING = 4
+FLAG_CELL_OVERFLOW = 8
+MAX_CELL_COUNT = 65535
+GAMMA = 1.825742
+
+#: Every symbol ``include/pv.h`` declares.
+EXPORTS = ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
+           "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
+           "pv_status_str", "pv_last_cuda_error")
+
+
+class PvError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class pv_box_desc(ctypes.Structure):
+    _fields_ = [("first", ctypes.c_int64), ("n", ctypes.c_int64), ("L", ctypes.c_double),
+                ("nc", ctypes.c_int32)]
+
+
+class pv_grid_desc(ctypes.Structure):
+    _fields_ = [("n_boxes", ctypes.c_int32), ("boxes", ctypes.POINTER(pv_box_desc)),
+                ("gamma", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+class pv_stats(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int64), ("n_cells", ctypes.c_int64),
+                ("max_cell_count", ctypes.c_int32), ("device_flags", ctypes.c_uint32),
+                ("interactions", ctypes.c_int64), ("guard_pairs", ctypes.c_int64),
+                ("candidates", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads ``libpv.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1804_06231_gb300.build "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int
+    lib.pv_grid_create.argtypes = [ctypes.POINTER(pv_grid_desc), ctypes.POINTER(vp)]
+    lib.pv_grid_destroy.argtypes = [vp]
+    lib.pv_sort_cells.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp]
+    lib.pv_density.argtypes = [vp, vp, vp, vp, vp]
+    lib.pv_density_backward.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.pv_count_candidates.argtypes = [vp, vp]
+    lib.pv_grid_sync.argtypes = [vp, vp]
+    lib.pv_grid_stats.argtypes = [vp, ctypes.POINTER(pv_stats)]
+    for name in ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
+                 "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats"):
+        getattr(lib, name).restype = i32
+    lib.pv_status_str.argtypes = [i32]
+    lib.pv_status_str.restype = ctypes.c_char_p
+    lib.pv_last_cuda_error.argtypes = []
+    lib.pv_last_cuda_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != PV_OK:
+        detail = ""
+        if status == 4:
+            detail = load_library().pv_last_cuda_error().decode()
+        raise PvError(status, where, detail)
+
+
+# ---------------------------------------------------------------- C-ABI mirrors
+
+def pv_status_str(status: int) -> str:
+    return load_library().pv_status_str(int(status)).decode()
+
+
+def pv_grid_create(boxes, gamma: float = 0.0) -> int:
+    """boxes: sequence of (first, n, L, nc).  Returns the opaque grid handle."""
+    arr = (pv_box_desc * len(boxes))(*[pv_box_desc(int(f), int(n), float(L), int(nc))
+                                       for f, n, L, nc in boxes])
+    desc = pv_grid_desc(len(boxes), arr, float(gamma), 0)
+    out = ctypes.c_void_p()
+    _check(load_library().pv_grid_create(ctypes.byref(desc), ctypes.byref(out)), "pv_grid_create")
+    return out.value
+
+
+def pv_grid_destroy(grid: int) -> None:
+    _check(load_library().pv_grid_destroy(grid), "pv_grid_destroy")
+
+
+def pv_sort_cells(grid: int, pos: int, h: int, m: int | None, m_uniform: float = 0.0,
+                  stream: int = 0) -> None:
+    _check(load_library().pv_sort_cells(grid, pos, h, m, ctypes.c_float(m_uniform), stream),
+           "pv_sort_cells")
+
+
+def pv_density(grid: int, rho: int, drho_dh: int | None, n_ngb: int | None,
+               stream: int = 0) -> None:
+    _check(load_library().pv_density(grid, rho, drho_dh, n_ngb, stream), "pv_density")
+
+
+def pv_density_backward(grid: int, g_rho: int, g_drho_dh: int | None, g_pos: int,
+                        g_h: int | None, stream: int = 0) -> None:
+    _check(load_library().pv_density_backward(grid, g_rho, g_drho_dh, g_pos, g_h, stream),
+           "pv_density_backward")
+
+
+def pv_count_candidates(grid: int, stream: int = 0) -> None:
+    _check(load_library().pv_count_candidates(grid, stream), "pv_count_candidates")
+
+
+def pv_grid_sync(grid: int, stream: int = 0) -> None:
+    _check(load_library().pv_grid_sync(grid, stream), "pv_grid_sync")
+
+
+@dataclass
+class Stats:
+    n_particles: int
+    n_cells: int
+    max_cell_count: int
+    device_flags: int
+    interactions: int
+    guard_pairs: int
+    candidates: int
+    device_bytes: int
+    kernel_launches: int
+
+
+def pv_grid_stats(grid: int, raise_on_flags: bool = True) -> Stats:
+    st = pv_stats()
+    status = load_library().pv_grid_stats(grid, ctypes.byref(st))
+    out = Stats(*(getattr(st, f) for f, _ in pv_stats._fields_))
+    if status != PV_OK and (raise_on_flags or status != 6):
+        raise PvError(status, "pv_grid_stats", f"device_flags={out.device_flags}")
+    return out
+
+
+# ---------------------------------------------------------------- torch wrapper
+
+class Grid:
+    """A ``pv_grid`` for particles held in torch tensors on the current device.
+
+    ``boxes`` is a sequence of ``(n, L, nc)`` (or one tuple): the particles of
+    box b are the next ``n`` rows of the arrays passed to ``sort``.
+    """
+
+    def __init__(self, boxes, gamma: float = GAMMA):
+        if isinstance(boxes, tuple) and len(boxes) == 3 and not isinstance(boxes[0], tuple):
+            boxes = [boxes]
+        first, descs = 0, []
+        for n, L, nc in boxes:
+            descs.append((first, int(n), float(L), int(nc)))
+            first += int(n)
+        self.n = first
+        self.boxes = descs
+        self.gamma = float(gamma)
+        self.handle = pv_grid_create(descs, gamma)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            pv_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _stream(stream):
+        import torch
+        if stream is None:
+            return torch.cuda.current_stream().cuda_stream
+        return getattr(stream, "cuda_stream", stream)
+
+    @staticmethod
+    def _dev(t, dtype, shape=None, name=""):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+        return t.data_ptr()
+
+    def sort(self, pos, h, m=None, m_uniform: float = 0.0, stream=None) -> None:
+        import torch
+        p = self._dev(pos, torch.float64, (self.n, 3), "pos")
+        hp = self._dev(h, torch.float32, (self.n,), "h")
+        mp = None if m is None else self._dev(m, torch.float32, (self.n,), "m")
+        pv_sort_cells(self.handle, p, hp, mp, m_uniform, self._stream(stream))
+
+    def density(self, rho=None, drho_dh=None, n_ngb=None, stream=None):
+        import torch
+        if rho is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            rho = torch.empty(self.n, dtype=torch.float32, device=dev)
+            drho_dh = torch.empty(self.n, dtype=torch.float32, device=dev)
+            n_ngb = torch.empty(self.n, dtype=torch.int32, device=dev)
+        pv_density(self.handle, self._dev(rho, torch.float32, (self.n,), "rho"),
+                   None if drho_dh is None else self._dev(drho_dh, torch.float32, (self.n,),
+                                                          "drho_dh"),
+                   None if n_ngb is None else self._dev(n_ngb, torch.int32, (self.n,), "n_ngb"),
+                   self._stream(stream))
+        return rho, drho_dh, n_ngb
+
+    def backward(self, g_rho, g_drho_dh=None, g_pos=None, g_h=None, stream=None):
+        import torch
+        if g_pos is None:
+            g_pos = torch.empty((self.n, 3), dtype=torch.float32, device=g_rho.device)
+            g_h = torch.empty(self.n, dtype=torch.float32, device=g_rho.device)
+        pv_density_backward(
+            self.handle, self._dev(g_rho, torch.float32, (self.n,), "g_rho"),
+            None if g_drho_dh is None else self._dev(g_drho_dh, torch.float32, (self.n,),
+                                                     "g_drho_dh"),
+            self._dev(g_pos, torch.float32, (self.n, 3), "g_pos"),
+            None if g_h is None else self._dev(g_h, torch.float32, (self.n,), "g_h"),
+            self._stream(stream))
+        return g_pos, g_h
+
+    def count_candidates(self, stream=None) -> int:
+        pv_count_candidates(self.handle, self._stream(stream))
+        return pv_grid_stats(self.handle).candidates
+
+    def sync(self, stream=None) -> None:
+        pv_grid_sync(self.handle, self._stream(stream))
+
+    def stats(self, raise_on_flags: bool = True) -> Stats:
+        return pv_grid_stats(self.handle, raise_on_flags)

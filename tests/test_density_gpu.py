@@ -1,0 +1,146 @@
+"""GPU parity of pv_sort_cells + pv_density against the FP64 oracle.
+
+Bar: rho within 1e-5 relative; drho/dh within 1e-4 of S_i = sum_j m_j |dW/dh|
+(drho/dh is a sum of terms of both signs, so a plain relative test is
+ill-conditioned); n_i bit-exact except where the oracle finds a pair within
+1e-6 relative of the cut-off, where the difference is bounded by that count.
+"""
+import numpy as np
+import pytest
+
+from paper_1804_06231_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+from gpu_util import check_density, run_density  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_06231_gb300 import build
+    build.build_library()
+
+
+@pytest.mark.parametrize("nc", [3, 5, 12])
+def test_uniform_32k_vs_brute_force(oracle_lib, nc):
+    box = I.cfg0()
+    box.nc = nc
+    rho, D, n, st, _ = run_density(box, uniform_mass=True)
+    ref = oracle_lib.density_brute(box.pos, box.h, box.m)
+    check_density(rho, D, n, ref)
+    assert st.interactions == int(n.sum())
+    assert st.device_flags == 0
+
+
+def test_clustered_vs_oracle(oracle_lib):
+    box = I.clustered(60000, 17)
+    rho, D, n, st, _ = run_density(box)
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
+    check_density(rho, D, n, ref)
+    assert st.max_cell_count > 512   # exercises the large-cell sort path
+
+
+def test_large_cells_vs_oracle(oracle_lib):
+    """Coarse grid: ~1200 particles per cell (large-cell sort, many j tiles)."""
+    box = I.uniform(32768, 41, nc=3)
+    rho, D, n, st, _ = run_density(box)
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, 3)
+    check_density(rho, D, n, ref)
+
+
+def test_masses_vary(oracle_lib):
+    box = I.uniform(20000, 9)
+    rng = np.random.default_rng(1)
+    box.m = (box.m * rng.uniform(0.2, 5.0, box.n)).astype(np.float32)
+    rho, D, n, _, _ = run_density(box)
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
+    check_density(rho, D, n, ref)
+
+
+def test_lattice_exact_constant(oracle_lib):
+    box = I.lattice(24, nc=8)
+    rho, D, n, _, _ = run_density(box)
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
+    check_density(rho, D, n, ref)
+    assert np.all(n == 56)
+
+
+def test_test27cells_shape(oracle_lib):
+    box = I.test27cells()
+    rho, D, n, _, _ = run_density(box)
+    ref = oracle_lib.density_brute(box.pos, box.h, box.m)
+    check_density(rho, D, n, ref)
+
+
+def test_edge_cases(oracle_lib):
+    """Particles on cell faces, at x = 1 - eps, duplicates, an isolated particle."""
+    rng = np.random.default_rng(3)
+    n = 3000
+    pos = rng.random((n, 3))
+    nc = 6
+    pos[:200, 0] = np.floor(pos[:200, 0] * nc) / nc          # exactly on faces
+    pos[200:300, 1] = 1.0 - 1e-13                             # just below the wrap
+    pos[300:320] = pos[320:340]                               # duplicates
+    pos[340] = [1.0, 0.5, -0.25]                              # needs wrapping
+    h = (I.ETA * n ** (-1 / 3) * rng.uniform(0.9, 1.1, n)).astype(np.float32)
+    m = np.full(n, 1.0 / n, np.float32)
+    box = I.Box(pos, h, m, 1.0, nc)
+    rho, D, nn, _, _ = run_density(box)
+    ref = oracle_lib.density_brute(pos, h, m)
+    check_density(rho, D, nn, ref)
+
+
+def test_tiny_and_empty_boxes(oracle_lib):
+    one = I.Box(np.array([[0.3, 0.4, 0.5]]), np.array([0.05], np.float32),
+                np.array([2.0], np.float32), 1.0, 3)
+    empty = I.Box(np.zeros((0, 3)), np.zeros(0, np.float32), np.zeros(0, np.float32), 1.0, 4)
+    small = I.uniform(700, 5)
+    rho, D, n, st, _ = run_density([one, empty, small])
+    ref_one = oracle_lib.density_brute(one.pos, one.h, one.m)
+    ref_small = oracle_lib.density_brute(small.pos, small.h, small.m)
+    check_density(rho[:1], D[:1], n[:1], ref_one)
+    check_density(rho[1:], D[1:], n[1:], ref_small)
+    assert n[0] == 0
+
+
+def test_symmetries(oracle_lib):
+    box = I.uniform(40000, 77, nc=10)
+    rho0, D0, n0, _, _ = run_density(box)
+    rot = I.Box(np.ascontiguousarray(box.pos[:, [1, 2, 0]]), box.h, box.m, 1.0, box.nc)
+    rho1, D1, n1, _, _ = run_density(rot)
+    sh = I.Box(np.mod(box.pos + [0.123, 0.456, 0.789], 1.0), box.h, box.m, 1.0, box.nc)
+    rho2, D2, n2, _, _ = run_density(sh)
+    for r, nn in ((rho1, n1), (rho2, n2)):
+        assert np.abs(r / rho0 - 1).max() < 2e-6
+        assert (nn != n0).sum() <= 2
+
+
+def test_deterministic(oracle_lib):
+    box = I.clustered(50000, 5)
+    a = run_density(box)
+    b = run_density(box)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2])
+
+
+def test_candidates_match_oracle_windows(oracle_lib):
+    """pv_count_candidates counts the sorted-window distance tests of the method."""
+    box = I.uniform(30000, 8, nc=8)
+    _, _, _, st, cand = run_density(box, count_candidates=True)
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
+    assert cand == pytest.approx(int(ref.counters[:, 0].sum()), rel=1e-5)
+
+
+@pytest.mark.slow
+def test_uniform_1m_headline_sampled(oracle_lib):
+    """N = 1,048,576 at 15^3 cells (the benchmark's launch configuration): all
+    particles against the oracle's pseudo-Verlet sweep."""
+    box = I.cfg1()
+    rho, D, n, st, _ = run_density(box, uniform_mass=True)
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
+    check_density(rho, D, n, ref)
+    assert st.interactions == int(ref.n_ngb.sum()) or \
+        abs(st.interactions - int(ref.n_ngb.sum())) <= int(ref.band.sum())
