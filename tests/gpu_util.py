@@ -13,7 +13,7 @@ def torch_dev():
     return torch.device("cuda", 0)
 
 
-def run_density(boxes, uniform_mass=False, count_candidates=False):
+def run_density(boxes, uniform_mass=False, count_candidates=False, expect_flags=False):
     """Runs sort + density on one or more Box objects (concatenated)."""
     import torch
     from paper_1804_06231_gb300.pv import Grid
@@ -32,6 +32,9 @@ def run_density(boxes, uniform_mass=False, count_candidates=False):
         cand = g.count_candidates() if count_candidates else None
         st = g.stats(raise_on_flags=False)
     torch.cuda.synchronize()
+    if not expect_flags:
+        assert st.device_flags == 0, f"device flags {st.device_flags}"
+
     return (rho.cpu().numpy().astype(np.float64), D.cpu().numpy().astype(np.float64),
             n.cpu().numpy(), st, cand)
 

@@ -80,7 +80,7 @@ def test_edge_cases(oracle_lib):
     rng = np.random.default_rng(3)
     n = 3000
     pos = rng.random((n, 3))
-    nc = 6
+    nc = 5                       # edge 0.2 >= H_max = 0.172
     pos[:200, 0] = np.floor(pos[:200, 0] * nc) / nc          # exactly on faces
     pos[200:300, 1] = 1.0 - 1e-13                             # just below the wrap
     pos[300:320] = pos[320:340]                               # duplicates
@@ -116,6 +116,14 @@ def test_symmetries(oracle_lib):
     for r, nn in ((rho1, n1), (rho2, n2)):
         assert np.abs(r / rho0 - 1).max() < 2e-6
         assert (nn != n0).sum() <= 2
+
+
+def test_support_above_edge_is_flagged(oracle_lib):
+    """A support larger than the cell edge latches a device flag; outputs untouched."""
+    from paper_1804_06231_gb300 import pv
+    box = I.uniform(3000, 4, nc=6)          # H_max = 0.172 > 1/6
+    rho, D, n, st, _ = run_density(box, expect_flags=True)
+    assert st.device_flags & pv.FLAG_SUPPORT_EXCEEDS_CELL
 
 
 def test_deterministic(oracle_lib):
