@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--impl", default="pv", choices=["pv", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    # smaller uniform workloads with the same h rule, for profiler captures
+    p.add_argument("--particles", type=int, default=0)
+    p.add_argument("--cells", type=int, default=0)
     return p.parse_args()
 
 
@@ -118,8 +121,10 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ workloads
 
-def workload(seed: int):
+def workload(seed: int, particles: int = 0, cells: int = 0):
     from paper_1804_06231_gb300 import inputs as I
+    if particles:
+        return I.uniform(particles, seed, nc=cells or None)
     return I.cfg1(seed)
 
 
@@ -211,7 +216,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     stream = torch.cuda.current_stream()
 
-    box = workload(1 + rank)  # independent box per rank (weak scaling)
+    box = workload(1 + rank, args.particles, args.cells)  # one box per rank (weak scaling)
     n = box.n
     pos = torch.from_numpy(box.pos).to(dev)
     h = torch.from_numpy(box.h).to(dev)
@@ -361,7 +366,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_particles_per_gpu": n, "cells": box.nc ** 3,
+            "config": {"workload": WORKLOAD if not args.particles else
+                       f"uniform N={n}, {box.nc}^3 cells (profiling size)", "n_particles_per_gpu": n, "cells": box.nc ** 3,
                        "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "e2e": e2e,
