@@ -149,6 +149,36 @@ pv_status pv_grid_sync(pv_grid* g, void* stream);
    PV_ERR_DEVICE when device_flags is non-zero (out is still filled). */
 pv_status pv_grid_stats(pv_grid* g, pv_stats* out);
 
+/* No-allocation variant of pv_sort_cells + pv_density for ONE periodic box.
+   The paper has no counterpart; this exists for callers that may not
+   allocate device memory while they run: an application whose memory pool
+   owns all of the GPU's memory and forbids cudaMalloc behind its back, a
+   plugin loaded into such a host, or a latency-critical loop that cannot take
+   the device synchronisation and allocator locks of cudaMalloc/cudaFree.
+   It computes the same rho, drho_dh and n_ngb as pv_sort_cells followed by
+   pv_density on a one-box grid, with the same arguments' meaning and layout
+   (pos device double [n][3], h device float [n], m device float [n] or NULL
+   for m_uniform, outputs device float/int32 [n] in the caller's order; box
+   [0, L)^3 with nc^3 cells; gamma <= 0 selects 1.825742).  flags_out, if not
+   NULL, is a device uint32 that receives the PV_FLAG_* bits the kernels
+   latched (0 = inputs valid; outputs are not written otherwise).
+   Memory: every intermediate array lives in one fixed device array inside
+   this library (about 14 MB, sized for the limits below) that each GPU
+   loading the library keeps until the process exits; nothing is allocated
+   or freed, by this library or by any library it calls.
+   Limits: n <= PV_STATIC_MAX_PARTICLES and nc^3 <= PV_STATIC_MAX_CELLS;
+   larger inputs return PV_ERR_TOO_LARGE before any work is queued.
+   The first call on each device looks up that device's address of the array
+   (cudaGetSymbolAddress, with the device current); make that first call
+   before any stream capture.  All calls share the one array: calls whose
+   work overlaps on the GPU (other streams, other host threads) race and
+   corrupt each other's results; serialise them. */
+#define PV_STATIC_MAX_PARTICLES 65536
+#define PV_STATIC_MAX_CELLS 4096
+pv_status pv_density_static(const double* pos, const float* h, const float* m, float m_uniform,
+                            int64_t n, double L, int32_t nc, double gamma, float* rho,
+                            float* drho_dh, int32_t* n_ngb, uint32_t* flags_out, void* stream);
+
 /* Static description of a status code (never NULL). */
 const char* pv_status_str(pv_status s);
 

@@ -30,7 +30,9 @@ GAMMA = 1.825742
 #: Every symbol ``include/pv.h`` declares.
 EXPORTS = ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
            "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
-           "pv_status_str", "pv_last_cuda_error")
+           "pv_status_str", "pv_last_cuda_error", "pv_density_static")
+STATIC_MAX_PARTICLES = 65536
+STATIC_MAX_CELLS = 4096
 
 
 class PvError(RuntimeError):
@@ -86,6 +88,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         getattr(lib, name).restype = i32
     lib.pv_status_str.argtypes = [i32]
     lib.pv_status_str.restype = ctypes.c_char_p
+    lib.pv_density_static.argtypes = [vp, vp, vp, ctypes.c_float, ctypes.c_int64,
+                                      ctypes.c_double, ctypes.c_int32, ctypes.c_double, vp, vp,
+                                      vp, vp, vp]
+    lib.pv_density_static.restype = i32
     lib.pv_last_cuda_error.argtypes = []
     lib.pv_last_cuda_error.restype = ctypes.c_char_p
     _lib = lib
@@ -143,6 +149,15 @@ def pv_count_candidates(grid: int, stream: int = 0) -> None:
 
 def pv_grid_sync(grid: int, stream: int = 0) -> None:
     _check(load_library().pv_grid_sync(grid, stream), "pv_grid_sync")
+
+
+def pv_density_static(pos: int, h: int, m: int | None, m_uniform: float, n: int, L: float,
+                      nc: int, gamma: float, rho: int, drho_dh: int | None, n_ngb: int | None,
+                      flags_out: int | None = None, stream: int = 0) -> None:
+    """One box, no allocation: see the header (fixed device scratch, shared by all calls)."""
+    _check(load_library().pv_density_static(pos, h, m, ctypes.c_float(m_uniform), int(n),
+                                            float(L), int(nc), float(gamma), rho, drho_dh,
+                                            n_ngb, flags_out, stream), "pv_density_static")
 
 
 @dataclass
