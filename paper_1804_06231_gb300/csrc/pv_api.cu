@@ -136,6 +136,9 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_TRY(dev_alloc(g, &d.gacc, 5 * N));
   PV_TRY(dev_alloc(g, &d.gk, N));
   PV_TRY(dev_alloc(g, &d.ghh, N));
+  PV_TRY(dev_alloc(g, &d.plan, (size_t)pv::kNSlot * C));
+  PV_TRY(dev_alloc(g, &d.ccells, C));
+  PV_TRY(dev_alloc(g, &d.tcells, C));
   const int64_t mt = pv::max_tasks_for(n, ncell);
   if (mt > 0x7fffffffLL) return PV_ERR_TOO_LARGE;
   d.max_tasks = (int32_t)mt;
@@ -149,6 +152,9 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   d.n_big = sc + 3;
   d.ntask = sc + 4;
   d.task_next = sc + 5;
+  d.n_ccells = sc + 6;
+  d.ccell_next = sc + 7;
+  d.n_tcells = sc + 8;
   unsigned long long* cnt;
   PV_TRY(dev_alloc(g, &cnt, 4));
   d.counters = cnt;
@@ -239,10 +245,11 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
   if (!g->sorted) return PV_ERR_NOT_SORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GridDev& d = g->d;
-  PV_CUDA(cudaMemsetAsync(d.ntask, 0, 2 * sizeof(int32_t), st));  // ntask, task_next
+  // ntask, task_next, n_ccells, ccell_next, n_tcells
+  PV_CUDA(cudaMemsetAsync(d.ntask, 0, 5 * sizeof(int32_t), st));
   PV_CUDA(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned long long), st));
   PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, st));
-  g->launches += g->n > 0 ? 3 : 1;
+  g->launches += g->n > 0 ? 5 : 0;  // plan_slots, plan_cells, cells, tasks, finalize_t
   return PV_OK;
 }
 
@@ -253,9 +260,9 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
   if (!g->sorted) return PV_ERR_NOT_SORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GridDev& d = g->d;
-  PV_CUDA(cudaMemsetAsync(d.ntask, 0, 2 * sizeof(int32_t), st));
+  PV_CUDA(cudaMemsetAsync(d.ntask, 0, 5 * sizeof(int32_t), st));
   PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, st));
-  g->launches += g->n > 0 ? 4 : 0;
+  g->launches += g->n > 0 ? 5 : 0;  // prep, plan_slots, plan_cells, tasks, finalize
   return PV_OK;
 }
 

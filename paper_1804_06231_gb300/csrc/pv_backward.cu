@@ -254,7 +254,7 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   k_bwd_prep<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if ((e = launch_plan(g, 1, st)) != cudaSuccess) return e;
+  if ((e = launch_plan(g, 1, 0, 1, 1, st)) != cudaSuccess) return e;  // all cells as tasks
   k_backward_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_bwd_finalize<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);

@@ -7,18 +7,28 @@
 // in order of increasing projection, stopping once the projected distance
 // reaches its own support (Section 2 and Section 3.3).  Particles of a that
 // lie further than the cell's largest support from b are skipped ("first_a",
-// Section 3.3).  The self slot uses a two-sided window on the axis (0,0,1).
+// Section 3.3), and only the part of b that the nearest particle of a can
+// reach is loaded ("max_index_a[count_a-1]", Section 3.3).  The self slot
+// uses a two-sided window on the axis (0,0,1).
 //
-// GPU mapping (gather only, no scatter, so no atomics between particles):
-//   * a task is (cell a, slot o, block of up to 128 particles of a in the
-//     slot's order); the plan kernel enumerates them and their window in b;
-//   * one CTA (4 warps) pops tasks from a device queue; it stages the window
-//     of b in sorted order into shared memory (the particle cache of Section
-//     3.2: FP32 offsets, SoA order of the sweep) and each warp sweeps it for
-//     its 32 particles, one particle per lane;
-//   * the per-particle partial sums of a task are added to fixed-point
-//     accumulators (integer atomics, so the result is independent of the
-//     order in which tasks run), converted by the finalize kernel.
+// GPU mapping (gather only):
+//   * plan: per (cell, slot) the reachable count of a and the window of b;
+//     per cell, whether its 27 windows fit the shared-memory budget;
+//   * k_density_cells (the common case): one CTA owns a cell.  It stages the
+//     27 trimmed windows of its neighbours, in sorted order, into shared
+//     memory (the particle cache of Section 3.2), then its warps pull work
+//     items (slot, run of 32 sorted particles of a) from a shared counter.  A
+//     warp sweeps the union of its 32 windows; each lane first tests 32
+//     candidates and records the in-range ones in a bit mask, then evaluates
+//     the kernel only for those (so the spline is not executed under a mask
+//     for every candidate).  Partial sums go to per-particle fixed-point
+//     accumulators in shared memory and the CTA writes the outputs;
+//   * k_density_tasks: cells whose windows do not fit (very dense cells) are
+//     split into tasks (cell, slot, block of 128 particles of a) that stage
+//     the window of b in tiles and add to fixed-point accumulators in global
+//     memory, converted by k_finalize_t.
+// Fixed-point (2^36 units of the largest mass) integer accumulation makes the
+// result independent of which warp or CTA processed which item.
 #include <cuda_runtime.h>
 
 #include "pv_internal.cuh"
@@ -27,8 +37,15 @@ namespace pv {
 
 namespace {
 
-constexpr int kBlkI = 128;    // particles of a per task
-constexpr int kTileJ = 1024;  // particles of b per shared-memory tile
+constexpr int kBlkI = 128;       // particles of a per task (task path)
+constexpr int kTileJ = 1024;     // particles of b per tile (task path)
+constexpr int kCellThreads = 256;
+constexpr int kCellSmem = 72 * 1024;  // dynamic shared memory of k_density_cells
+constexpr int kPad = 32;         // slack after staged arrays for the 32-wide sweep
+
+// slots ordered by expected cost: self, faces, edges, corners
+__constant__ int8_t c_slot_order[kNSlot] = {13, 4,  10, 12, 14, 16, 22, 1,  3,  5,  7,  9, 11, 15,
+                                            17, 19, 21, 23, 25, 0,  2,  6,  8,  18, 20, 24, 26};
 
 struct Task {
   int a, o, p0, p1, j0, j1;
@@ -52,77 +69,119 @@ __device__ __forceinline__ float proj_asc(const GridDev& g, int k, int s, int cs
   return s * g.dist[(size_t)k * g.n + cs + order_pos(s, t, cnt)] + off;
 }
 
-// ---- plan -------------------------------------------------------------------
-// One thread per (cell a, slot o).  Counts the particles of a that can reach
-// b (first_a trimming with the cell's largest support) and, per block of
-// kBlkI of them, the window of b they can touch.  `wide` widens every window
-// to the larger of the two cells' largest supports (backward pass).
-__global__ void k_plan(GridDev g, int wide) {
+// #{t : proj_asc(t) < lim} (ascending)
+__device__ __forceinline__ int count_below(const GridDev& g, int k, int s, int cs, int cnt,
+                                           float off, float lim) {
+  int lo = 0, hi = cnt;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (proj_asc(g, k, s, cs, cnt, mid, off) < lim) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// ---- plan ------------------------------------------------------------------------
+// One thread per (cell a, slot o): the number of particles of a that can reach
+// b (first_a trimming with the cell's largest support) and the window [J0, J1)
+// of b that the nearest of them can touch.  `wide` widens every reach to the
+// larger of the two cells' largest supports (adjoint pass).
+__global__ void k_plan_slots(GridDev g, int wide) {
   if (*g.flags) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.ncell * kNSlot) return;
   const int a = idx / kNSlot, o = idx % kNSlot;
   const int na = g.cell_count[a];
-  if (na == 0) return;
-  const int b = neighbour_cell(g, a, o);
-  const int nb = g.cell_count[b];
-  if (nb == 0) return;
-  const BoxDev& B = g.boxes[g.cell_box[a]];
-  const Slot sl = slot_info(o);
-  const int ca = g.cell_start[a], cb = g.cell_start[b];
-  float reach = g.cell_Hmax[a];
-  if (wide) reach = fmaxf(reach, g.cell_Hmax[b]);
-  reach += B.pad;
-  const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
-  int nblk, nI;
-  if (o == kSelfSlot) {
-    nI = na;
-  } else {
-    // descending order along u: position p <-> ascending index na-1-p
-    const float db_min = proj_asc(g, sl.k, sl.s, cb, nb, 0, off);
-    int lo = 0, hi = na;  // nI = #{p : d(p) + reach > db_min}, d decreasing in p
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      float d = proj_asc(g, sl.k, sl.s, ca, na, na - 1 - mid, 0.0f);
-      if (d + reach > db_min) lo = mid + 1; else hi = mid;
+  int4 pl = make_int4(0, 0, 0, 0);
+  if (na > 0) {
+    const int b = neighbour_cell(g, a, o);
+    const int nb = g.cell_count[b];
+    if (nb > 0) {
+      const BoxDev& B = g.boxes[g.cell_box[a]];
+      const Slot sl = slot_info(o);
+      const int ca = g.cell_start[a], cb = g.cell_start[b];
+      float reach = g.cell_Hmax[a];
+      if (wide) reach = fmaxf(reach, g.cell_Hmax[b]);
+      reach += B.pad;
+      if (o == kSelfSlot) {
+        pl = make_int4(na, 0, nb, 0);
+      } else {
+        const float off = vnorm(sl.v2) * B.edge_f;
+        const float db_min = proj_asc(g, sl.k, sl.s, cb, nb, 0, off);
+        // descending order along u: position p <-> ascending index na-1-p
+        int lo = 0, hi = na;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          float d = proj_asc(g, sl.k, sl.s, ca, na, na - 1 - mid, 0.0f);
+          if (d + reach > db_min) lo = mid + 1; else hi = mid;
+        }
+        if (lo > 0) {
+          const float dmax = proj_asc(g, sl.k, sl.s, ca, na, na - 1, 0.0f);
+          pl = make_int4(lo, 0, count_below(g, sl.k, sl.s, cb, nb, off, dmax + reach), 0);
+        }
+      }
     }
-    nI = lo;
   }
-  if (nI == 0) return;
-  nblk = (nI + kBlkI - 1) / kBlkI;
-  const int base = atomicAdd(g.ntask, nblk);
-  if (base + nblk > g.max_tasks) {  // cannot happen with the allocated bound
-    atomicOr(g.flags, PV_FLAG_CELL_OVERFLOW);
+  g.plan[idx] = pl;
+}
+
+// One thread per cell: route the cell to the cell-centric kernel when its
+// staged windows fit `smem_budget`, else expand it into tasks of kBlkI
+// particles with their own windows.
+__global__ void k_plan_cells(GridDev g, int wide, int smem_budget, int elem_j, int elem_a) {
+  if (*g.flags) return;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= g.ncell) return;
+  const int na = g.cell_count[a];
+  if (na == 0) return;
+  const int4* pl = g.plan + (size_t)a * kNSlot;
+  int total = 0;
+  for (int o = 0; o < kNSlot; o++) total += pl[o].z - pl[o].y;
+  if (elem_j * (total + kPad) + elem_a * na <= smem_budget) {
+    g.ccells[atomicAdd(g.n_ccells, 1)] = a;
     return;
   }
-  for (int bk = 0; bk < nblk; bk++) {
-    const int p0 = bk * kBlkI, p1 = min(nI, p0 + kBlkI);
-    int j0, j1;
-    if (o == kSelfSlot) {
-      const float* d = g.dist + cb;  // axis 0, ascending
-      j0 = upper_bound_f(d, nb, d[p0] - reach);
-      j1 = lower_bound_f(d, nb, d[p1 - 1] + reach);
-    } else {
-      const float dmax = proj_asc(g, sl.k, sl.s, ca, na, na - 1 - p0, 0.0f);
-      const float lim = dmax + reach;
-      int lo = 0, hi = nb;
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (proj_asc(g, sl.k, sl.s, cb, nb, mid, off) < lim) lo = mid + 1; else hi = mid;
-      }
-      j0 = 0;
-      j1 = lo;
+  g.tcells[atomicAdd(g.n_tcells, 1)] = a;
+  const BoxDev& B = g.boxes[g.cell_box[a]];
+  const int ca = g.cell_start[a];
+  for (int o = 0; o < kNSlot; o++) {
+    const int nI = pl[o].x;
+    if (nI == 0) continue;
+    const int b = neighbour_cell(g, a, o);
+    const int nb = g.cell_count[b], cb = g.cell_start[b];
+    const Slot sl = slot_info(o);
+    float reach = g.cell_Hmax[a];
+    if (wide) reach = fmaxf(reach, g.cell_Hmax[b]);
+    reach += B.pad;
+    const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
+    const int nblk = (nI + kBlkI - 1) / kBlkI;
+    const int base = atomicAdd(g.ntask, nblk);
+    if (base + nblk > g.max_tasks) {  // cannot happen with the allocated bound
+      atomicOr(g.flags, PV_FLAG_CELL_OVERFLOW);
+      return;
     }
-    g.tasks[base + bk] = make_int4(a, o, (int)((unsigned)p0 | ((unsigned)p1 << 16)),
-                                   (int)((unsigned)j0 | ((unsigned)j1 << 16)));
+    for (int bk = 0; bk < nblk; bk++) {
+      const int p0 = bk * kBlkI, p1 = min(nI, p0 + kBlkI);
+      int j0, j1;
+      if (o == kSelfSlot) {
+        const float* d = g.dist + cb;  // axis 0, ascending
+        j0 = upper_bound_f(d, nb, d[p0] - reach);
+        j1 = lower_bound_f(d, nb, d[p1 - 1] + reach);
+      } else {
+        const float dmax = proj_asc(g, sl.k, sl.s, ca, na, na - 1 - p0, 0.0f);
+        j0 = 0;
+        j1 = count_below(g, sl.k, sl.s, cb, nb, off, dmax + reach);
+      }
+      g.tasks[base + bk] = make_int4(a, o, (int)((unsigned)p0 | ((unsigned)p1 << 16)),
+                                     (int)((unsigned)j0 | ((unsigned)j1 << 16)));
+    }
   }
 }
 
-// ---- forward sweep -------------------------------------------------------------
+// ---- the sweep ------------------------------------------------------------------
 
 struct LaneI {
   float x, y, z;           // position of i in b's frame: x'_i - o edge
-  float Hsq_hi, Hsq_lo;    // guard band around H_i^2
+  float Hsq_hi, Hsq_lo;    // guard band around H_i^2 (-1: inactive lane)
   float Hinv2;             // 1 / H_i^2
   double Hd;               // FP64 support, for the guard re-decision
   int si;                  // cell-order index of i
@@ -130,14 +189,251 @@ struct LaneI {
   int n;                   // pairs with r < H_i (j = i included)
 };
 
+__device__ __forceinline__ void lane_init(LaneI& L) {
+  L.x = L.y = L.z = 0.0f;
+  L.Hsq_hi = -1.0f; L.Hsq_lo = -1.0f; L.Hinv2 = 0.0f; L.Hd = 0.0; L.si = 0;
+  L.rho = 0.0f; L.D = 0.0f; L.n = 0;
+}
+
+__device__ __forceinline__ void lane_set(LaneI& L, const GridDev& g, const BoxDev& B,
+                                         const Slot& sl, int si, float4 xi, float h) {
+  const float H = g.gamma * h;
+  L.si = si;
+  L.x = xi.x - sl.ox * B.edge_f;
+  L.y = xi.y - sl.oy * B.edge_f;
+  L.z = xi.z - sl.oz * B.edge_f;
+  const float Hsq = H * H, gb = guard_band(H, B.edge_f);
+  L.Hsq_hi = Hsq + gb;
+  L.Hsq_lo = Hsq - gb;
+  L.Hinv2 = 1.0f / Hsq;
+  L.Hd = g.gamma_d * (double)h;
+}
+
+// Sweeps the staged particles Sx[lo, hi) for the warp's 32 particles.  Reads
+// up to Sx[hi - 1 + 31] (the staged arrays carry kPad slack).
+__device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ Sx,
+                                          const int* __restrict__ Sj, int lo, int hi,
+                                          const GridDev& g, const BoxDev& B, int& guards) {
+  for (int base = lo; base < hi; base += 32) {
+    unsigned mask = 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < 32; c0 += 8) {
+      unsigned m8 = 0;
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const float4 q = Sx[base + c0 + c];
+        const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        m8 |= (r2 < L.Hsq_hi) ? (1u << c) : 0u;
+      }
+      mask |= m8 << c0;
+    }
+    const int cnt = hi - base;
+    if (cnt < 32) mask &= (1u << cnt) - 1u;
+    while (mask) {
+      const int c = __ffs(mask) - 1;
+      mask &= mask - 1u;
+      const float4 q = Sx[base + c];
+      const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      bool in = true;
+      if (r2 >= L.Hsq_lo) {
+        in = guard_inside(g.pos64, L.si, Sj[base + c], B.L, B.inv_L, L.Hd);
+        guards++;
+      }
+      if (in) {
+        const float q2 = r2 * L.Hinv2;
+        const float qq = q2 * rsqrtf(fmaxf(q2, 1e-30f));
+        float wh, th;
+        spline_half(qq, q2, wh, th);
+        L.rho = fmaf(q.w, wh, L.rho);
+        L.D = fmaf(q.w, th, L.D);
+        L.n++;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+  for (int s = 16; s > 0; s >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, s));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+  for (int s = 16; s > 0; s >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, s));
+  return v;
+}
+
+// rho, drho/dh, n of one particle from its fixed-point sums (FP32 scaling)
+__device__ __forceinline__ void write_out(const GridDev& g, int s, long long ar, long long ad,
+                                          int an, float* rho, float* drho_dh, int32_t* n_ngb,
+                                          float mscale) {
+  const int i = g.orig[s];
+  const float h = g.hs[s];
+  const float H = g.gamma * h;
+  const float c = mscale / (H * H * H);  // (16/pi) m_max 2^-36 / H^3
+  rho[i] = c * __ll2float_rn(ar);
+  if (drho_dh) drho_dh[i] = -(c / h) * __ll2float_rn(ad);
+  if (n_ngb) n_ngb[i] = an - 1;  // the self pair j = i
+}
+
+// ---- cell-centric kernel ------------------------------------------------------------
+
+struct CellShared {
+  int I[kNSlot], J0[kNSlot];
+  int off[kNSlot + 1];      // staged segment of the q-th slot of c_slot_order
+  int runs[kNSlot + 1];     // prefix of run counts, same order
+  int nb_[kNSlot], cb_[kNSlot];
+  float offv[kNSlot];
+  int cell, item_next;
+};
+
+__global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float* __restrict__ rho,
+                                                                float* __restrict__ drho_dh,
+                                                                int32_t* __restrict__ n_ngb) {
+  extern __shared__ float4 dsm[];
+  __shared__ CellShared cs;
+  if (*g.flags) return;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ncells = *g.n_ccells;
+  const float mscale = (float)(16.0 / 3.14159265358979323846 * kFixInv) * *g.m_max;
+  int guards = 0;
+  unsigned long long inter = 0;
+  for (;;) {
+    if (tid == 0) cs.cell = atomicAdd(g.ccell_next, 1);
+    __syncthreads();
+    const int ci = cs.cell;
+    if (ci >= ncells) break;
+    const int a = g.ccells[ci];
+    const int na = g.cell_count[a], ca = g.cell_start[a];
+    const BoxDev B = g.boxes[g.cell_box[a]];
+    const int4* pl = g.plan + (size_t)a * kNSlot;
+    if (tid < kNSlot) {
+      const int o = c_slot_order[tid];
+      const int4 p = pl[o];
+      cs.I[tid] = p.x;
+      cs.J0[tid] = p.y;
+      cs.off[tid + 1] = p.z - p.y;
+      cs.runs[tid + 1] = (p.x + 31) >> 5;
+      const int b = neighbour_cell(g, a, o);
+      cs.nb_[tid] = g.cell_count[b];
+      cs.cb_[tid] = g.cell_start[b];
+      const Slot sl = slot_info(o);
+      cs.offv[tid] = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
+    }
+    if (tid == 0) {
+      cs.off[0] = 0;
+      cs.runs[0] = 0;
+      cs.item_next = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int q = 0; q < kNSlot; q++) {
+        cs.off[q + 1] += cs.off[q];
+        cs.runs[q + 1] += cs.runs[q];
+      }
+    }
+    __syncthreads();
+    const int total = cs.off[kNSlot];
+    // shared-memory carve: 24 (total + kPad) + 40 na bytes, checked by the plan
+    float4* Sx = dsm;                                          // [total + kPad]
+    float4* Ax = Sx + total + kPad;                            // [na]
+    long long* acc_r = reinterpret_cast<long long*>(Ax + na);  // [na]
+    long long* acc_d = acc_r + na;                             // [na]
+    float* Sd = reinterpret_cast<float*>(acc_d + na);          // [total + kPad]
+    int* Sj = reinterpret_cast<int*>(Sd + total + kPad);       // [total + kPad]
+    float* Ah = reinterpret_cast<float*>(Sj + total + kPad);   // [na]
+    int* acc_n = reinterpret_cast<int*>(Ah + na);              // [na]
+    // stage the 27 windows in sorted order, and cell a in cell order
+    for (int f = tid; f < total; f += kCellThreads) {
+      int q = 0;
+      while (cs.off[q + 1] <= f) q++;
+      const int o = c_slot_order[q];
+      const Slot sl = slot_info(o);
+      const int nb = cs.nb_[q], cb = cs.cb_[q];
+      const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], nb);
+      const size_t kb = (size_t)sl.k * g.n + cb + pos;
+      const int jl = g.perm[kb];
+      Sx[f] = g.xm[cb + jl];
+      Sd[f] = sl.s * g.dist[kb] + cs.offv[q];
+      Sj[f] = cb + jl;
+    }
+    for (int t = tid; t < na; t += kCellThreads) {
+      Ax[t] = g.xm[ca + t];
+      Ah[t] = g.hs[ca + t];
+      acc_r[t] = 0;
+      acc_d[t] = 0;
+      acc_n[t] = 0;
+    }
+    __syncthreads();
+    // work items: (slot, run of 32 particles of a), pulled by warps
+    const int nitems = cs.runs[kNSlot];
+    for (;;) {
+      int it = 0;
+      if (lane == 0) it = atomicAdd(&cs.item_next, 1);
+      it = __shfl_sync(0xffffffffu, it, 0);
+      if (it >= nitems) break;
+      int q = 0;
+      while (cs.runs[q + 1] <= it) q++;
+      const int o = c_slot_order[q];
+      const Slot sl = slot_info(o);
+      const int p = ((it - cs.runs[q]) << 5) + lane;
+      LaneI L;
+      lane_init(L);
+      float d_lo = 3.0e38f, d_hi = -3.0e38f;
+      int il = 0;
+      const bool valid = p < cs.I[q];
+      if (valid) {
+        const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
+        const size_t kb = (size_t)sl.k * g.n + ca + pos_i;
+        il = g.perm[kb];
+        const float di = sl.s * g.dist[kb];
+        const float h = Ah[il];
+        lane_set(L, g, B, sl, ca + il, Ax[il], h);
+        const float H = g.gamma * h;
+        d_lo = di - H - B.pad;
+        d_hi = di + H + B.pad;
+      }
+      const float w_lo = warp_min(d_lo), w_hi = warp_max(d_hi);
+      const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
+      const int lo = s0 + ((o == kSelfSlot) ? upper_bound_f(Sd + s0, len, w_lo) : 0);
+      const int hi = s0 + lower_bound_f(Sd + s0, len, w_hi);
+      sweep_fwd(L, Sx, Sj, lo, hi, g, B, guards);
+      if (valid && L.n > 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&acc_r[il]),
+                  (unsigned long long)__float2ll_rn(L.rho * (float)kFixScale));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&acc_d[il]),
+                  (unsigned long long)__float2ll_rn(L.D * (float)kFixScale));
+        atomicAdd(&acc_n[il], L.n);
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < na; t += kCellThreads) {
+      write_out(g, ca + t, acc_r[t], acc_d[t], acc_n[t], rho, drho_dh, n_ngb, mscale);
+      inter += (unsigned long long)(acc_n[t] - 1);
+    }
+    __syncthreads();
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    inter += __shfl_xor_sync(0xffffffffu, inter, s);
+    guards += __shfl_xor_sync(0xffffffffu, guards, s);
+  }
+  if (lane == 0) {
+    if (inter) atomicAdd(&g.counters[0], inter);
+    if (guards) atomicAdd(&g.counters[1], (unsigned long long)guards);
+  }
+}
+
+// ---- task kernel (cells too dense for the cell-centric kernel) ---------------------
+
 __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
-  __shared__ float4 s_x[kTileJ];
+  __shared__ float4 s_x[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
-  __shared__ int s_j[kTileJ];
+  __shared__ int s_j[kTileJ + kPad];
   __shared__ int s_task;
   if (*g.flags) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ntask = *g.ntask;
+  int guards = 0;
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(g.task_next, 1);
     __syncthreads();
@@ -153,41 +449,22 @@ __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
     const Slot sl = slot_info(o);
     const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
     const size_t kbase = (size_t)sl.k * g.n;
-
-    // lane setup
     LaneI L;
+    lane_init(L);
     const int p = tk.p0 + warp * 32 + lane;
     const bool valid = p < tk.p1;
     float d_lo = 3.0e38f, d_hi = -3.0e38f;
-    L.rho = 0.0f; L.D = 0.0f; L.n = 0;
-    L.x = L.y = L.z = 0.0f;
-    L.Hsq_hi = -1.0f; L.Hsq_lo = -1.0f; L.Hinv2 = 0.0f; L.Hd = 0.0; L.si = 0;
     if (valid) {
       const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
-      const int il = g.perm[kbase + ca + pos_i];
-      L.si = ca + il;
-      const float4 xi = g.xm[L.si];
-      const float h = g.hs[L.si];
-      const float H = g.gamma * h;
-      L.x = xi.x - sl.ox * B.edge_f;
-      L.y = xi.y - sl.oy * B.edge_f;
-      L.z = xi.z - sl.oz * B.edge_f;
-      const float Hsq = H * H, gb = guard_band(H, B.edge_f);
-      L.Hsq_hi = Hsq + gb;
-      L.Hsq_lo = Hsq - gb;
-      L.Hinv2 = 1.0f / Hsq;
-      L.Hd = g.gamma_d * (double)h;
+      const int si = ca + g.perm[kbase + ca + pos_i];
+      const float h = g.hs[si];
+      lane_set(L, g, B, sl, si, g.xm[si], h);
       const float di = sl.s * g.dist[kbase + ca + pos_i];
+      const float H = g.gamma * h;
       d_lo = di - H - B.pad;
       d_hi = di + H + B.pad;
     }
-    // window of the warp (in b's ascending order)
-    float w_lo = d_lo, w_hi = d_hi;
-    for (int s = 16; s > 0; s >>= 1) {
-      w_lo = fminf(w_lo, __shfl_xor_sync(0xffffffffu, w_lo, s));
-      w_hi = fmaxf(w_hi, __shfl_xor_sync(0xffffffffu, w_hi, s));
-    }
-    int guards = 0;
+    const float w_lo = warp_min(d_lo), w_hi = warp_max(d_hi);
     for (int j0 = tk.j0; j0 < tk.j1; j0 += kTileJ) {
       const int len = min(kTileJ, tk.j1 - j0);
       for (int e = threadIdx.x; e < len; e += blockDim.x) {
@@ -201,27 +478,7 @@ __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
       if (w_hi > w_lo) {
         const int lo = (o == kSelfSlot) ? upper_bound_f(s_d, len, w_lo) : 0;
         const int hi = lower_bound_f(s_d, len, w_hi);
-        for (int e = lo; e < hi; e++) {
-          const float4 xj = s_x[e];
-          const float dx = L.x - xj.x, dy = L.y - xj.y, dz = L.z - xj.z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (r2 < L.Hsq_hi) {
-            bool in = true;
-            if (r2 >= L.Hsq_lo) {
-              in = guard_inside(g.pos64, L.si, s_j[e], B.L, B.inv_L, L.Hd);
-              guards++;
-            }
-            if (in) {
-              const float q2 = r2 * L.Hinv2;
-              const float q = q2 * rsqrtf(fmaxf(q2, 1e-30f));
-              float wh, th;
-              spline_half(q, q2, wh, th);
-              L.rho = fmaf(xj.w, wh, L.rho);
-              L.D = fmaf(xj.w, th, L.D);
-              L.n++;
-            }
-          }
-        }
+        sweep_fwd(L, s_x, s_j, lo, hi, g, B, guards);
       }
       __syncthreads();
     }
@@ -233,34 +490,34 @@ __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
       atomicAdd(reinterpret_cast<unsigned long long*>(&g.acc[2 * (size_t)g.n + L.si]),
                 (unsigned long long)L.n);
     }
-    if (guards) atomicAdd(&g.counters[1], (unsigned long long)guards);
   }
+  for (int s = 16; s > 0; s >>= 1) guards += __shfl_xor_sync(0xffffffffu, guards, s);
+  if (lane == 0 && guards) atomicAdd(&g.counters[1], (unsigned long long)guards);
 }
 
-// ---- finalize: fixed point -> caller order ---------------------------------------
-__global__ void k_finalize(GridDev g, float* __restrict__ rho, float* __restrict__ drho_dh,
-                           int32_t* __restrict__ n_ngb) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  long long nn = 0;
-  if (s < g.n && !*g.flags) {
-    const int i = g.orig[s];
-    const double h = (double)g.hs[s];
-    const double H = g.gamma_d * h;
-    const double c = (16.0 / 3.14159265358979323846) * (double)*g.m_max / (H * H * H);
-    const double sr = (double)g.acc[s] * kFixInv;
-    const double sd = (double)g.acc[(size_t)g.n + s] * kFixInv;
-    nn = g.acc[2 * (size_t)g.n + s] - 1;  // the self pair j = i
-    rho[i] = (float)(c * sr);
-    if (drho_dh) drho_dh[i] = (float)(-c * sd / h);
-    if (n_ngb) n_ngb[i] = (int32_t)nn;
+// Fixed point -> caller order for the particles of the task-path cells.
+__global__ void k_finalize_t(GridDev g, float* __restrict__ rho, float* __restrict__ drho_dh,
+                             int32_t* __restrict__ n_ngb) {
+  if (*g.flags) return;
+  const int nt = *g.n_tcells;
+  const float mscale = (float)(16.0 / 3.14159265358979323846 * kFixInv) * *g.m_max;
+  unsigned long long inter = 0;
+  const size_t N = (size_t)g.n;
+  for (int c = blockIdx.x; c < nt; c += gridDim.x) {
+    const int a = g.tcells[c];
+    const int ca = g.cell_start[a], na = g.cell_count[a];
+    for (int t = threadIdx.x; t < na; t += blockDim.x) {
+      const int s = ca + t;
+      const long long an = g.acc[2 * N + s];
+      write_out(g, s, g.acc[s], g.acc[N + s], (int)an, rho, drho_dh, n_ngb, mscale);
+      inter += (unsigned long long)(an - 1);
+      g.acc[s] = 0;
+      g.acc[N + s] = 0;
+      g.acc[2 * N + s] = 0;
+    }
   }
-  if (s < g.n) {
-    g.acc[s] = 0;
-    g.acc[(size_t)g.n + s] = 0;
-    g.acc[2 * (size_t)g.n + s] = 0;
-  }
-  for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-  if ((threadIdx.x & 31) == 0 && nn) atomicAdd(&g.counters[0], (unsigned long long)nn);
+  for (int s = 16; s > 0; s >>= 1) inter += __shfl_xor_sync(0xffffffffu, inter, s);
+  if ((threadIdx.x & 31) == 0 && inter) atomicAdd(&g.counters[0], inter);
 }
 
 // ---- candidates of the method's windows (diagnostic) -------------------------------
@@ -290,12 +547,7 @@ __global__ void k_count_candidates(GridDev g) {
           const float* d = g.dist + cb;
           cnt += lower_bound_f(d, nb, di + H) - upper_bound_f(d, nb, di - H);
         } else {
-          int lo = 0, hi = nb;
-          while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (proj_asc(g, sl.k, sl.s, cb, nb, mid, off) < di + H) lo = mid + 1; else hi = mid;
-          }
-          cnt += lo;
+          cnt += count_below(g, sl.k, sl.s, cb, nb, off, di + H);
         }
       }
     }
@@ -306,10 +558,13 @@ __global__ void k_count_candidates(GridDev g) {
 
 }  // namespace
 
-cudaError_t launch_plan(const GridDev& g, int wide, cudaStream_t st) {
+cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
+                        cudaStream_t st) {
   const int nthr = g.ncell * kNSlot;
-  if (nthr == 0) return cudaSuccess;
-  k_plan<<<(nthr + 255) / 256, 256, 0, st>>>(g, wide);
+  k_plan_slots<<<(nthr + 255) / 256, 256, 0, st>>>(g, wide);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_plan_cells<<<(g.ncell + 127) / 128, 128, 0, st>>>(g, wide, smem_budget, elem_j, elem_a);
   return cudaGetLastError();
 }
 
@@ -319,13 +574,21 @@ int64_t max_tasks_for(int64_t n, int64_t ncell) {
 
 cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t* n_ngb,
                            int num_sms, cudaStream_t st) {
-  cudaError_t e = launch_plan(g, 0, st);
-  if (e != cudaSuccess) return e;
   if (g.n == 0) return cudaSuccess;
-  k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
-  e = cudaGetLastError();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_density_cells,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kCellSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaError_t e = launch_plan(g, 0, kCellSmem, 24, 40, st);
   if (e != cudaSuccess) return e;
-  k_finalize<<<(g.n + 255) / 256, 256, 0, st>>>(g, rho, drho_dh, n_ngb);
+  k_density_cells<<<num_sms * 3, kCellThreads, kCellSmem, st>>>(g, rho, drho_dh, n_ngb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_finalize_t<<<num_sms * 2, 256, 0, st>>>(g, rho, drho_dh, n_ngb);
   return cudaGetLastError();
 }
 

@@ -48,32 +48,37 @@ __device__ __forceinline__ double wrap_coord(double x, double L) {
 
 __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
                       const float* __restrict__ m, float m_uniform) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= g.n) return;
-  const BoxDev B = g.boxes[box_of_particle(g, p)];
-  uint32_t flags = 0;
-  int c3[3];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  float mw = 0.0f;
+  if (p < g.n) {
+    const BoxDev B = g.boxes[box_of_particle(g, p)];
+    uint32_t flags = 0;
+    int c3[3];
 #pragma unroll
-  for (int c = 0; c < 3; c++) {
-    double x = pos[3 * (size_t)p + c];
-    if (!isfinite(x)) { flags |= PV_FLAG_BAD_POSITION; x = 0.0; }
-    x = wrap_coord(x, B.L);
-    int ci = (int)floor(x / B.edge);
-    c3[c] = ci < 0 ? 0 : (ci >= B.nc ? B.nc - 1 : ci);
+    for (int c = 0; c < 3; c++) {
+      double x = pos[3 * (size_t)p + c];
+      if (!isfinite(x)) { flags |= PV_FLAG_BAD_POSITION; x = 0.0; }
+      if (!(x >= 0.0 && x < B.L)) x = wrap_coord(x, B.L);  // FP64 division only when needed
+      const int ci = (int)(x * B.inv_edge);
+      c3[c] = ci < 0 ? 0 : (ci >= B.nc ? B.nc - 1 : ci);
+    }
+    const int cell = B.cell_base + (c3[0] * B.nc + c3[1]) * B.nc + c3[2];
+    float hv = h[p];
+    const float mv = m ? m[p] : m_uniform;
+    if (!(hv > 0.0f) || !isfinite(hv) || !(mv >= 0.0f) || !isfinite(mv)) {
+      flags |= PV_FLAG_BAD_SMOOTHING;
+      hv = 0.0f;
+    }
+    if (g.gamma_d * (double)hv > B.edge) flags |= PV_FLAG_SUPPORT_EXCEEDS_CELL;
+    if (flags) atomicOr(g.flags, flags);
+    g.pcell[p] = cell;
+    g.prank[p] = atomicAdd(&g.cell_count[cell], 1);
+    atomic_max_nonneg(&g.cell_Hmax[cell], g.gamma * hv);
+    mw = (mv > 0.0f && isfinite(mv)) ? mv : 0.0f;
   }
-  int cell = B.cell_base + (c3[0] * B.nc + c3[1]) * B.nc + c3[2];
-  float hv = h[p];
-  float mv = m ? m[p] : m_uniform;
-  if (!(hv > 0.0f) || !isfinite(hv) || !(mv >= 0.0f) || !isfinite(mv)) {
-    flags |= PV_FLAG_BAD_SMOOTHING;
-    hv = 0.0f;
-  }
-  if (g.gamma_d * (double)hv > B.edge) flags |= PV_FLAG_SUPPORT_EXCEEDS_CELL;
-  if (flags) atomicOr(g.flags, flags);
-  g.pcell[p] = cell;
-  g.prank[p] = atomicAdd(&g.cell_count[cell], 1);
-  atomic_max_nonneg(&g.cell_Hmax[cell], g.gamma * hv);
-  if (mv > 0.0f) atomic_max_nonneg(g.m_max, mv);
+  // m_max is one address for all particles: reduce over the warp first
+  for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+  if ((threadIdx.x & 31) == 0 && mw > 0.0f) atomic_max_nonneg(g.m_max, mw);
 }
 
 // Single-CTA exclusive scan of the cell occupancies (C is at most a few
@@ -132,8 +137,9 @@ __global__ void k_scatter(GridDev g, const double* __restrict__ pos, const float
   for (int c = 0; c < 3; c++) {
     double x = pos[3 * (size_t)p + c];
     if (!isfinite(x)) x = 0.0;
-    xw[c] = wrap_coord(x, B.L);
-    off[c] = (float)(xw[c] - (c3[c] + 0.5) * B.edge);  // shift first, then round
+    if (!(x >= 0.0 && x < B.L)) x = wrap_coord(x, B.L);
+    xw[c] = x;
+    off[c] = (float)fma(-(c3[c] + 0.5), B.edge, x);  // shift first, then round
     g.pos64[3 * (size_t)s + c] = xw[c];
   }
   float mmax = *g.m_max;
@@ -153,50 +159,78 @@ __device__ __forceinline__ void group_sync() {
   if (kBlock) __syncthreads(); else __syncwarp();
 }
 
+// Exclusive prefix of v over the group (a warp, or the whole block when
+// kBlock; `scratch` holds one int per warp of the block).
+template <bool kBlock>
+__device__ __forceinline__ int group_exclusive_scan(int v, int rank, int* scratch) {
+  const int lane = rank & 31;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (!kBlock) return x - v;
+  const int warp = rank >> 5, nw = (int)(blockDim.x >> 5);
+  if (lane == 31) scratch[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int t = lane < nw ? scratch[lane] : 0;
+    const int t0 = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) scratch[lane] = t - t0;
+  }
+  __syncthreads();
+  const int r = x - v + scratch[warp];
+  __syncthreads();
+  return r;
+}
+
 // Sorts the cnt particles of one cell by key.  `grp` threads (a warp, or the
 // whole block when kBlock) with ranks 0..grp-1 cooperate.  Arrays:
 //   orig[cnt] (tie break), key[cnt], out[cnt] (sorted cell-local indices),
-//   bucket[B], chunk[grp] (scratch for the scan).
+//   bucket[B] (B a power of two >= grp), scratch[32] (block scan).
+// Buckets are monotone in the key, so after the counting sort only the order
+// inside a bucket remains; it is fixed by insertion on (key, caller index).
 template <bool kBlock>
 __device__ void sort_axis(int cnt, const int* orig, const float* key, int* out, int* bucket,
-                          int* chunk, int B, int rank, int grp, float kmin, float kmax) {
+                          int* scratch, int B, int rank, int grp, float kmin, float kmax) {
   const float scale = kmax > kmin ? (float)B / (kmax - kmin) : 0.0f;
   for (int b = rank; b < B; b += grp) bucket[b] = 0;
   group_sync<kBlock>();
   for (int t = rank; t < cnt; t += grp) {
-    int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
+    const int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
     atomicAdd(&bucket[b], 1);
   }
   group_sync<kBlock>();
-  // exclusive scan of bucket[0..B): contiguous chunks, then a serial pass
-  // over the chunk totals by the group (B / grp is small)
-  const int per = (B + grp - 1) / grp;
-  const int b0 = min(B, rank * per), b1 = min(B, b0 + per);
+  // exclusive scan: each rank owns B/grp consecutive buckets
+  const int per = B / grp;
+  const int b0 = rank * per;
   int sum = 0;
-  for (int b = b0; b < b1; b++) sum += bucket[b];
-  chunk[rank] = sum;
-  group_sync<kBlock>();
-  if (rank == 0) {
-    int run = 0;
-    for (int r = 0; r < grp; r++) { int v = chunk[r]; chunk[r] = run; run += v; }
+  for (int b = b0; b < b0 + per; b++) sum += bucket[b];
+  int run = group_exclusive_scan<kBlock>(sum, rank, scratch);
+  for (int b = b0; b < b0 + per; b++) {
+    const int v = bucket[b];
+    bucket[b] = run;
+    run += v;
   }
   group_sync<kBlock>();
-  int run = chunk[rank];
-  for (int b = b0; b < b1; b++) { int v = bucket[b]; bucket[b] = run; run += v; }
-  group_sync<kBlock>();
-  // scatter (order inside a bucket is fixed below)
   for (int t = rank; t < cnt; t += grp) {
-    int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
+    const int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
     out[atomicAdd(&bucket[b], 1)] = t;
   }
   group_sync<kBlock>();
   // bucket[b] is now the end of bucket b: insertion sort by (key, orig)
   for (int b = rank; b < B; b += grp) {
-    int s0 = b ? bucket[b - 1] : 0, s1 = bucket[b];
+    const int s0 = b ? bucket[b - 1] : 0, s1 = bucket[b];
     for (int i = s0 + 1; i < s1; i++) {
-      int v = out[i];
-      float kv = key[v];
-      int ov = orig[v];
+      const int v = out[i];
+      const float kv = key[v];
+      const int ov = orig[v];
       int j = i - 1;
       while (j >= s0 && key_less(kv, ov, key[out[j]], orig[out[j]])) {
         out[j + 1] = out[j];
@@ -244,7 +278,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
   }
   int B = 32;
   while (B < cnt) B <<= 1;
-  sort_axis<false>(cnt, s_orig, key, out, bkt, bkt + kSortSmallMax, B, lane, 32, kmin, kmax);
+  sort_axis<false>(cnt, s_orig, key, out, bkt, nullptr, B, lane, 32, kmin, kmax);
   const size_t base = (size_t)k * g.n + cs;
   for (int t = lane; t < cnt; t += 32) {
     int v = out[t];
@@ -255,17 +289,18 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
 
 __global__ void __launch_bounds__(1024) k_sort_big(GridDev g) {
   __shared__ float s_red[2][32];
-  __shared__ int s_chunk[1024];
+  __shared__ int s_chunk[32];
   const int nbig = *g.n_big;
   for (int idx = blockIdx.x; idx < nbig; idx += gridDim.x) {
     const int c = g.big_cells[idx];
     const int cnt = min(g.cell_count[c], PV_MAX_CELL_COUNT);
     const int cs = g.cell_start[c];
-    int B = 32;
+    int B = 1024;  // >= the block size, and >= cnt
     while (B < cnt) B <<= 1;
     float* key = g.skey + cs;
     int* out = g.sbuf + cs;
     // buckets: B <= 2 cnt slots of the cell's own range [2 cs, 2 cs + 2 cnt)
+    // (cnt > 512 and B = max(1024, next power of two >= cnt))
     int* bkt = g.sbucket + 2 * (size_t)cs;
     for (int k = 0; k < kNDir; k++) {
       float ux, uy, uz;

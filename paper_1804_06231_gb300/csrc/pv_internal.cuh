@@ -77,6 +77,13 @@ struct GridDev {
   long long* gacc;
   float4* gk;        // [N] backward: {g/H^5, k/(h H^5), H^2+guard, H^2-guard}, cell order
   float2* ghh;       // [N] backward: {1/H, H}
+  // plan: per (cell, slot) {reachable count of a, window [J0, J1) of b, 0}
+  int4* plan;        // [C][27]
+  int32_t* ccells;   // [C] cells for the cell-centric kernel
+  int32_t* n_ccells;
+  int32_t* ccell_next;
+  int32_t* tcells;   // [C] cells expanded into tasks
+  int32_t* n_tcells;
   // tasks
   int4* tasks;
   int32_t* ntask;
@@ -225,7 +232,11 @@ cudaError_t launch_scan(const GridDev& g, cudaStream_t st);
 cudaError_t launch_scatter(const GridDev& g, const double* pos, const float* h, const float* m,
                            float m_uniform, cudaStream_t st);
 cudaError_t launch_sort(const GridDev& g, cudaStream_t st);
-cudaError_t launch_plan(const GridDev& g, int wide, cudaStream_t st);
+// Per-(cell, slot) plan, then per-cell routing: cells whose staged windows fit
+// `smem_budget` bytes (elem_j bytes per staged particle, elem_a per particle
+// of the cell) go to the cell-centric kernel, the others are split into tasks.
+cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
+                        cudaStream_t st);
 int64_t max_tasks_for(int64_t n, int64_t ncell);
 cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t* n_ngb,
                            int num_sms, cudaStream_t st);

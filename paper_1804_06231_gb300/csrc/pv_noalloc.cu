@@ -34,6 +34,7 @@ constexpr size_t scratch_bytes(int64_t n, int64_t c) {
   return align_up(sizeof(pv::BoxDev)) + align_up(sizeof(int64_t)) +
          3 * align_up(C * sizeof(int32_t)) + align_up((C + 1) * sizeof(int32_t)) +
          align_up(C * sizeof(float)) +
+         align_up(pv::kNSlot * C * sizeof(int4)) + 2 * align_up(C * sizeof(int32_t)) +  // plan
          2 * align_up(N * sizeof(int32_t)) +          // pcell, prank
          align_up(N * sizeof(float4)) + align_up(N * sizeof(float)) +
          align_up(N * sizeof(int32_t)) + align_up(3 * N * sizeof(double)) +
@@ -134,6 +135,9 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.big_cells = carve<int32_t>(cur, C);
   d.cell_start = carve<int32_t>(cur, C + 1);
   d.cell_Hmax = carve<float>(cur, C);
+  d.plan = carve<int4>(cur, pv::kNSlot * C);
+  d.ccells = carve<int32_t>(cur, C);
+  d.tcells = carve<int32_t>(cur, C);
   d.pcell = carve<int32_t>(cur, N);
   d.prank = carve<int32_t>(cur, N);
   d.xm = carve<float4>(cur, N);
@@ -157,6 +161,9 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.n_big = sc + 3;
   d.ntask = sc + 4;
   d.task_next = sc + 5;
+  d.n_ccells = sc + 6;
+  d.ccell_next = sc + 7;
+  d.n_tcells = sc + 8;
   d.gacc = nullptr;
   d.gk = nullptr;
   d.ghh = nullptr;
