@@ -147,7 +147,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   int32_t* sc;
   PV_TRY(dev_alloc(g, &sc, 16));
   d.flags = reinterpret_cast<uint32_t*>(sc + 0);
-  d.m_max = reinterpret_cast<float*>(sc + 1);
+  PV_TRY(dev_alloc(g, &d.m_max, hb.size()));
   d.max_count = sc + 2;
   d.n_big = sc + 3;
   d.ntask = sc + 4;
@@ -229,7 +229,8 @@ pv_status pv_sort_cells(pv_grid* g, const double* pos, const float* h, const flo
   const size_t C = (size_t)g->ncell;
   PV_CUDA(cudaMemsetAsync(d.cell_count, 0, C * sizeof(int32_t), st));
   PV_CUDA(cudaMemsetAsync(d.cell_Hmax, 0, C * sizeof(float), st));
-  PV_CUDA(cudaMemsetAsync(d.flags, 0, 4 * sizeof(int32_t), st));  // flags, m_max, max_count, n_big
+  PV_CUDA(cudaMemsetAsync(d.flags, 0, 4 * sizeof(int32_t), st));  // flags, -, max_count, n_big
+  PV_CUDA(cudaMemsetAsync(d.m_max, 0, g->boxes.size() * sizeof(float), st));
   PV_CUDA(pv::launch_bin(d, pos, h, m, m_uniform, st));
   PV_CUDA(pv::launch_scan(d, st));
   PV_CUDA(pv::launch_scatter(d, pos, h, m, m_uniform, st));
@@ -262,7 +263,7 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
   GridDev& d = g->d;
   PV_CUDA(cudaMemsetAsync(d.ntask, 0, 5 * sizeof(int32_t), st));
   PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, st));
-  g->launches += g->n > 0 ? 5 : 0;  // prep, plan_slots, plan_cells, tasks, finalize
+  g->launches += g->n > 0 ? 6 : 0;  // prep, plan_slots, plan_cells, cells, tasks, finalize_t
   return PV_OK;
 }
 

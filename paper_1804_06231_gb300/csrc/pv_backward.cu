@@ -21,6 +21,13 @@
 // G = g/H^5 and K = k/(h H^5) per particle:
 //   dL/dx_i = (16/pi) sum_j (x_i-x_j) [ m_j (G_i vr_i - K_i vh_i) + m_i (G_j vr_j - K_j vh_j) ]
 //   dL/dh_i = (16/pi)/(h_i H_i^3) [ -g_i sum_j m_j th_i + (k_i/h_i) sum_j m_j uh_i ]
+//
+// Mapping: the cell-centric kernel of the forward pass (one CTA per cell, 27
+// staged windows, warps pulling (slot, run) items, candidates pre-filtered 64
+// at a time into a bit mask), with both the own and the transposed cut-off in
+// the pre-filter; per-particle sums in FP64 shared-memory accumulators.
+// Cells whose windows exceed the shared-memory budget run as tasks
+// (cell, slot, block of 128 particles) with FP64 global accumulators.
 #include <cuda_runtime.h>
 
 #include "pv_internal.cuh"
@@ -31,6 +38,14 @@ namespace {
 
 constexpr int kBlkI = 128;   // must match the plan kernel
 constexpr int kTileJ = 512;
+constexpr int kCellThreads = 256;
+constexpr int kCellSmem = 112 * 1024;
+constexpr int kPad = 32;
+constexpr int kElemJ = 44;   // staged bytes per particle of a window
+constexpr int kElemA = 56;   // bytes per particle of the cell
+
+__constant__ int8_t c_border[kNSlot] = {13, 4,  10, 12, 14, 16, 22, 1,  3,  5,  7,  9, 11, 15,
+                                        17, 19, 21, 23, 25, 0,  2,  6,  8,  18, 20, 24, 26};
 
 struct TaskB {
   int a, o, p0, p1, j0, j1;
@@ -58,13 +73,12 @@ __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
   const BoxDev& B = g.boxes[g.cell_box[g.pcell[i]]];
   const float h = g.hs[s];
   const float H = g.gamma * h;
-  const double Hd = (double)H;
-  const double H5 = Hd * Hd * Hd * Hd * Hd;
+  const float H2 = H * H;
+  const float iH5 = 1.0f / (H2 * H2 * H);
   const float gi = g_rho[i];
   const float ki = g_D ? g_D[i] : 0.0f;
   const float gb = guard_band(H, B.edge_f);
-  g.gk[s] = make_float4((float)((double)gi / H5), (float)((double)ki / ((double)h * H5)),
-                        H * H + gb, H * H - gb);
+  g.gk[s] = make_float4(gi * iH5, ki * iH5 / h, H2 + gb, H2 - gb);
   g.ghh[s] = make_float2(1.0f / H, H);
 }
 
@@ -98,12 +112,282 @@ __device__ __forceinline__ void spline_bwd_v(float q, float qinv, float& vr, flo
   }
 }
 
+__device__ __forceinline__ float warp_min_b(float v) {
+  for (int s = 16; s > 0; s >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, s));
+  return v;
+}
+__device__ __forceinline__ float warp_max_b(float v) {
+  for (int s = 16; s > 0; s >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, s));
+  return v;
+}
+
+struct LaneB {
+  float x, y, z;         // i in b's frame
+  float nx, ny, nz;      // -2 x_i
+  float ci, di;          // pre-filter bounds: own H_i^2+guard-|x_i|^2+margin, margin-|x_i|^2
+  float Hsq_hi, Hsq_lo, Hinv, H, G, K, m;
+  double Hd;
+  int si;
+  float Sth, Suh, gx, gy, gz;
+};
+
+__device__ __forceinline__ void laneb_init(LaneB& L) {
+  L.x = L.y = L.z = L.nx = L.ny = L.nz = 0.0f;
+  L.ci = -3.0e38f;
+  L.di = -3.0e38f;
+  L.Hsq_hi = L.Hsq_lo = -1.0f;
+  L.Hinv = L.H = L.G = L.K = L.m = 0.0f;
+  L.Hd = 0.0;
+  L.si = 0;
+  L.Sth = L.Suh = L.gx = L.gy = L.gz = 0.0f;
+}
+
+__device__ __forceinline__ void laneb_set(LaneB& L, const GridDev& g, const BoxDev& B,
+                                          const Slot& sl, int si, float4 xi) {
+  const float4 ak = g.gk[si];
+  const float2 hh = g.ghh[si];
+  L.si = si;
+  L.x = xi.x - sl.ox * B.edge_f;
+  L.y = xi.y - sl.oy * B.edge_f;
+  L.z = xi.z - sl.oz * B.edge_f;
+  L.m = xi.w;
+  L.G = ak.x; L.K = ak.y; L.Hsq_hi = ak.z; L.Hsq_lo = ak.w;
+  L.Hinv = hh.x; L.H = hh.y;
+  L.Hd = g.gamma_d * (double)g.hs[si];
+  L.nx = -2.0f * L.x;
+  L.ny = -2.0f * L.y;
+  L.nz = -2.0f * L.z;
+  // the pre-filter of the forward sweep, for both cut-offs
+  const float xi2 = fmaf(L.x, L.x, fmaf(L.y, L.y, L.z * L.z));
+  const float margin = 1.0e-5f * B.edge_f * B.edge_f;
+  L.ci = (L.Hsq_hi - xi2) + margin;
+  L.di = margin - xi2;
+}
+
+// Sx {x,y,z,|x|^2}, Se H_j^2+guard, Sa {m_j, G_j, K_j, H_j}, Sj cell-order index.
+__device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ Sx,
+                                          const float* __restrict__ Se,
+                                          const float4* __restrict__ Sa,
+                                          const int* __restrict__ Sj, int lo, int hi,
+                                          const GridDev& g, const BoxDev& B) {
+  for (int base = lo; base < hi; base += 64) {
+    unsigned long long mask = 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < 64 && base + c0 < hi; c0 += 8) {
+      unsigned m8 = 0;
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const float4 q = Sx[base + c0 + c];
+        const float t = fmaf(L.nx, q.x, fmaf(L.ny, q.y, fmaf(L.nz, q.z, q.w)));
+        const float lim = fmaxf(L.ci, L.di + Se[base + c0 + c]);
+        m8 |= (t < lim) ? (1u << c) : 0u;
+      }
+      mask |= (unsigned long long)m8 << c0;
+    }
+    const int cnt = hi - base;
+    if (cnt < 64) mask &= (1ull << cnt) - 1ull;
+    while (mask) {
+      const int c = __ffsll(mask) - 1;
+      mask &= mask - 1ull;
+      const float4 q = Sx[base + c];
+      const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const float Ej = Se[base + c];
+      bool own = r2 < L.Hsq_hi;
+      bool trans = r2 < Ej;
+      if (!(own || trans)) continue;
+      const float4 aj = Sa[base + c];  // m_j, G_j, K_j, H_j
+      if (own && r2 >= L.Hsq_lo)
+        own = guard_inside(g.pos64, L.si, Sj[base + c], B.L, B.inv_L, L.Hd);
+      if (trans && r2 >= Ej - 2.0f * guard_band(aj.w, B.edge_f))
+        trans = guard_inside(g.pos64, L.si, Sj[base + c], B.L, B.inv_L,
+                             g.gamma_d * (double)g.hs[Sj[base + c]]);
+      const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+      const float r = r2 * rinv;
+      float cc = 0.0f;
+      if (own) {
+        float th, uh, vr, vh;
+        spline_bwd(r * L.Hinv, L.H * rinv, th, uh, vr, vh);
+        L.Sth = fmaf(aj.x, th, L.Sth);
+        L.Suh = fmaf(aj.x, uh, L.Suh);
+        cc = aj.x * fmaf(L.G, vr, -L.K * vh);
+      }
+      if (trans) {
+        float vr, vh;
+        spline_bwd_v(r / aj.w, aj.w * rinv, vr, vh);
+        cc = fmaf(L.m, fmaf(aj.y, vr, -aj.z * vh), cc);
+      }
+      L.gx = fmaf(cc, dx, L.gx);
+      L.gy = fmaf(cc, dy, L.gy);
+      L.gz = fmaf(cc, dz, L.gz);
+    }
+  }
+}
+
+__device__ __forceinline__ float4 staged_b(float4 x) {
+  return make_float4(x.x, x.y, x.z, fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z)));
+}
+
+// outputs of one particle from its five sums
+__device__ __forceinline__ void write_bwd(const GridDev& g, int s, double Sth, double Suh,
+                                          double gx, double gy, double gz,
+                                          const float* __restrict__ g_rho,
+                                          const float* __restrict__ g_D, float* __restrict__ g_pos,
+                                          float* __restrict__ g_h, float mscale) {
+  const int i = g.orig[s];
+  const float h = g.hs[s];
+  const float H = g.gamma * h;
+  g_pos[3 * (size_t)i + 0] = mscale * (float)gx;
+  g_pos[3 * (size_t)i + 1] = mscale * (float)gy;
+  g_pos[3 * (size_t)i + 2] = mscale * (float)gz;
+  if (g_h) {
+    const float gi = g_rho[i];
+    const float ki = g_D ? g_D[i] : 0.0f;
+    g_h[i] = mscale / (h * H * H * H) * (float)(-(double)gi * Sth + (double)(ki / h) * Suh);
+  }
+}
+
+struct CellSharedB {
+  int I[kNSlot], J0[kNSlot];
+  int off[kNSlot + 1];
+  int runs[kNSlot + 1];
+  int nb_[kNSlot], cb_[kNSlot];
+  float offv[kNSlot], Hmaxb[kNSlot];
+  int cell, item_next;
+};
+
+__global__ void __launch_bounds__(kCellThreads) k_backward_cells(
+    GridDev g, const float* __restrict__ g_rho, const float* __restrict__ g_D,
+    float* __restrict__ g_pos, float* __restrict__ g_h) {
+  extern __shared__ float4 dsm[];
+  __shared__ CellSharedB cs;
+  if (*g.flags) return;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ncells = *g.n_ccells;
+  const float munit = (float)(16.0 / 3.14159265358979323846);
+  for (;;) {
+    if (tid == 0) cs.cell = atomicAdd(g.ccell_next, 1);
+    __syncthreads();
+    const int ci = cs.cell;
+    if (ci >= ncells) break;
+    const int a = g.ccells[ci];
+    const int na = g.cell_count[a], ca = g.cell_start[a];
+    const BoxDev B = g.boxes[g.cell_box[a]];
+    const float mscale = munit * g.m_max[g.cell_box[a]];
+    const int4* pl = g.plan + (size_t)a * kNSlot;
+    if (tid < kNSlot) {
+      const int o = c_border[tid];
+      const int4 p = pl[o];
+      cs.I[tid] = p.x;
+      cs.J0[tid] = p.y;
+      cs.off[tid + 1] = p.z - p.y;
+      cs.runs[tid + 1] = (p.x + 31) >> 5;
+      const int b = neighbour_cell(g, a, o);
+      cs.nb_[tid] = g.cell_count[b];
+      cs.cb_[tid] = g.cell_start[b];
+      cs.Hmaxb[tid] = g.cell_Hmax[b];
+      const Slot sl = slot_info(o);
+      cs.offv[tid] = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
+    }
+    if (tid == 0) {
+      cs.off[0] = 0;
+      cs.runs[0] = 0;
+      cs.item_next = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int q = 0; q < kNSlot; q++) {
+        cs.off[q + 1] += cs.off[q];
+        cs.runs[q + 1] += cs.runs[q];
+      }
+    }
+    __syncthreads();
+    const int total = cs.off[kNSlot];
+    // carve: kElemJ (total + kPad) + kElemA na bytes, checked by the plan
+    float4* Sx = dsm;                                     // [total + kPad]
+    float4* Sa = Sx + total + kPad;                       // [total + kPad]
+    float4* Ax = Sa + total + kPad;                       // [na]
+    double* acc = reinterpret_cast<double*>(Ax + na);     // [5][na]
+    float* Se = reinterpret_cast<float*>(acc + 5 * na);   // [total + kPad]
+    float* Sd = Se + total + kPad;                        // [total + kPad]
+    int* Sj = reinterpret_cast<int*>(Sd + total + kPad);  // [total + kPad]
+    for (int f = tid; f < total; f += kCellThreads) {
+      int q = 0;
+      while (cs.off[q + 1] <= f) q++;
+      const int o = c_border[q];
+      const Slot sl = slot_info(o);
+      const int nb = cs.nb_[q], cb = cs.cb_[q];
+      const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], nb);
+      const size_t kb = (size_t)sl.k * g.n + cb + pos;
+      const int sj = cb + g.perm[kb];
+      const float4 xj = g.xm[sj];
+      const float4 ak = g.gk[sj];
+      Sx[f] = staged_b(xj);
+      Se[f] = ak.z;
+      Sa[f] = make_float4(xj.w, ak.x, ak.y, g.ghh[sj].y);
+      Sd[f] = sl.s * g.dist[kb] + cs.offv[q];
+      Sj[f] = sj;
+    }
+    for (int t = tid; t < na; t += kCellThreads) {
+      Ax[t] = g.xm[ca + t];
+      for (int c = 0; c < 5; c++) acc[c * na + t] = 0.0;
+    }
+    __syncthreads();
+    const int nitems = cs.runs[kNSlot];
+    for (;;) {
+      int it = 0;
+      if (lane == 0) it = atomicAdd(&cs.item_next, 1);
+      it = __shfl_sync(0xffffffffu, it, 0);
+      if (it >= nitems) break;
+      int q = 0;
+      while (cs.runs[q + 1] <= it) q++;
+      const int o = c_border[q];
+      const Slot sl = slot_info(o);
+      const int p = ((it - cs.runs[q]) << 5) + lane;
+      LaneB L;
+      laneb_init(L);
+      float d_lo = 3.0e38f, d_hi = -3.0e38f;
+      int il = 0;
+      const bool valid = p < cs.I[q];
+      if (valid) {
+        const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
+        const size_t kb = (size_t)sl.k * g.n + ca + pos_i;
+        il = g.perm[kb];
+        laneb_set(L, g, B, sl, ca + il, Ax[il]);
+        const float di = sl.s * g.dist[kb];
+        const float reach = fmaxf(L.H, cs.Hmaxb[q]) + B.pad;
+        d_lo = di - reach;
+        d_hi = di + reach;
+      }
+      const float w_lo = warp_min_b(d_lo), w_hi = warp_max_b(d_hi);
+      const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
+      const int lo = s0 + ((o == kSelfSlot) ? upper_bound_f(Sd + s0, len, w_lo) : 0);
+      const int hi = s0 + lower_bound_f(Sd + s0, len, w_hi);
+      sweep_bwd(L, Sx, Se, Sa, Sj, lo, hi, g, B);
+      if (valid) {
+        atomicAdd(&acc[0 * na + il], (double)L.Sth);
+        atomicAdd(&acc[1 * na + il], (double)L.Suh);
+        atomicAdd(&acc[2 * na + il], (double)L.gx);
+        atomicAdd(&acc[3 * na + il], (double)L.gy);
+        atomicAdd(&acc[4 * na + il], (double)L.gz);
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < na; t += kCellThreads)
+      write_bwd(g, ca + t, acc[t], acc[na + t], acc[2 * na + t], acc[3 * na + t],
+                acc[4 * na + t], g_rho, g_D, g_pos, g_h, mscale);
+    __syncthreads();
+  }
+}
+
+// ---- task kernel (cells too dense for the cell-centric kernel) ----------------------
+
 __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
-  __shared__ float4 s_x[kTileJ];
-  __shared__ float4 s_a[kTileJ];
-  __shared__ float2 s_h[kTileJ];
+  __shared__ float4 s_x[kTileJ + kPad];
+  __shared__ float4 s_a[kTileJ + kPad];
+  __shared__ float s_e[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
-  __shared__ int s_j[kTileJ];
+  __shared__ int s_j[kTileJ + kPad];
   __shared__ int s_task;
   if (*g.flags) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -124,46 +408,31 @@ __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
     const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
     const size_t kbase = (size_t)sl.k * g.n;
     const float Hmax_b = g.cell_Hmax[b];
-
     const int p = tk.p0 + warp * 32 + lane;
     const bool valid = p < tk.p1;
-    float xi = 0.f, yi = 0.f, zi = 0.f, mi = 0.f, Gi = 0.f, Ki = 0.f;
-    float Hsq_hi = -1.f, Hsq_lo = -1.f, Hinv = 0.f, Hi = 0.f;
-    double Hd = 0.0;
-    int si = 0;
+    LaneB L;
+    laneb_init(L);
     float d_lo = 3.0e38f, d_hi = -3.0e38f;
     if (valid) {
       const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
-      si = ca + g.perm[kbase + ca + pos_i];
-      const float4 x = g.xm[si];
-      const float4 ak = g.gk[si];
-      const float2 hh = g.ghh[si];
-      xi = x.x - sl.ox * B.edge_f;
-      yi = x.y - sl.oy * B.edge_f;
-      zi = x.z - sl.oz * B.edge_f;
-      mi = x.w;
-      Gi = ak.x; Ki = ak.y; Hsq_hi = ak.z; Hsq_lo = ak.w;
-      Hinv = hh.x; Hi = hh.y;
-      Hd = g.gamma_d * (double)g.hs[si];
+      const int si = ca + g.perm[kbase + ca + pos_i];
+      laneb_set(L, g, B, sl, si, g.xm[si]);
       const float di = sl.s * g.dist[kbase + ca + pos_i];
-      const float reach = fmaxf(Hi, Hmax_b) + B.pad;
+      const float reach = fmaxf(L.H, Hmax_b) + B.pad;
       d_lo = di - reach;
       d_hi = di + reach;
     }
-    float w_lo = d_lo, w_hi = d_hi;
-    for (int s = 16; s > 0; s >>= 1) {
-      w_lo = fminf(w_lo, __shfl_xor_sync(0xffffffffu, w_lo, s));
-      w_hi = fmaxf(w_hi, __shfl_xor_sync(0xffffffffu, w_hi, s));
-    }
-    float Sth = 0.f, Suh = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    const float w_lo = warp_min_b(d_lo), w_hi = warp_max_b(d_hi);
     for (int j0 = tk.j0; j0 < tk.j1; j0 += kTileJ) {
       const int len = min(kTileJ, tk.j1 - j0);
       for (int e = threadIdx.x; e < len; e += blockDim.x) {
         const int pos_j = order_pos(sl.s, j0 + e, nb);
         const int sj = cb + g.perm[kbase + cb + pos_j];
-        s_x[e] = g.xm[sj];
-        s_a[e] = g.gk[sj];
-        s_h[e] = g.ghh[sj];
+        const float4 xj = g.xm[sj];
+        const float4 ak = g.gk[sj];
+        s_x[e] = staged_b(xj);
+        s_e[e] = ak.z;
+        s_a[e] = make_float4(xj.w, ak.x, ak.y, g.ghh[sj].y);
         s_d[e] = sl.s * g.dist[kbase + cb + pos_j] + off;
         s_j[e] = sj;
       }
@@ -171,78 +440,41 @@ __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
       if (w_hi > w_lo) {
         const int lo = (o == kSelfSlot) ? upper_bound_f(s_d, len, w_lo) : 0;
         const int hi = lower_bound_f(s_d, len, w_hi);
-        for (int e = lo; e < hi; e++) {
-          const float4 xj = s_x[e];
-          const float dx = xi - xj.x, dy = yi - xj.y, dz = zi - xj.z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float4 aj = s_a[e];
-          bool own = r2 < Hsq_hi;
-          bool trans = valid && r2 < aj.z;
-          if (own || trans) {
-            if (own && r2 >= Hsq_lo) own = guard_inside(g.pos64, si, s_j[e], B.L, B.inv_L, Hd);
-            if (trans && r2 >= aj.w)
-              trans = guard_inside(g.pos64, si, s_j[e], B.L, B.inv_L,
-                                   g.gamma_d * (double)g.hs[s_j[e]]);
-            const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-            const float r = r2 * rinv;
-            float c = 0.0f;
-            if (own) {
-              float th, uh, vr, vh;
-              spline_bwd(r * Hinv, Hi * rinv, th, uh, vr, vh);
-              Sth = fmaf(xj.w, th, Sth);
-              Suh = fmaf(xj.w, uh, Suh);
-              c = xj.w * fmaf(Gi, vr, -Ki * vh);
-            }
-            if (trans) {
-              const float2 hj = s_h[e];
-              float vr, vh;
-              spline_bwd_v(r * hj.x, hj.y * rinv, vr, vh);
-              c = fmaf(mi, fmaf(aj.x, vr, -aj.y * vh), c);
-            }
-            gx = fmaf(c, dx, gx);
-            gy = fmaf(c, dy, gy);
-            gz = fmaf(c, dz, gz);
-          }
-        }
+        sweep_bwd(L, s_x, s_e, s_a, s_j, lo, hi, g, B);
       }
       __syncthreads();
     }
     if (valid) {
       double* acc = reinterpret_cast<double*>(g.gacc);
       const size_t N = (size_t)g.n;
-      if (Sth != 0.f || Suh != 0.f) {
-        atomicAdd(&acc[si], (double)Sth);
-        atomicAdd(&acc[N + si], (double)Suh);
-      }
-      if (gx != 0.f || gy != 0.f || gz != 0.f) {
-        atomicAdd(&acc[2 * N + si], (double)gx);
-        atomicAdd(&acc[3 * N + si], (double)gy);
-        atomicAdd(&acc[4 * N + si], (double)gz);
-      }
+      atomicAdd(&acc[L.si], (double)L.Sth);
+      atomicAdd(&acc[N + L.si], (double)L.Suh);
+      atomicAdd(&acc[2 * N + L.si], (double)L.gx);
+      atomicAdd(&acc[3 * N + L.si], (double)L.gy);
+      atomicAdd(&acc[4 * N + L.si], (double)L.gz);
     }
   }
 }
 
-__global__ void k_bwd_finalize(GridDev g, const float* __restrict__ g_rho,
-                               const float* __restrict__ g_D, float* __restrict__ g_pos,
-                               float* __restrict__ g_h) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.n) return;
+__global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
+                                 const float* __restrict__ g_D, float* __restrict__ g_pos,
+                                 float* __restrict__ g_h) {
+  if (*g.flags) return;
+  const int nt = *g.n_tcells;
+  const float munit = (float)(16.0 / 3.14159265358979323846);
   double* acc = reinterpret_cast<double*>(g.gacc);
   const size_t N = (size_t)g.n;
-  if (!*g.flags) {
-    const int i = g.orig[s];
-    const double h = (double)g.hs[s];
-    const double H = g.gamma_d * h;
-    const double c = (16.0 / 3.14159265358979323846) * (double)*g.m_max;
-    const double gi = g_rho[i];
-    const double ki = g_D ? (double)g_D[i] : 0.0;
-    g_pos[3 * (size_t)i + 0] = (float)(c * acc[2 * N + s]);
-    g_pos[3 * (size_t)i + 1] = (float)(c * acc[3 * N + s]);
-    g_pos[3 * (size_t)i + 2] = (float)(c * acc[4 * N + s]);
-    if (g_h) g_h[i] = (float)(c / (h * H * H * H) * (-gi * acc[s] + (ki / h) * acc[N + s]));
+  for (int c = blockIdx.x; c < nt; c += gridDim.x) {
+    const int a = g.tcells[c];
+    const int ca = g.cell_start[a], na = g.cell_count[a];
+    const float mscale = munit * g.m_max[g.cell_box[a]];
+    for (int t = threadIdx.x; t < na; t += blockDim.x) {
+      const int s = ca + t;
+      write_bwd(g, s, acc[s], acc[N + s], acc[2 * N + s], acc[3 * N + s], acc[4 * N + s],
+                g_rho, g_D, g_pos, g_h, mscale);
+      for (int q = 0; q < 5; q++) acc[q * N + s] = 0.0;
+    }
   }
-  for (int q = 0; q < 5; q++) acc[q * N + s] = 0.0;
 }
 
 }  // namespace
@@ -250,14 +482,23 @@ __global__ void k_bwd_finalize(GridDev g, const float* __restrict__ g_rho,
 cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g_drho_dh,
                             float* g_pos, float* g_h, int num_sms, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_backward_cells,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kCellSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   const int nb = (g.n + 255) / 256;
   k_bwd_prep<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if ((e = launch_plan(g, 1, 0, 1, 1, st)) != cudaSuccess) return e;  // all cells as tasks
+  if ((e = launch_plan(g, 1, kCellSmem, kElemJ, kElemA, st)) != cudaSuccess) return e;
+  k_backward_cells<<<num_sms * 2, kCellThreads, kCellSmem, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_backward_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_bwd_finalize<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
+  k_bwd_finalize_t<<<num_sms * 2, 256, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
   return cudaGetLastError();
 }
 

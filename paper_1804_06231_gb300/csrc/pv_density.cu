@@ -181,6 +181,7 @@ __global__ void k_plan_cells(GridDev g, int wide, int smem_budget, int elem_j, i
 
 struct LaneI {
   float x, y, z;           // position of i in b's frame: x'_i - o edge
+  float nx, ny, nz, ci;    // -2 x_i and H_i^2 + guard - |x_i|^2 + margin (prefilter)
   float Hsq_hi, Hsq_lo;    // guard band around H_i^2 (-1: inactive lane)
   float Hinv2;             // 1 / H_i^2
   double Hd;               // FP64 support, for the guard re-decision
@@ -191,6 +192,8 @@ struct LaneI {
 
 __device__ __forceinline__ void lane_init(LaneI& L) {
   L.x = L.y = L.z = 0.0f;
+  L.nx = L.ny = L.nz = 0.0f;
+  L.ci = -3.0e38f;
   L.Hsq_hi = -1.0f; L.Hsq_lo = -1.0f; L.Hinv2 = 0.0f; L.Hd = 0.0; L.si = 0;
   L.rho = 0.0f; L.D = 0.0f; L.n = 0;
 }
@@ -207,51 +210,69 @@ __device__ __forceinline__ void lane_set(LaneI& L, const GridDev& g, const BoxDe
   L.Hsq_lo = Hsq - gb;
   L.Hinv2 = 1.0f / Hsq;
   L.Hd = g.gamma_d * (double)h;
+  L.nx = -2.0f * L.x;
+  L.ny = -2.0f * L.y;
+  L.nz = -2.0f * L.z;
+  // prefilter r^2 < Hsq_hi as |x_j|^2 - 2 x_i.x_j < Hsq_hi - |x_i|^2.  Its FP32
+  // rounding is below 3 ulp of (|x_i| + |x_j|)^2 <= 12 edge^2, i.e. < 5e-6 edge^2;
+  // the margin 1e-5 edge^2 keeps every in-range pair (the exact test follows).
+  const float xi2 = fmaf(L.x, L.x, fmaf(L.y, L.y, L.z * L.z));
+  L.ci = (L.Hsq_hi - xi2) + 1.0e-5f * B.edge_f * B.edge_f;
 }
 
-// Sweeps the staged particles Sx[lo, hi) for the warp's 32 particles.  Reads
-// up to Sx[hi - 1 + 31] (the staged arrays carry kPad slack).
+// Sweeps the staged particles [lo, hi) for the warp's 32 particles.  Sx holds
+// {x, y, z, |x|^2} of each staged particle, Sm its mass, Sj its cell-order
+// index.  Candidates are pre-filtered 64 at a time into a bit mask with the
+// 4-instruction test above, then the in-range ones are evaluated exactly.
+// Reads up to Sx[hi - 1 + 7] (the staged arrays carry kPad slack).
 __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ Sx,
+                                          const float* __restrict__ Sm,
                                           const int* __restrict__ Sj, int lo, int hi,
                                           const GridDev& g, const BoxDev& B, int& guards) {
-  for (int base = lo; base < hi; base += 32) {
-    unsigned mask = 0;
+  for (int base = lo; base < hi; base += 64) {
+    unsigned long long mask = 0;
 #pragma unroll 1
-    for (int c0 = 0; c0 < 32; c0 += 8) {
+    for (int c0 = 0; c0 < 64 && base + c0 < hi; c0 += 8) {
       unsigned m8 = 0;
 #pragma unroll
       for (int c = 0; c < 8; c++) {
         const float4 q = Sx[base + c0 + c];
-        const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        m8 |= (r2 < L.Hsq_hi) ? (1u << c) : 0u;
+        const float t = fmaf(L.nx, q.x, fmaf(L.ny, q.y, fmaf(L.nz, q.z, q.w)));
+        m8 |= (t < L.ci) ? (1u << c) : 0u;
       }
-      mask |= m8 << c0;
+      mask |= (unsigned long long)m8 << c0;
     }
     const int cnt = hi - base;
-    if (cnt < 32) mask &= (1u << cnt) - 1u;
+    if (cnt < 64) mask &= (1ull << cnt) - 1ull;
     while (mask) {
-      const int c = __ffs(mask) - 1;
-      mask &= mask - 1u;
+      const int c = __ffsll(mask) - 1;
+      mask &= mask - 1ull;
       const float4 q = Sx[base + c];
       const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (r2 >= L.Hsq_hi) continue;
       bool in = true;
       if (r2 >= L.Hsq_lo) {
         in = guard_inside(g.pos64, L.si, Sj[base + c], B.L, B.inv_L, L.Hd);
         guards++;
       }
       if (in) {
+        const float mj = Sm[base + c];
         const float q2 = r2 * L.Hinv2;
         const float qq = q2 * rsqrtf(fmaxf(q2, 1e-30f));
         float wh, th;
         spline_half(qq, q2, wh, th);
-        L.rho = fmaf(q.w, wh, L.rho);
-        L.D = fmaf(q.w, th, L.D);
+        L.rho = fmaf(mj, wh, L.rho);
+        L.D = fmaf(mj, th, L.D);
         L.n++;
       }
     }
   }
+}
+
+// staged form of a particle: {x, y, z, |x|^2}
+__device__ __forceinline__ float4 staged(float4 x) {
+  return make_float4(x.x, x.y, x.z, fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z)));
 }
 
 __device__ __forceinline__ float warp_min(float v) {
@@ -295,7 +316,7 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
   if (*g.flags) return;
   const int tid = threadIdx.x, lane = tid & 31;
   const int ncells = *g.n_ccells;
-  const float mscale = (float)(16.0 / 3.14159265358979323846 * kFixInv) * *g.m_max;
+  const float munit = (float)(16.0 / 3.14159265358979323846 * kFixInv);
   int guards = 0;
   unsigned long long inter = 0;
   for (;;) {
@@ -306,6 +327,7 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
     const int a = g.ccells[ci];
     const int na = g.cell_count[a], ca = g.cell_start[a];
     const BoxDev B = g.boxes[g.cell_box[a]];
+    const float mscale = munit * g.m_max[g.cell_box[a]];
     const int4* pl = g.plan + (size_t)a * kNSlot;
     if (tid < kNSlot) {
       const int o = c_slot_order[tid];
@@ -334,14 +356,15 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
     }
     __syncthreads();
     const int total = cs.off[kNSlot];
-    // shared-memory carve: 24 (total + kPad) + 40 na bytes, checked by the plan
+    // shared-memory carve: 28 (total + kPad) + 40 na bytes, checked by the plan
     float4* Sx = dsm;                                          // [total + kPad]
     float4* Ax = Sx + total + kPad;                            // [na]
     long long* acc_r = reinterpret_cast<long long*>(Ax + na);  // [na]
     long long* acc_d = acc_r + na;                             // [na]
     float* Sd = reinterpret_cast<float*>(acc_d + na);          // [total + kPad]
     int* Sj = reinterpret_cast<int*>(Sd + total + kPad);       // [total + kPad]
-    float* Ah = reinterpret_cast<float*>(Sj + total + kPad);   // [na]
+    float* Sm = reinterpret_cast<float*>(Sj + total + kPad);   // [total + kPad]
+    float* Ah = Sm + total + kPad;                             // [na]
     int* acc_n = reinterpret_cast<int*>(Ah + na);              // [na]
     // stage the 27 windows in sorted order, and cell a in cell order
     for (int f = tid; f < total; f += kCellThreads) {
@@ -353,7 +376,9 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
       const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], nb);
       const size_t kb = (size_t)sl.k * g.n + cb + pos;
       const int jl = g.perm[kb];
-      Sx[f] = g.xm[cb + jl];
+      const float4 xj = g.xm[cb + jl];
+      Sx[f] = staged(xj);
+      Sm[f] = xj.w;
       Sd[f] = sl.s * g.dist[kb] + cs.offv[q];
       Sj[f] = cb + jl;
     }
@@ -397,7 +422,7 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
       const int lo = s0 + ((o == kSelfSlot) ? upper_bound_f(Sd + s0, len, w_lo) : 0);
       const int hi = s0 + lower_bound_f(Sd + s0, len, w_hi);
-      sweep_fwd(L, Sx, Sj, lo, hi, g, B, guards);
+      sweep_fwd(L, Sx, Sm, Sj, lo, hi, g, B, guards);
       if (valid && L.n > 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&acc_r[il]),
                   (unsigned long long)__float2ll_rn(L.rho * (float)kFixScale));
@@ -427,6 +452,7 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
 
 __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
   __shared__ float4 s_x[kTileJ + kPad];
+  __shared__ float s_m[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
   __shared__ int s_j[kTileJ + kPad];
   __shared__ int s_task;
@@ -470,7 +496,9 @@ __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
       for (int e = threadIdx.x; e < len; e += blockDim.x) {
         const int pos_j = order_pos(sl.s, j0 + e, nb);
         const int jl = g.perm[kbase + cb + pos_j];
-        s_x[e] = g.xm[cb + jl];
+        const float4 xj = g.xm[cb + jl];
+        s_x[e] = staged(xj);
+        s_m[e] = xj.w;
         s_d[e] = sl.s * g.dist[kbase + cb + pos_j] + off;
         s_j[e] = cb + jl;
       }
@@ -478,7 +506,7 @@ __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
       if (w_hi > w_lo) {
         const int lo = (o == kSelfSlot) ? upper_bound_f(s_d, len, w_lo) : 0;
         const int hi = lower_bound_f(s_d, len, w_hi);
-        sweep_fwd(L, s_x, s_j, lo, hi, g, B, guards);
+        sweep_fwd(L, s_x, s_m, s_j, lo, hi, g, B, guards);
       }
       __syncthreads();
     }
@@ -500,12 +528,13 @@ __global__ void k_finalize_t(GridDev g, float* __restrict__ rho, float* __restri
                              int32_t* __restrict__ n_ngb) {
   if (*g.flags) return;
   const int nt = *g.n_tcells;
-  const float mscale = (float)(16.0 / 3.14159265358979323846 * kFixInv) * *g.m_max;
+  const float munit = (float)(16.0 / 3.14159265358979323846 * kFixInv);
   unsigned long long inter = 0;
   const size_t N = (size_t)g.n;
   for (int c = blockIdx.x; c < nt; c += gridDim.x) {
     const int a = g.tcells[c];
     const int ca = g.cell_start[a], na = g.cell_count[a];
+    const float mscale = munit * g.m_max[g.cell_box[a]];
     for (int t = threadIdx.x; t < na; t += blockDim.x) {
       const int s = ca + t;
       const long long an = g.acc[2 * N + s];
@@ -582,7 +611,7 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  cudaError_t e = launch_plan(g, 0, kCellSmem, 24, 40, st);
+  cudaError_t e = launch_plan(g, 0, kCellSmem, 28, 40, st);
   if (e != cudaSuccess) return e;
   k_density_cells<<<num_sms * 3, kCellThreads, kCellSmem, st>>>(g, rho, drho_dh, n_ngb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

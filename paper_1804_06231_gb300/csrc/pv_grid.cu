@@ -8,7 +8,7 @@
 // frame in double precision and only then converted to single precision.
 //
 // Kernels (all HBM-bound except the sort, which is shared-memory bound):
-//   k_bin      particle -> cell id, occupancy histogram, cell H_max, m_max,
+//   k_bin      particle -> cell id, occupancy histogram, cell H_max, box m_max,
 //              input checks (latched flags)
 //   k_scan     exclusive scan of the occupancies, list of big cells
 //   k_scatter  cell-order copies: FP32 offsets + normalised mass, h, caller
@@ -50,8 +50,10 @@ __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __
                       const float* __restrict__ m, float m_uniform) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   float mw = 0.0f;
+  int bx = -1;
   if (p < g.n) {
-    const BoxDev B = g.boxes[box_of_particle(g, p)];
+    bx = box_of_particle(g, p);
+    const BoxDev B = g.boxes[bx];
     uint32_t flags = 0;
     int c3[3];
 #pragma unroll
@@ -76,9 +78,15 @@ __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __
     atomic_max_nonneg(&g.cell_Hmax[cell], g.gamma * hv);
     mw = (mv > 0.0f && isfinite(mv)) ? mv : 0.0f;
   }
-  // m_max is one address for all particles: reduce over the warp first
-  for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
-  if ((threadIdx.x & 31) == 0 && mw > 0.0f) atomic_max_nonneg(g.m_max, mw);
+  // m_max of a box is one address for all its particles: reduce over the
+  // warp first when the warp lies in one box (the common case)
+  const int b0 = __shfl_sync(0xffffffffu, bx, 0);
+  if (__all_sync(0xffffffffu, bx == b0 || bx < 0)) {
+    for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+    if ((threadIdx.x & 31) == 0 && mw > 0.0f && b0 >= 0) atomic_max_nonneg(&g.m_max[b0], mw);
+  } else if (bx >= 0 && mw > 0.0f) {
+    atomic_max_nonneg(&g.m_max[bx], mw);
+  }
 }
 
 // Single-CTA exclusive scan of the cell occupancies (C is at most a few
@@ -142,7 +150,7 @@ __global__ void k_scatter(GridDev g, const double* __restrict__ pos, const float
     off[c] = (float)fma(-(c3[c] + 0.5), B.edge, x);  // shift first, then round
     g.pos64[3 * (size_t)s + c] = xw[c];
   }
-  float mmax = *g.m_max;
+  const float mmax = g.m_max[g.cell_box[cell]];
   float mv = m ? m[p] : m_uniform;
   float mn = mmax > 0.0f ? mv / mmax : 0.0f;
   g.xm[s] = make_float4(off[0], off[1], off[2], mn);

@@ -4,7 +4,7 @@
 // Layout in HBM (all particle arrays are in "cell order": the particles of a
 // cell are contiguous, cells in global cell-id order, boxes one after the
 // other):
-//   xm    float4 [N]       {x', y', z', m/m_max}: FP32 offset of the particle
+//   xm    float4 [N]       {x', y', z', m/m_max(box)}: FP32 offset of the particle
 //                          from its cell centre (Section 3.2: shift, then
 //                          convert to single precision) and normalised mass
 //   hs    float  [N]       smoothing length h (support H = gamma h)
@@ -91,7 +91,7 @@ struct GridDev {
   int32_t max_tasks;
   // scalars
   uint32_t* flags;
-  float* m_max;
+  float* m_max;     // [n_boxes] largest mass of each box (mass unit of the accumulators)
   int32_t* max_count;
   unsigned long long* counters;  // [0] interactions, [1] guard pairs, [2] candidates
 };

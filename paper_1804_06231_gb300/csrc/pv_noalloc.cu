@@ -156,7 +156,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.counters = carve<unsigned long long>(cur, 4);
   if ((size_t)(cur - static_cast<unsigned char*>(base)) > kScratchBytes) return PV_ERR_TOO_LARGE;
   d.flags = reinterpret_cast<uint32_t*>(sc + 0);
-  d.m_max = reinterpret_cast<float*>(sc + 1);
+  d.m_max = reinterpret_cast<float*>(sc + 1);  // one box
   d.max_count = sc + 2;
   d.n_big = sc + 3;
   d.ntask = sc + 4;
