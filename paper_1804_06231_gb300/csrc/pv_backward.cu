@@ -41,8 +41,8 @@ constexpr int kTileJ = 512;
 constexpr int kCellThreads = 256;
 constexpr int kCellSmem = 112 * 1024;
 constexpr int kPad = 32;
-constexpr int kElemJ = 44;   // staged bytes per particle of a window
-constexpr int kElemA = 56;   // bytes per particle of the cell
+constexpr int kElemJ = 32;   // staged bytes per particle of a window: {x,y,z,|x|^2}, {m,G,K,H}
+constexpr int kElemA = 40;   // bytes per particle of the cell: five FP64 sums
 
 __constant__ int8_t c_border[kNSlot] = {13, 4,  10, 12, 14, 16, 22, 1,  3,  5,  7,  9, 11, 15,
                                         17, 19, 21, 23, 25, 0,  2,  6,  8,  18, 20, 24, 26};
@@ -256,15 +256,48 @@ struct CellSharedB {
   int cell, item_next;
 };
 
-__global__ void __launch_bounds__(kCellThreads) k_backward_cells(
+constexpr int kCellWarps = kCellThreads / 32;
+constexpr int kQueue = 1024;
+// per warp: hit queue (2 B x 1024), run table (3 float4 + 1 double per lane),
+// round results (2 float4 per lane)
+constexpr int kCellFixedSmem = kCellWarps * (kQueue * 2 + 32 * 56 + 32 * 32);
+
+__device__ __forceinline__ float sproj(float4 x, float ux, float uy, float uz, int s, float off) {
+  return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
+}
+
+__device__ __forceinline__ int sbound(const float4* S, int len, float v, bool strict, float ux,
+                                      float uy, float uz, int s, float off) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const float d = sproj(S[mid], ux, uy, uz, s, off);
+    if (strict ? (d <= v) : (d < v)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
     GridDev g, const float* __restrict__ g_rho, const float* __restrict__ g_D,
     float* __restrict__ g_pos, float* __restrict__ g_h) {
   extern __shared__ float4 dsm[];
   __shared__ CellSharedB cs;
   if (*g.flags) return;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncells = *g.n_ccells;
   const float munit = (float)(16.0 / 3.14159265358979323846);
+  // fixed carve
+  float4* Ta = dsm + warp * 32;                       // {x, y, z, 1/H}
+  float4* Tb = dsm + (kCellWarps + warp) * 32;        // {Hsq_hi, Hsq_lo, si, H}
+  float4* Tc = dsm + (2 * kCellWarps + warp) * 32;    // {G, K, m, -}
+  double* Td = reinterpret_cast<double*>(dsm + 3 * kCellWarps * 32) + warp * 32;
+  float4* R = reinterpret_cast<float4*>(reinterpret_cast<double*>(dsm + 3 * kCellWarps * 32) +
+                                        kCellWarps * 32) + warp * 64;
+  unsigned short* Q = reinterpret_cast<unsigned short*>(
+                          reinterpret_cast<float4*>(
+                              reinterpret_cast<double*>(dsm + 3 * kCellWarps * 32) +
+                              kCellWarps * 32) + kCellWarps * 64) + warp * kQueue;
+  float4* var = dsm + kCellFixedSmem / 16;
   for (;;) {
     if (tid == 0) cs.cell = atomicAdd(g.ccell_next, 1);
     __syncthreads();
@@ -303,14 +336,10 @@ __global__ void __launch_bounds__(kCellThreads) k_backward_cells(
     }
     __syncthreads();
     const int total = cs.off[kNSlot];
-    // carve: kElemJ (total + kPad) + kElemA na bytes, checked by the plan
-    float4* Sx = dsm;                                     // [total + kPad]
-    float4* Sa = Sx + total + kPad;                       // [total + kPad]
-    float4* Ax = Sa + total + kPad;                       // [na]
-    double* acc = reinterpret_cast<double*>(Ax + na);     // [5][na]
-    float* Se = reinterpret_cast<float*>(acc + 5 * na);   // [total + kPad]
-    float* Sd = Se + total + kPad;                        // [total + kPad]
-    int* Sj = reinterpret_cast<int*>(Sd + total + kPad);  // [total + kPad]
+    // variable carve: kElemJ (total + kPad) + kElemA na bytes, checked by the plan
+    float4* Sx = var;                                  // [total + kPad] {x,y,z,|x|^2}
+    float4* Sa = Sx + total + kPad;                    // [total + kPad] {m, G, K, H}
+    double* acc = reinterpret_cast<double*>(Sa + total + kPad);  // [5][na]
     for (int f = tid; f < total; f += kCellThreads) {
       int q = 0;
       while (cs.off[q + 1] <= f) q++;
@@ -318,20 +347,13 @@ __global__ void __launch_bounds__(kCellThreads) k_backward_cells(
       const Slot sl = slot_info(o);
       const int nb = cs.nb_[q], cb = cs.cb_[q];
       const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], nb);
-      const size_t kb = (size_t)sl.k * g.n + cb + pos;
-      const int sj = cb + g.perm[kb];
+      const int sj = cb + g.perm[(size_t)sl.k * g.n + cb + pos];
       const float4 xj = g.xm[sj];
       const float4 ak = g.gk[sj];
       Sx[f] = staged_b(xj);
-      Se[f] = ak.z;
       Sa[f] = make_float4(xj.w, ak.x, ak.y, g.ghh[sj].y);
-      Sd[f] = sl.s * g.dist[kb] + cs.offv[q];
-      Sj[f] = sj;
     }
-    for (int t = tid; t < na; t += kCellThreads) {
-      Ax[t] = g.xm[ca + t];
-      for (int c = 0; c < 5; c++) acc[c * na + t] = 0.0;
-    }
+    for (int t = tid; t < 5 * na; t += kCellThreads) acc[t] = 0.0;
     __syncthreads();
     const int nitems = cs.runs[kNSlot];
     for (;;) {
@@ -343,27 +365,130 @@ __global__ void __launch_bounds__(kCellThreads) k_backward_cells(
       while (cs.runs[q + 1] <= it) q++;
       const int o = c_border[q];
       const Slot sl = slot_info(o);
+      float ux, uy, uz;
+      axis_u(sl.k, ux, uy, uz);
       const int p = ((it - cs.runs[q]) << 5) + lane;
+      const bool valid = p < cs.I[q];
       LaneB L;
       laneb_init(L);
       float d_lo = 3.0e38f, d_hi = -3.0e38f;
       int il = 0;
-      const bool valid = p < cs.I[q];
+      const float Hmb = cs.Hmaxb[q];
       if (valid) {
         const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
         const size_t kb = (size_t)sl.k * g.n + ca + pos_i;
         il = g.perm[kb];
-        laneb_set(L, g, B, sl, ca + il, Ax[il]);
+        laneb_set(L, g, B, sl, ca + il, g.xm[ca + il]);
         const float di = sl.s * g.dist[kb];
-        const float reach = fmaxf(L.H, cs.Hmaxb[q]) + B.pad;
+        const float reach = fmaxf(L.H, Hmb) + B.pad;
         d_lo = di - reach;
         d_hi = di + reach;
+        // one pre-filter bound for both cut-offs: r < max(H_i, H_max of b)
+        const float Hb = fmaxf(L.H, Hmb);
+        L.ci = fmaxf(L.ci, L.di + Hb * Hb + guard_band(Hb, B.edge_f));
       }
+      Ta[lane] = make_float4(L.x, L.y, L.z, L.Hinv);
+      Tb[lane] = make_float4(L.Hsq_hi, L.Hsq_lo, __int_as_float(L.si), L.H);
+      Tc[lane] = make_float4(L.G, L.K, L.m, 0.0f);
+      Td[lane] = L.Hd;
       const float w_lo = warp_min_b(d_lo), w_hi = warp_max_b(d_hi);
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
-      const int lo = s0 + ((o == kSelfSlot) ? upper_bound_f(Sd + s0, len, w_lo) : 0);
-      const int hi = s0 + lower_bound_f(Sd + s0, len, w_hi);
-      sweep_bwd(L, Sx, Se, Sa, Sj, lo, hi, g, B);
+      const float offv = cs.offv[q];
+      const int lo = s0 + ((o == kSelfSlot)
+                               ? sbound(Sx + s0, len, w_lo, true, ux, uy, uz, sl.s, offv)
+                               : 0);
+      const int hi = s0 + sbound(Sx + s0, len, w_hi, false, ux, uy, uz, sl.s, offv);
+      __syncwarp();
+      for (int base = lo; base < hi; base += 32) {
+        unsigned mask = 0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 32 && base + c0 < hi; c0 += 8) {
+          unsigned m8 = 0;
+#pragma unroll
+          for (int c = 0; c < 8; c++) {
+            const float4 qv = Sx[base + c0 + c];
+            const float t = fmaf(L.nx, qv.x, fmaf(L.ny, qv.y, fmaf(L.nz, qv.z, qv.w)));
+            m8 |= (t < L.ci) ? (1u << c) : 0u;
+          }
+          mask |= m8 << c0;
+        }
+        if (hi - base < 32) mask &= (1u << (hi - base)) - 1u;
+        const int cnt = __popc(mask);
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+        const int nq = __shfl_sync(0xffffffffu, incl, 31);
+        if (nq == 0) continue;
+        int w = incl - cnt;
+        for (unsigned m = mask; m; m &= m - 1u) Q[w++] = (unsigned short)((lane << 5) | (__ffs(m) - 1));
+        __syncwarp();
+        const int q0 = incl - cnt, q1 = incl;
+        for (int r0 = 0; r0 < nq; r0 += 32) {
+          const int k = r0 + lane;
+          float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          float v1 = 0.0f;
+          if (k < nq) {
+            const int e = Q[k];
+            const int src = e >> 5, c = e & 31;
+            const float4 ia = Ta[src];
+            const float4 qv = Sx[base + c];
+            const float dx = ia.x - qv.x, dy = ia.y - qv.y, dz = ia.z - qv.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float4 ib = Tb[src];
+            const float4 aj = Sa[base + c];  // m_j, G_j, K_j, H_j
+            const float gbj = guard_band(aj.w, B.edge_f);
+            const float Ej = fmaf(aj.w, aj.w, gbj);
+            bool own = r2 < ib.x;
+            bool trans = r2 < Ej;
+            if (own || trans) {
+              int sj = -1;
+              if ((own && r2 >= ib.y) || (trans && r2 >= Ej - 2.0f * gbj)) {
+                const int pos = order_pos(sl.s, cs.J0[q] + base + c - s0, cs.nb_[q]);
+                sj = cs.cb_[q] + g.perm[(size_t)sl.k * g.n + cs.cb_[q] + pos];
+              }
+              if (own && r2 >= ib.y)
+                own = guard_inside(g.pos64, __float_as_int(ib.z), sj, B.L, B.inv_L, Td[src]);
+              if (trans && r2 >= Ej - 2.0f * gbj)
+                trans = guard_inside(g.pos64, __float_as_int(ib.z), sj, B.L, B.inv_L,
+                                     g.gamma_d * (double)g.hs[sj]);
+              const float4 ic = Tc[src];
+              const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+              const float r = r2 * rinv;
+              float cc = 0.0f;
+              if (own) {
+                float th, uh, vr, vh;
+                spline_bwd(r * ia.w, ib.w * rinv, th, uh, vr, vh);
+                v0.x = aj.x * th;
+                v0.y = aj.x * uh;
+                cc = aj.x * fmaf(ic.x, vr, -ic.y * vh);
+              }
+              if (trans) {
+                float vr, vh;
+                spline_bwd_v(r / aj.w, aj.w * rinv, vr, vh);
+                cc = fmaf(ic.z, fmaf(aj.y, vr, -aj.z * vh), cc);
+              }
+              v0.z = cc * dx;
+              v0.w = cc * dy;
+              v1 = cc * dz;
+            }
+          }
+          R[lane] = v0;
+          R[32 + lane].x = v1;
+          __syncwarp();
+          for (int t = max(q0, r0) - r0, t1 = min(q1, r0 + 32) - r0; t < t1; t++) {
+            const float4 u = R[t];
+            L.Sth += u.x;
+            L.Suh += u.y;
+            L.gx += u.z;
+            L.gy += u.w;
+            L.gz += R[32 + t].x;
+          }
+          __syncwarp();
+        }
+      }
       if (valid) {
         atomicAdd(&acc[0 * na + il], (double)L.Sth);
         atomicAdd(&acc[1 * na + il], (double)L.Suh);
@@ -493,7 +618,8 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   k_bwd_prep<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if ((e = launch_plan(g, 1, kCellSmem, kElemJ, kElemA, st)) != cudaSuccess) return e;
+  if ((e = launch_plan(g, 1, kCellSmem - kCellFixedSmem, kElemJ, kElemA, st)) != cudaSuccess)
+    return e;
   k_backward_cells<<<num_sms * 2, kCellThreads, kCellSmem, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_backward_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);

@@ -40,7 +40,7 @@ namespace {
 constexpr int kBlkI = 128;       // particles of a per task (task path)
 constexpr int kTileJ = 1024;     // particles of b per tile (task path)
 constexpr int kCellThreads = 256;
-constexpr int kCellSmem = 72 * 1024;  // dynamic shared memory of k_density_cells
+constexpr int kCellSmem = 104 * 1024;  // dynamic shared memory of k_density_cells (2 per SM)
 constexpr int kPad = 32;         // slack after staged arrays for the 32-wide sweep
 
 // slots ordered by expected cost: self, faces, edges, corners
@@ -299,6 +299,14 @@ __device__ __forceinline__ void write_out(const GridDev& g, int s, long long ar,
 
 // ---- cell-centric kernel ------------------------------------------------------------
 
+constexpr int kCellWarps = kCellThreads / 32;
+constexpr int kQueue = 1024;  // entries of a warp's hit queue (32 lanes x 32 candidates)
+// per-CTA shared memory that does not depend on the cell: hit queues and the
+// per-warp table of the 32 particles of the current run
+constexpr int kCellFixedSmem = kCellWarps * (kQueue * 2 + 32 * 40 + 32 * 16);
+constexpr int kCellElemJ = 20;  // staged bytes per particle of a window: {x,y,z,|x|^2}, m
+constexpr int kCellElemA = 40;  // bytes per particle of the cell
+
 struct CellShared {
   int I[kNSlot], J0[kNSlot];
   int off[kNSlot + 1];      // staged segment of the q-th slot of c_slot_order
@@ -308,15 +316,46 @@ struct CellShared {
   int cell, item_next;
 };
 
+// projection of a staged particle in the frame of slot (k, s): the same FP32
+// expression the sort used for `dist`, so the values are bit-identical
+__device__ __forceinline__ float staged_proj(float4 x, float ux, float uy, float uz, int s,
+                                             float off) {
+  return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
+}
+
+// first e in [0, len) of the staged segment with projection >= v (> v if strict)
+__device__ __forceinline__ int staged_bound(const float4* S, int len, float v, bool strict,
+                                            float ux, float uy, float uz, int s, float off) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const float d = staged_proj(S[mid], ux, uy, uz, s, off);
+    if (strict ? (d <= v) : (d < v)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float* __restrict__ rho,
                                                                 float* __restrict__ drho_dh,
                                                                 int32_t* __restrict__ n_ngb) {
   extern __shared__ float4 dsm[];
   __shared__ CellShared cs;
   if (*g.flags) return;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncells = *g.n_ccells;
   const float munit = (float)(16.0 / 3.14159265358979323846 * kFixInv);
+  // fixed part of the carve: per-warp tables and hit queues
+  float4* Ta = dsm + (warp * 32);                                    // {x,y,z,1/H^2}
+  float4* Tb = dsm + kCellWarps * 32 + warp * 32;                    // {Hsq_hi,Hsq_lo,si,il}
+  double* Td = reinterpret_cast<double*>(dsm + 2 * kCellWarps * 32) + warp * 32;  // H (FP64)
+  float4* R = reinterpret_cast<float4*>(
+                  reinterpret_cast<double*>(dsm + 2 * kCellWarps * 32) + kCellWarps * 32) +
+              warp * 32;                                              // results of a round
+  unsigned short* Q = reinterpret_cast<unsigned short*>(
+                          reinterpret_cast<float4*>(
+                              reinterpret_cast<double*>(dsm + 2 * kCellWarps * 32) +
+                              kCellWarps * 32) + kCellWarps * 32) + warp * kQueue;
+  float4* var = dsm + kCellFixedSmem / 16;
   int guards = 0;
   unsigned long long inter = 0;
   for (;;) {
@@ -356,14 +395,12 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
     }
     __syncthreads();
     const int total = cs.off[kNSlot];
-    // shared-memory carve: 28 (total + kPad) + 40 na bytes, checked by the plan
-    float4* Sx = dsm;                                          // [total + kPad]
+    // variable part: kCellElemJ (total + kPad) + kCellElemA na bytes (checked by the plan)
+    float4* Sx = var;                                          // [total + kPad]
     float4* Ax = Sx + total + kPad;                            // [na]
     long long* acc_r = reinterpret_cast<long long*>(Ax + na);  // [na]
     long long* acc_d = acc_r + na;                             // [na]
-    float* Sd = reinterpret_cast<float*>(acc_d + na);          // [total + kPad]
-    int* Sj = reinterpret_cast<int*>(Sd + total + kPad);       // [total + kPad]
-    float* Sm = reinterpret_cast<float*>(Sj + total + kPad);   // [total + kPad]
+    float* Sm = reinterpret_cast<float*>(acc_d + na);          // [total + kPad]
     float* Ah = Sm + total + kPad;                             // [na]
     int* acc_n = reinterpret_cast<int*>(Ah + na);              // [na]
     // stage the 27 windows in sorted order, and cell a in cell order
@@ -374,13 +411,10 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
       const Slot sl = slot_info(o);
       const int nb = cs.nb_[q], cb = cs.cb_[q];
       const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], nb);
-      const size_t kb = (size_t)sl.k * g.n + cb + pos;
-      const int jl = g.perm[kb];
+      const int jl = g.perm[(size_t)sl.k * g.n + cb + pos];
       const float4 xj = g.xm[cb + jl];
       Sx[f] = staged(xj);
       Sm[f] = xj.w;
-      Sd[f] = sl.s * g.dist[kb] + cs.offv[q];
-      Sj[f] = cb + jl;
     }
     for (int t = tid; t < na; t += kCellThreads) {
       Ax[t] = g.xm[ca + t];
@@ -401,13 +435,14 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
       while (cs.runs[q + 1] <= it) q++;
       const int o = c_slot_order[q];
       const Slot sl = slot_info(o);
+      float ux, uy, uz;
+      axis_u(sl.k, ux, uy, uz);
       const int p = ((it - cs.runs[q]) << 5) + lane;
       LaneI L;
       lane_init(L);
       float d_lo = 3.0e38f, d_hi = -3.0e38f;
       int il = 0;
-      const bool valid = p < cs.I[q];
-      if (valid) {
+      if (p < cs.I[q]) {
         const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
         const size_t kb = (size_t)sl.k * g.n + ca + pos_i;
         il = g.perm[kb];
@@ -418,12 +453,89 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
         d_lo = di - H - B.pad;
         d_hi = di + H + B.pad;
       }
+      Ta[lane] = make_float4(L.x, L.y, L.z, L.Hinv2);
+      Tb[lane] = make_float4(L.Hsq_hi, L.Hsq_lo, __int_as_float(L.si), __int_as_float(il));
+      Td[lane] = L.Hd;
       const float w_lo = warp_min(d_lo), w_hi = warp_max(d_hi);
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
-      const int lo = s0 + ((o == kSelfSlot) ? upper_bound_f(Sd + s0, len, w_lo) : 0);
-      const int hi = s0 + lower_bound_f(Sd + s0, len, w_hi);
-      sweep_fwd(L, Sx, Sm, Sj, lo, hi, g, B, guards);
-      if (valid && L.n > 0) {
+      const float offv = cs.offv[q];
+      const int lo = s0 + ((o == kSelfSlot)
+                               ? staged_bound(Sx + s0, len, w_lo, true, ux, uy, uz, sl.s, offv)
+                               : 0);
+      const int hi = s0 + staged_bound(Sx + s0, len, w_hi, false, ux, uy, uz, sl.s, offv);
+      __syncwarp();
+      for (int base = lo; base < hi; base += 32) {
+        // 1. pre-filter 32 candidates into a bit mask per lane
+        unsigned mask = 0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < 32 && base + c0 < hi; c0 += 8) {
+          unsigned m8 = 0;
+#pragma unroll
+          for (int c = 0; c < 8; c++) {
+            const float4 qv = Sx[base + c0 + c];
+            const float t = fmaf(L.nx, qv.x, fmaf(L.ny, qv.y, fmaf(L.nz, qv.z, qv.w)));
+            m8 |= (t < L.ci) ? (1u << c) : 0u;
+          }
+          mask |= m8 << c0;
+        }
+        if (hi - base < 32) mask &= (1u << (hi - base)) - 1u;
+        // 2. compact the hits of the 32 lanes into the warp's queue
+        const int cnt = __popc(mask);
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += y;
+        }
+        const int nq = __shfl_sync(0xffffffffu, incl, 31);
+        if (nq == 0) continue;
+        int w = incl - cnt;
+        for (unsigned m = mask; m; m &= m - 1u) Q[w++] = (unsigned short)((lane << 5) | (__ffs(m) - 1));
+        __syncwarp();
+        // 3. evaluate the queued pairs, 32 at a time, every lane busy; each
+        //    lane then adds the results of its own entries, in queue order
+        const int q0 = incl - cnt, q1 = incl;
+        for (int r0 = 0; r0 < nq; r0 += 32) {
+          const int k = r0 + lane;
+          float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if (k < nq) {
+            const int e = Q[k];
+            const int src = e >> 5, c = e & 31;
+            const float4 ia = Ta[src];
+            const float4 qv = Sx[base + c];
+            const float dx = ia.x - qv.x, dy = ia.y - qv.y, dz = ia.z - qv.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float4 ib = Tb[src];
+            if (r2 < ib.x) {
+              bool in = true;
+              if (r2 >= ib.y) {  // within rounding of the cut-off: decide in FP64
+                const int pos = order_pos(sl.s, cs.J0[q] + base + c - s0, cs.nb_[q]);
+                const int sj = cs.cb_[q] + g.perm[(size_t)sl.k * g.n + cs.cb_[q] + pos];
+                in = guard_inside(g.pos64, __float_as_int(ib.z), sj, B.L, B.inv_L, Td[src]);
+                guards++;
+              }
+              if (in) {
+                const float q2 = r2 * ia.w;
+                const float qq = q2 * rsqrtf(fmaxf(q2, 1e-30f));
+                float wh, th;
+                spline_half(qq, q2, wh, th);
+                const float mj = Sm[base + c];
+                v = make_float4(mj * wh, mj * th, 1.0f, 0.0f);
+              }
+            }
+          }
+          R[lane] = v;
+          __syncwarp();
+          for (int t = max(q0, r0) - r0, t1 = min(q1, r0 + 32) - r0; t < t1; t++) {
+            const float4 u = R[t];
+            L.rho += u.x;
+            L.D += u.y;
+            L.n += (int)u.z;
+          }
+          __syncwarp();
+        }
+      }
+      if (p < cs.I[q] && L.n > 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&acc_r[il]),
                   (unsigned long long)__float2ll_rn(L.rho * (float)kFixScale));
         atomicAdd(reinterpret_cast<unsigned long long*>(&acc_d[il]),
@@ -611,9 +723,9 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  cudaError_t e = launch_plan(g, 0, kCellSmem, 28, 40, st);
+  cudaError_t e = launch_plan(g, 0, kCellSmem - kCellFixedSmem, kCellElemJ, kCellElemA, st);
   if (e != cudaSuccess) return e;
-  k_density_cells<<<num_sms * 3, kCellThreads, kCellSmem, st>>>(g, rho, drho_dh, n_ngb);
+  k_density_cells<<<num_sms * 2, kCellThreads, kCellSmem, st>>>(g, rho, drho_dh, n_ngb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
