@@ -39,7 +39,7 @@ namespace {
 constexpr int kBlkI = 128;   // must match the plan kernel
 constexpr int kTileJ = 512;
 constexpr int kCellThreads = 256;
-constexpr int kCellSmem = 112 * 1024;
+constexpr int kCellSmem = 100 * 1024;
 constexpr int kPad = 32;
 constexpr int kElemJ = 32;   // staged bytes per particle of a window: {x,y,z,|x|^2}, {m,G,K,H}
 constexpr int kElemA = 40;   // bytes per particle of the cell: five FP64 sums
@@ -164,44 +164,69 @@ __device__ __forceinline__ void laneb_set(LaneB& L, const GridDev& g, const BoxD
   L.di = margin - xi2;
 }
 
-// Sx {x,y,z,|x|^2}, Se H_j^2+guard, Sa {m_j, G_j, K_j, H_j}, Sj cell-order index.
+constexpr int kMaskChunks = 8;  // 32-candidate chunks per segment of the sweep
+
+// Adjoint sweep over staged particles [lo, hi): Sx {x,y,z,|x|^2}, Sa {m_j, G_j,
+// K_j, H_j}; jidx(e) gives the cell-order index of staged particle e (read
+// only for FP64 re-decisions near a cut-off).  Same two passes as the forward
+// sweep: the pre-filter bound L.ci covers r < max(H_i, H_max of the other
+// cell), then each lane walks its own hits and applies the exact own (r < H_i)
+// and transposed (r < H_j) tests.
+template <typename JIndex>
 __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ Sx,
-                                          const float* __restrict__ Se,
-                                          const float4* __restrict__ Sa,
-                                          const int* __restrict__ Sj, int lo, int hi,
-                                          const GridDev& g, const BoxDev& B) {
-  for (int base = lo; base < hi; base += 64) {
-    unsigned long long mask = 0;
+                                          const float4* __restrict__ Sa, int lo, int hi,
+                                          unsigned* __restrict__ M, int lane, const GridDev& g,
+                                          const BoxDev& B, JIndex jidx) {
+  for (int seg = lo; seg < hi; seg += 32 * kMaskChunks) {
+    const int seg_end = min(hi, seg + 32 * kMaskChunks);
+    const int nk = (seg_end - seg + 31) >> 5;
+    for (int k = 0; k < nk; k++) {
+      const int base = seg + 32 * k;
+      const int cnt = min(32, seg_end - base);
+      unsigned m = 0;
+      int c0 = 0;
 #pragma unroll 1
-    for (int c0 = 0; c0 < 64 && base + c0 < hi; c0 += 8) {
-      unsigned m8 = 0;
+      for (; c0 < cnt; c0 += 8) {
 #pragma unroll
-      for (int c = 0; c < 8; c++) {
-        const float4 q = Sx[base + c0 + c];
-        const float t = fmaf(L.nx, q.x, fmaf(L.ny, q.y, fmaf(L.nz, q.z, q.w)));
-        const float lim = fmaxf(L.ci, L.di + Se[base + c0 + c]);
-        m8 |= (t < lim) ? (1u << c) : 0u;
+        for (int c = 0; c < 8; c++) {
+          const float4 q = Sx[base + c0 + c];
+          const float d = fmaf(L.nx, q.x, fmaf(L.ny, q.y, fmaf(L.nz, q.z, q.w - L.ci)));
+          m = __funnelshift_l(__float_as_uint(d), m, 1);
+        }
       }
-      mask |= (unsigned long long)m8 << c0;
+      m <<= (32 - c0);
+      if (cnt < 32) m &= ~(0xFFFFFFFFu >> cnt);
+      M[k * 32 + lane] = m;
     }
-    const int cnt = hi - base;
-    if (cnt < 64) mask &= (1ull << cnt) - 1ull;
-    while (mask) {
-      const int c = __ffsll(mask) - 1;
-      mask &= mask - 1ull;
-      const float4 q = Sx[base + c];
+    int k = 0;
+    unsigned m = M[lane];
+    for (;;) {
+      while (m == 0u && k + 1 < nk) {
+        k++;
+        m = M[k * 32 + lane];
+      }
+      if (!__any_sync(0xffffffffu, m != 0u)) break;
+      if (m == 0u) continue;
+      const int c = __clz(m);
+      m ^= 0x80000000u >> c;
+      const int j = seg + 32 * k + c;
+      const float4 q = Sx[j];
       const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float Ej = Se[base + c];
+      const float4 aj = Sa[j];  // m_j, G_j, K_j, H_j
+      const float gbj = guard_band(aj.w, B.edge_f);
+      const float Ej = fmaf(aj.w, aj.w, gbj);
       bool own = r2 < L.Hsq_hi;
       bool trans = r2 < Ej;
       if (!(own || trans)) continue;
-      const float4 aj = Sa[base + c];  // m_j, G_j, K_j, H_j
-      if (own && r2 >= L.Hsq_lo)
-        own = guard_inside(g.pos64, L.si, Sj[base + c], B.L, B.inv_L, L.Hd);
-      if (trans && r2 >= Ej - 2.0f * guard_band(aj.w, B.edge_f))
-        trans = guard_inside(g.pos64, L.si, Sj[base + c], B.L, B.inv_L,
-                             g.gamma_d * (double)g.hs[Sj[base + c]]);
+      const bool gown = own && r2 >= L.Hsq_lo;
+      const bool gtr = trans && r2 >= Ej - 2.0f * gbj;
+      if (gown || gtr) {  // within rounding of a cut-off: decide in FP64
+        const int sj = jidx(j);
+        if (gown) own = guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, L.Hd);
+        if (gtr)
+          trans = guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, g.gamma_d * (double)g.hs[sj]);
+      }
       const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
       const float r = r2 * rinv;
       float cc = 0.0f;
@@ -257,10 +282,7 @@ struct CellSharedB {
 };
 
 constexpr int kCellWarps = kCellThreads / 32;
-constexpr int kQueue = 1024;
-// per warp: hit queue (2 B x 1024), run table (3 float4 + 1 double per lane),
-// round results (2 float4 per lane)
-constexpr int kCellFixedSmem = kCellWarps * (kQueue * 2 + 32 * 56 + 32 * 32);
+constexpr int kCellFixedSmem = kCellWarps * kMaskChunks * 32 * 4;  // the warps' hit masks
 
 __device__ __forceinline__ float sproj(float4 x, float ux, float uy, float uz, int s, float off) {
   return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
@@ -286,17 +308,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncells = *g.n_ccells;
   const float munit = (float)(16.0 / 3.14159265358979323846);
-  // fixed carve
-  float4* Ta = dsm + warp * 32;                       // {x, y, z, 1/H}
-  float4* Tb = dsm + (kCellWarps + warp) * 32;        // {Hsq_hi, Hsq_lo, si, H}
-  float4* Tc = dsm + (2 * kCellWarps + warp) * 32;    // {G, K, m, -}
-  double* Td = reinterpret_cast<double*>(dsm + 3 * kCellWarps * 32) + warp * 32;
-  float4* R = reinterpret_cast<float4*>(reinterpret_cast<double*>(dsm + 3 * kCellWarps * 32) +
-                                        kCellWarps * 32) + warp * 64;
-  unsigned short* Q = reinterpret_cast<unsigned short*>(
-                          reinterpret_cast<float4*>(
-                              reinterpret_cast<double*>(dsm + 3 * kCellWarps * 32) +
-                              kCellWarps * 32) + kCellWarps * 64) + warp * kQueue;
+  unsigned* Mw = reinterpret_cast<unsigned*>(dsm) + warp * kMaskChunks * 32;
   float4* var = dsm + kCellFixedSmem / 16;
   for (;;) {
     if (tid == 0) cs.cell = atomicAdd(g.ccell_next, 1);
@@ -387,10 +399,6 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
         const float Hb = fmaxf(L.H, Hmb);
         L.ci = fmaxf(L.ci, L.di + Hb * Hb + guard_band(Hb, B.edge_f));
       }
-      Ta[lane] = make_float4(L.x, L.y, L.z, L.Hinv);
-      Tb[lane] = make_float4(L.Hsq_hi, L.Hsq_lo, __int_as_float(L.si), L.H);
-      Tc[lane] = make_float4(L.G, L.K, L.m, 0.0f);
-      Td[lane] = L.Hd;
       const float w_lo = warp_min_b(d_lo), w_hi = warp_max_b(d_hi);
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
       const float offv = cs.offv[q];
@@ -398,97 +406,12 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
                                ? sbound(Sx + s0, len, w_lo, true, ux, uy, uz, sl.s, offv)
                                : 0);
       const int hi = s0 + sbound(Sx + s0, len, w_hi, false, ux, uy, uz, sl.s, offv);
-      __syncwarp();
-      for (int base = lo; base < hi; base += 32) {
-        unsigned mask = 0;
-#pragma unroll 1
-        for (int c0 = 0; c0 < 32 && base + c0 < hi; c0 += 8) {
-          unsigned m8 = 0;
-#pragma unroll
-          for (int c = 0; c < 8; c++) {
-            const float4 qv = Sx[base + c0 + c];
-            const float t = fmaf(L.nx, qv.x, fmaf(L.ny, qv.y, fmaf(L.nz, qv.z, qv.w)));
-            m8 |= (t < L.ci) ? (1u << c) : 0u;
-          }
-          mask |= m8 << c0;
-        }
-        if (hi - base < 32) mask &= (1u << (hi - base)) - 1u;
-        const int cnt = __popc(mask);
-        int incl = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, d);
-          if (lane >= d) incl += y;
-        }
-        const int nq = __shfl_sync(0xffffffffu, incl, 31);
-        if (nq == 0) continue;
-        int w = incl - cnt;
-        for (unsigned m = mask; m; m &= m - 1u) Q[w++] = (unsigned short)((lane << 5) | (__ffs(m) - 1));
-        __syncwarp();
-        const int q0 = incl - cnt, q1 = incl;
-        for (int r0 = 0; r0 < nq; r0 += 32) {
-          const int k = r0 + lane;
-          float4 v0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          float v1 = 0.0f;
-          if (k < nq) {
-            const int e = Q[k];
-            const int src = e >> 5, c = e & 31;
-            const float4 ia = Ta[src];
-            const float4 qv = Sx[base + c];
-            const float dx = ia.x - qv.x, dy = ia.y - qv.y, dz = ia.z - qv.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float4 ib = Tb[src];
-            const float4 aj = Sa[base + c];  // m_j, G_j, K_j, H_j
-            const float gbj = guard_band(aj.w, B.edge_f);
-            const float Ej = fmaf(aj.w, aj.w, gbj);
-            bool own = r2 < ib.x;
-            bool trans = r2 < Ej;
-            if (own || trans) {
-              int sj = -1;
-              if ((own && r2 >= ib.y) || (trans && r2 >= Ej - 2.0f * gbj)) {
-                const int pos = order_pos(sl.s, cs.J0[q] + base + c - s0, cs.nb_[q]);
-                sj = cs.cb_[q] + g.perm[(size_t)sl.k * g.n + cs.cb_[q] + pos];
-              }
-              if (own && r2 >= ib.y)
-                own = guard_inside(g.pos64, __float_as_int(ib.z), sj, B.L, B.inv_L, Td[src]);
-              if (trans && r2 >= Ej - 2.0f * gbj)
-                trans = guard_inside(g.pos64, __float_as_int(ib.z), sj, B.L, B.inv_L,
-                                     g.gamma_d * (double)g.hs[sj]);
-              const float4 ic = Tc[src];
-              const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-              const float r = r2 * rinv;
-              float cc = 0.0f;
-              if (own) {
-                float th, uh, vr, vh;
-                spline_bwd(r * ia.w, ib.w * rinv, th, uh, vr, vh);
-                v0.x = aj.x * th;
-                v0.y = aj.x * uh;
-                cc = aj.x * fmaf(ic.x, vr, -ic.y * vh);
-              }
-              if (trans) {
-                float vr, vh;
-                spline_bwd_v(r / aj.w, aj.w * rinv, vr, vh);
-                cc = fmaf(ic.z, fmaf(aj.y, vr, -aj.z * vh), cc);
-              }
-              v0.z = cc * dx;
-              v0.w = cc * dy;
-              v1 = cc * dz;
-            }
-          }
-          R[lane] = v0;
-          R[32 + lane].x = v1;
-          __syncwarp();
-          for (int t = max(q0, r0) - r0, t1 = min(q1, r0 + 32) - r0; t < t1; t++) {
-            const float4 u = R[t];
-            L.Sth += u.x;
-            L.Suh += u.y;
-            L.gx += u.z;
-            L.gy += u.w;
-            L.gz += R[32 + t].x;
-          }
-          __syncwarp();
-        }
-      }
+      const int J0q = cs.J0[q], nbq = cs.nb_[q], cbq = cs.cb_[q];
+      const size_t kbq = (size_t)sl.k * g.n + cbq;
+      auto jidx = [&](int j) {
+        return cbq + (int)g.perm[kbq + order_pos(sl.s, J0q + j - s0, nbq)];
+      };
+      sweep_bwd(L, Sx, Sa, lo, hi, Mw, lane, g, B, jidx);
       if (valid) {
         atomicAdd(&acc[0 * na + il], (double)L.Sth);
         atomicAdd(&acc[1 * na + il], (double)L.Suh);
@@ -510,9 +433,9 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
 __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
   __shared__ float4 s_x[kTileJ + kPad];
   __shared__ float4 s_a[kTileJ + kPad];
-  __shared__ float s_e[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
   __shared__ int s_j[kTileJ + kPad];
+  __shared__ unsigned s_mask[kBlkI / 32][kMaskChunks * 32];
   __shared__ int s_task;
   if (*g.flags) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -546,6 +469,8 @@ __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
       const float reach = fmaxf(L.H, Hmax_b) + B.pad;
       d_lo = di - reach;
       d_hi = di + reach;
+      const float Hb = fmaxf(L.H, Hmax_b);
+      L.ci = fmaxf(L.ci, L.di + Hb * Hb + guard_band(Hb, B.edge_f));
     }
     const float w_lo = warp_min_b(d_lo), w_hi = warp_max_b(d_hi);
     for (int j0 = tk.j0; j0 < tk.j1; j0 += kTileJ) {
@@ -556,7 +481,6 @@ __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
         const float4 xj = g.xm[sj];
         const float4 ak = g.gk[sj];
         s_x[e] = staged_b(xj);
-        s_e[e] = ak.z;
         s_a[e] = make_float4(xj.w, ak.x, ak.y, g.ghh[sj].y);
         s_d[e] = sl.s * g.dist[kbase + cb + pos_j] + off;
         s_j[e] = sj;
@@ -565,7 +489,8 @@ __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
       if (w_hi > w_lo) {
         const int lo = (o == kSelfSlot) ? upper_bound_f(s_d, len, w_lo) : 0;
         const int hi = lower_bound_f(s_d, len, w_hi);
-        sweep_bwd(L, s_x, s_e, s_a, s_j, lo, hi, g, B);
+        auto jidx = [&](int j) { return s_j[j]; };
+        sweep_bwd(L, s_x, s_a, lo, hi, s_mask[warp], lane, g, B, jidx);
       }
       __syncthreads();
     }

@@ -40,7 +40,7 @@ namespace {
 constexpr int kBlkI = 128;       // particles of a per task (task path)
 constexpr int kTileJ = 1024;     // particles of b per tile (task path)
 constexpr int kCellThreads = 256;
-constexpr int kCellSmem = 104 * 1024;  // dynamic shared memory of k_density_cells (2 per SM)
+constexpr int kCellSmem = 72 * 1024;  // dynamic shared memory of k_density_cells (3 per SM)
 constexpr int kPad = 32;         // slack after staged arrays for the 32-wide sweep
 
 // slots ordered by expected cost: self, faces, edges, corners
@@ -220,48 +220,71 @@ __device__ __forceinline__ void lane_set(LaneI& L, const GridDev& g, const BoxDe
   L.ci = (L.Hsq_hi - xi2) + 1.0e-5f * B.edge_f * B.edge_f;
 }
 
+constexpr int kMaskChunks = 8;  // 32-candidate chunks per segment of the sweep
+
 // Sweeps the staged particles [lo, hi) for the warp's 32 particles.  Sx holds
-// {x, y, z, |x|^2} of each staged particle, Sm its mass, Sj its cell-order
-// index.  Candidates are pre-filtered 64 at a time into a bit mask with the
-// 4-instruction test above, then the in-range ones are evaluated exactly.
+// {x, y, z, |x|^2} of each staged particle and Sm its mass; jidx(e) returns the
+// cell-order index of staged particle e (read only for the rare FP64
+// re-decisions near the cut-off).  M is the warp's [kMaskChunks][32] scratch.
+//
+// Pass 1 pre-filters every candidate of a segment of up to 8 x 32 with four
+// FP32 instructions, |x_j|^2 - 2 x_i.x_j - (H_i^2 + guard - |x_i|^2 + margin),
+// whose sign bit is shifted into a 32-bit hit mask per chunk.  Pass 2 lets
+// each lane walk its own hits across the whole segment, so a pass costs the
+// largest number of hits of a lane, not the sum of per-chunk maxima.
 // Reads up to Sx[hi - 1 + 7] (the staged arrays carry kPad slack).
+template <typename JIndex>
 __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ Sx,
-                                          const float* __restrict__ Sm,
-                                          const int* __restrict__ Sj, int lo, int hi,
-                                          const GridDev& g, const BoxDev& B, int& guards) {
-  for (int base = lo; base < hi; base += 64) {
-    unsigned long long mask = 0;
+                                          const float* __restrict__ Sm, int lo, int hi,
+                                          unsigned* __restrict__ M, int lane, const GridDev& g,
+                                          const BoxDev& B, JIndex jidx, int& guards) {
+  for (int seg = lo; seg < hi; seg += 32 * kMaskChunks) {
+    const int seg_end = min(hi, seg + 32 * kMaskChunks);
+    const int nk = (seg_end - seg + 31) >> 5;
+    for (int k = 0; k < nk; k++) {
+      const int base = seg + 32 * k;
+      const int cnt = min(32, seg_end - base);
+      unsigned m = 0;
+      int c0 = 0;
 #pragma unroll 1
-    for (int c0 = 0; c0 < 64 && base + c0 < hi; c0 += 8) {
-      unsigned m8 = 0;
+      for (; c0 < cnt; c0 += 8) {
 #pragma unroll
-      for (int c = 0; c < 8; c++) {
-        const float4 q = Sx[base + c0 + c];
-        const float t = fmaf(L.nx, q.x, fmaf(L.ny, q.y, fmaf(L.nz, q.z, q.w)));
-        m8 |= (t < L.ci) ? (1u << c) : 0u;
+        for (int c = 0; c < 8; c++) {
+          const float4 q = Sx[base + c0 + c];
+          const float d = fmaf(L.nx, q.x, fmaf(L.ny, q.y, fmaf(L.nz, q.z, q.w - L.ci)));
+          m = __funnelshift_l(__float_as_uint(d), m, 1);  // sign bit: hit
+        }
       }
-      mask |= (unsigned long long)m8 << c0;
+      m <<= (32 - c0);                                   // candidate c at bit 31 - c
+      if (cnt < 32) m &= ~(0xFFFFFFFFu >> cnt);
+      M[k * 32 + lane] = m;
     }
-    const int cnt = hi - base;
-    if (cnt < 64) mask &= (1ull << cnt) - 1ull;
-    while (mask) {
-      const int c = __ffsll(mask) - 1;
-      mask &= mask - 1ull;
-      const float4 q = Sx[base + c];
+    int k = 0;
+    unsigned m = M[lane];
+    for (;;) {
+      while (m == 0u && k + 1 < nk) {
+        k++;
+        m = M[k * 32 + lane];
+      }
+      if (!__any_sync(0xffffffffu, m != 0u)) break;
+      if (m == 0u) continue;
+      const int c = __clz(m);
+      m ^= 0x80000000u >> c;
+      const int j = seg + 32 * k + c;
+      const float4 q = Sx[j];
       const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      if (r2 >= L.Hsq_hi) continue;
-      bool in = true;
-      if (r2 >= L.Hsq_lo) {
-        in = guard_inside(g.pos64, L.si, Sj[base + c], B.L, B.inv_L, L.Hd);
+      bool in = r2 < L.Hsq_lo;
+      if (!in && r2 < L.Hsq_hi) {  // within rounding of the cut-off: decide in FP64
+        in = guard_inside(g.pos64, L.si, jidx(j), B.L, B.inv_L, L.Hd);
         guards++;
       }
       if (in) {
-        const float mj = Sm[base + c];
         const float q2 = r2 * L.Hinv2;
         const float qq = q2 * rsqrtf(fmaxf(q2, 1e-30f));
         float wh, th;
-        spline_half(qq, q2, wh, th);
+        spline_half(qq, wh, th);
+        const float mj = Sm[j];
         L.rho = fmaf(mj, wh, L.rho);
         L.D = fmaf(mj, th, L.D);
         L.n++;
@@ -300,10 +323,8 @@ __device__ __forceinline__ void write_out(const GridDev& g, int s, long long ar,
 // ---- cell-centric kernel ------------------------------------------------------------
 
 constexpr int kCellWarps = kCellThreads / 32;
-constexpr int kQueue = 1024;  // entries of a warp's hit queue (32 lanes x 32 candidates)
-// per-CTA shared memory that does not depend on the cell: hit queues and the
-// per-warp table of the 32 particles of the current run
-constexpr int kCellFixedSmem = kCellWarps * (kQueue * 2 + 32 * 40 + 32 * 16);
+// per-CTA shared memory that does not depend on the cell: the warps' hit masks
+constexpr int kCellFixedSmem = kCellWarps * kMaskChunks * 32 * 4;
 constexpr int kCellElemJ = 20;  // staged bytes per particle of a window: {x,y,z,|x|^2}, m
 constexpr int kCellElemA = 40;  // bytes per particle of the cell
 
@@ -344,17 +365,7 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncells = *g.n_ccells;
   const float munit = (float)(16.0 / 3.14159265358979323846 * kFixInv);
-  // fixed part of the carve: per-warp tables and hit queues
-  float4* Ta = dsm + (warp * 32);                                    // {x,y,z,1/H^2}
-  float4* Tb = dsm + kCellWarps * 32 + warp * 32;                    // {Hsq_hi,Hsq_lo,si,il}
-  double* Td = reinterpret_cast<double*>(dsm + 2 * kCellWarps * 32) + warp * 32;  // H (FP64)
-  float4* R = reinterpret_cast<float4*>(
-                  reinterpret_cast<double*>(dsm + 2 * kCellWarps * 32) + kCellWarps * 32) +
-              warp * 32;                                              // results of a round
-  unsigned short* Q = reinterpret_cast<unsigned short*>(
-                          reinterpret_cast<float4*>(
-                              reinterpret_cast<double*>(dsm + 2 * kCellWarps * 32) +
-                              kCellWarps * 32) + kCellWarps * 32) + warp * kQueue;
+  unsigned* Mw = reinterpret_cast<unsigned*>(dsm) + warp * kMaskChunks * 32;
   float4* var = dsm + kCellFixedSmem / 16;
   int guards = 0;
   unsigned long long inter = 0;
@@ -453,9 +464,6 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
         d_lo = di - H - B.pad;
         d_hi = di + H + B.pad;
       }
-      Ta[lane] = make_float4(L.x, L.y, L.z, L.Hinv2);
-      Tb[lane] = make_float4(L.Hsq_hi, L.Hsq_lo, __int_as_float(L.si), __int_as_float(il));
-      Td[lane] = L.Hd;
       const float w_lo = warp_min(d_lo), w_hi = warp_max(d_hi);
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
       const float offv = cs.offv[q];
@@ -463,78 +471,12 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
                                ? staged_bound(Sx + s0, len, w_lo, true, ux, uy, uz, sl.s, offv)
                                : 0);
       const int hi = s0 + staged_bound(Sx + s0, len, w_hi, false, ux, uy, uz, sl.s, offv);
-      __syncwarp();
-      for (int base = lo; base < hi; base += 32) {
-        // 1. pre-filter 32 candidates into a bit mask per lane
-        unsigned mask = 0;
-#pragma unroll 1
-        for (int c0 = 0; c0 < 32 && base + c0 < hi; c0 += 8) {
-          unsigned m8 = 0;
-#pragma unroll
-          for (int c = 0; c < 8; c++) {
-            const float4 qv = Sx[base + c0 + c];
-            const float t = fmaf(L.nx, qv.x, fmaf(L.ny, qv.y, fmaf(L.nz, qv.z, qv.w)));
-            m8 |= (t < L.ci) ? (1u << c) : 0u;
-          }
-          mask |= m8 << c0;
-        }
-        if (hi - base < 32) mask &= (1u << (hi - base)) - 1u;
-        // 2. compact the hits of the 32 lanes into the warp's queue
-        const int cnt = __popc(mask);
-        int incl = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, d);
-          if (lane >= d) incl += y;
-        }
-        const int nq = __shfl_sync(0xffffffffu, incl, 31);
-        if (nq == 0) continue;
-        int w = incl - cnt;
-        for (unsigned m = mask; m; m &= m - 1u) Q[w++] = (unsigned short)((lane << 5) | (__ffs(m) - 1));
-        __syncwarp();
-        // 3. evaluate the queued pairs, 32 at a time, every lane busy; each
-        //    lane then adds the results of its own entries, in queue order
-        const int q0 = incl - cnt, q1 = incl;
-        for (int r0 = 0; r0 < nq; r0 += 32) {
-          const int k = r0 + lane;
-          float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          if (k < nq) {
-            const int e = Q[k];
-            const int src = e >> 5, c = e & 31;
-            const float4 ia = Ta[src];
-            const float4 qv = Sx[base + c];
-            const float dx = ia.x - qv.x, dy = ia.y - qv.y, dz = ia.z - qv.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float4 ib = Tb[src];
-            if (r2 < ib.x) {
-              bool in = true;
-              if (r2 >= ib.y) {  // within rounding of the cut-off: decide in FP64
-                const int pos = order_pos(sl.s, cs.J0[q] + base + c - s0, cs.nb_[q]);
-                const int sj = cs.cb_[q] + g.perm[(size_t)sl.k * g.n + cs.cb_[q] + pos];
-                in = guard_inside(g.pos64, __float_as_int(ib.z), sj, B.L, B.inv_L, Td[src]);
-                guards++;
-              }
-              if (in) {
-                const float q2 = r2 * ia.w;
-                const float qq = q2 * rsqrtf(fmaxf(q2, 1e-30f));
-                float wh, th;
-                spline_half(qq, q2, wh, th);
-                const float mj = Sm[base + c];
-                v = make_float4(mj * wh, mj * th, 1.0f, 0.0f);
-              }
-            }
-          }
-          R[lane] = v;
-          __syncwarp();
-          for (int t = max(q0, r0) - r0, t1 = min(q1, r0 + 32) - r0; t < t1; t++) {
-            const float4 u = R[t];
-            L.rho += u.x;
-            L.D += u.y;
-            L.n += (int)u.z;
-          }
-          __syncwarp();
-        }
-      }
+      const int J0q = cs.J0[q], nbq = cs.nb_[q], cbq = cs.cb_[q];
+      const size_t kbq = (size_t)sl.k * g.n + cbq;
+      auto jidx = [&](int j) {
+        return cbq + (int)g.perm[kbq + order_pos(sl.s, J0q + j - s0, nbq)];
+      };
+      sweep_fwd(L, Sx, Sm, lo, hi, Mw, lane, g, B, jidx, guards);
       if (p < cs.I[q] && L.n > 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&acc_r[il]),
                   (unsigned long long)__float2ll_rn(L.rho * (float)kFixScale));
@@ -567,6 +509,7 @@ __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
   __shared__ float s_m[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
   __shared__ int s_j[kTileJ + kPad];
+  __shared__ unsigned s_mask[kBlkI / 32][kMaskChunks * 32];
   __shared__ int s_task;
   if (*g.flags) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -618,7 +561,8 @@ __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
       if (w_hi > w_lo) {
         const int lo = (o == kSelfSlot) ? upper_bound_f(s_d, len, w_lo) : 0;
         const int hi = lower_bound_f(s_d, len, w_hi);
-        sweep_fwd(L, s_x, s_m, s_j, lo, hi, g, B, guards);
+        auto jidx = [&](int j) { return s_j[j]; };
+        sweep_fwd(L, s_x, s_m, lo, hi, s_mask[warp], lane, g, B, jidx, guards);
       }
       __syncthreads();
     }
@@ -725,7 +669,7 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
   }
   cudaError_t e = launch_plan(g, 0, kCellSmem - kCellFixedSmem, kCellElemJ, kCellElemA, st);
   if (e != cudaSuccess) return e;
-  k_density_cells<<<num_sms * 2, kCellThreads, kCellSmem, st>>>(g, rho, drho_dh, n_ngb);
+  k_density_cells<<<num_sms * 3, kCellThreads, kCellSmem, st>>>(g, rho, drho_dh, n_ngb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

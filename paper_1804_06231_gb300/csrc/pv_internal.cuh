@@ -184,21 +184,19 @@ __host__ __device__ __forceinline__ int order_pos(int s, int t, int cnt) { retur
 
 // ---- cubic spline, half-scaled ---------------------------------------------
 // With w(q) the shape function of the workload (8/pi factor included),
-// wh(q) = w(q) / (16/pi) and th(q) = (3 w(q) + q w'(q)) / (16/pi):
-//   q < 1/2 : wh = 1/2 + q^2 (3q - 3),  th = 3/2 + q^2 (18q - 15)
-//   q < 1   : wh = s^3,                  th = s^2 (3 - 6q),   s = 1 - q
-// so rho_i = (16/pi) H_i^-3 sum_j m_j wh(q_ij) and
-//    drho/dh_i = -(16/pi) / (h_i H_i^3) sum_j m_j th(q_ij).
-__device__ __forceinline__ void spline_half(float q, float q2, float& wh, float& th) {
-  float win = fmaf(q2, fmaf(3.0f, q, -3.0f), 0.5f);
-  float tin = fmaf(q2, fmaf(18.0f, q, -15.0f), 1.5f);
-  float s = fmaxf(1.0f - q, 0.0f);
-  float s2 = s * s;
-  float wout = s2 * s;
-  float tout = s2 * fmaf(-6.0f, q, 3.0f);
-  bool inner = q < 0.5f;
-  wh = inner ? win : wout;
-  th = inner ? tin : tout;
+// wh(q) = w(q) / (16/pi) and th(q) = (3 w(q) + q w'(q)) / (16/pi).  Writing
+// s = 1 - q and t = max(1/2 - q, 0), the two cubic pieces combine into
+//   wh = s^3 - 4 t^3
+//   th = s^2 (3 - 6q) - t^2 (6 - 24q)
+// (for q < 1/2 this expands to 1/2 - 3q^2 + 3q^3 and 3/2 - 15q^2 + 18q^3), so
+// rho_i = (16/pi) H_i^-3 sum_j m_j wh(q_ij) and
+// drho/dh_i = -(16/pi) / (h_i H_i^3) sum_j m_j th(q_ij).
+__device__ __forceinline__ void spline_half(float q, float& wh, float& th) {
+  const float s = 1.0f - q;
+  const float t = fmaxf(0.5f - q, 0.0f);
+  const float s2 = s * s, t2 = t * t;
+  wh = fmaf(-4.0f * t, t2, s2 * s);
+  th = fmaf(s2, fmaf(-6.0f, q, 3.0f), -t2 * fmaf(-24.0f, q, 6.0f));
 }
 
 // Guard band of the FP32 distance test.  The FP32 r^2 of a pair differs from
