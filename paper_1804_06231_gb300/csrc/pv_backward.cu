@@ -198,14 +198,16 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
       if (cnt < 32) m &= ~(0xFFFFFFFFu >> cnt);
       M[k * 32 + lane] = m;
     }
+    int nh = 0;
+    for (int k = 0; k < nk; k++) nh += __popc(M[k * 32 + lane]);
+    for (int s = 16; s > 0; s >>= 1) nh = max(nh, __shfl_xor_sync(0xffffffffu, nh, s));
     int k = 0;
     unsigned m = M[lane];
-    for (;;) {
+    for (int round = 0; round < nh; round++) {
       while (m == 0u && k + 1 < nk) {
         k++;
         m = M[k * 32 + lane];
       }
-      if (!__any_sync(0xffffffffu, m != 0u)) break;
       if (m == 0u) continue;
       const int c = __clz(m);
       m ^= 0x80000000u >> c;
@@ -353,8 +355,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
     float4* Sa = Sx + total + kPad;                    // [total + kPad] {m, G, K, H}
     double* acc = reinterpret_cast<double*>(Sa + total + kPad);  // [5][na]
     for (int f = tid; f < total; f += kCellThreads) {
-      int q = 0;
-      while (cs.off[q + 1] <= f) q++;
+      const int q = seg_of(cs.off, kNSlot, f);  // cs.off[q] <= f < cs.off[q+1]
       const int o = c_border[q];
       const Slot sl = slot_info(o);
       const int nb = cs.nb_[q], cb = cs.cb_[q];
@@ -373,8 +374,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
       if (lane == 0) it = atomicAdd(&cs.item_next, 1);
       it = __shfl_sync(0xffffffffu, it, 0);
       if (it >= nitems) break;
-      int q = 0;
-      while (cs.runs[q + 1] <= it) q++;
+      const int q = seg_of(cs.runs, kNSlot, it);
       const int o = c_border[q];
       const Slot sl = slot_info(o);
       float ux, uy, uz;

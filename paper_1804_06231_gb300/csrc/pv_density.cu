@@ -208,7 +208,7 @@ __device__ __forceinline__ void lane_set(LaneI& L, const GridDev& g, const BoxDe
   const float Hsq = H * H, gb = guard_band(H, B.edge_f);
   L.Hsq_hi = Hsq + gb;
   L.Hsq_lo = Hsq - gb;
-  L.Hinv2 = 1.0f / Hsq;
+  L.Hinv2 = __fdividef(1.0f, Hsq);
   L.Hd = g.gamma_d * (double)h;
   L.nx = -2.0f * L.x;
   L.ny = -2.0f * L.y;
@@ -259,14 +259,17 @@ __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ S
       if (cnt < 32) m &= ~(0xFFFFFFFFu >> cnt);
       M[k * 32 + lane] = m;
     }
+    // pass 2: as many rounds as the busiest lane has hits
+    int nh = 0;
+    for (int k = 0; k < nk; k++) nh += __popc(M[k * 32 + lane]);
+    for (int s = 16; s > 0; s >>= 1) nh = max(nh, __shfl_xor_sync(0xffffffffu, nh, s));
     int k = 0;
     unsigned m = M[lane];
-    for (;;) {
+    for (int round = 0; round < nh; round++) {
       while (m == 0u && k + 1 < nk) {
         k++;
         m = M[k * 32 + lane];
       }
-      if (!__any_sync(0xffffffffu, m != 0u)) break;
       if (m == 0u) continue;
       const int c = __clz(m);
       m ^= 0x80000000u >> c;
@@ -280,8 +283,7 @@ __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ S
         guards++;
       }
       if (in) {
-        const float q2 = r2 * L.Hinv2;
-        const float qq = q2 * rsqrtf(fmaxf(q2, 1e-30f));
+        const float qq = sqrt_approx(r2 * L.Hinv2);
         float wh, th;
         spline_half(qq, wh, th);
         const float mj = Sm[j];
@@ -416,8 +418,7 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
     int* acc_n = reinterpret_cast<int*>(Ah + na);              // [na]
     // stage the 27 windows in sorted order, and cell a in cell order
     for (int f = tid; f < total; f += kCellThreads) {
-      int q = 0;
-      while (cs.off[q + 1] <= f) q++;
+      const int q = seg_of(cs.off, kNSlot, f);  // cs.off[q] <= f < cs.off[q+1]
       const int o = c_slot_order[q];
       const Slot sl = slot_info(o);
       const int nb = cs.nb_[q], cb = cs.cb_[q];
@@ -442,8 +443,7 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
       if (lane == 0) it = atomicAdd(&cs.item_next, 1);
       it = __shfl_sync(0xffffffffu, it, 0);
       if (it >= nitems) break;
-      int q = 0;
-      while (cs.runs[q + 1] <= it) q++;
+      const int q = seg_of(cs.runs, kNSlot, it);
       const int o = c_slot_order[q];
       const Slot sl = slot_info(o);
       float ux, uy, uz;

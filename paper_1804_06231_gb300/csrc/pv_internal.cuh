@@ -157,6 +157,23 @@ __device__ __forceinline__ void atomic_max_nonneg(float* p, float v) {
   atomicMax(reinterpret_cast<int*>(p), __float_as_int(v));
 }
 
+// sqrt with the hardware approximation (about 1 ulp; 0 -> 0)
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// last q in [0, n) with a[q] <= v for a non-decreasing int array with a[0] <= v
+__device__ __forceinline__ int seg_of(const int* a, int n, int v) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a[mid] <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // first index t in [0, n) with a[t] >= x (a ascending), n if none
 __device__ __forceinline__ int lower_bound_f(const float* a, int n, float x) {
   int lo = 0, hi = n;
