@@ -131,6 +131,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_TRY(dev_alloc(g, &d.dist, pv::kNDir * N));
   PV_TRY(dev_alloc(g, &d.skey, N));
   PV_TRY(dev_alloc(g, &d.sbuf, N));
+  PV_TRY(dev_alloc(g, &d.stmp, N));
   PV_TRY(dev_alloc(g, &d.sbucket, 2 * N));
   PV_TRY(dev_alloc(g, &d.acc, 3 * N));
   PV_TRY(dev_alloc(g, &d.gacc, 5 * N));

@@ -185,14 +185,10 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
       const int cnt = min(32, seg_end - base);
       unsigned m = 0;
       int c0 = 0;
+      const unsigned sbase = (unsigned)__cvta_generic_to_shared(Sx + base);
 #pragma unroll 1
       for (; c0 < cnt; c0 += 8) {
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-          const float4 q = Sx[base + c0 + c];
-          const float d = fmaf(L.nx, q.x, fmaf(L.ny, q.y, fmaf(L.nz, q.z, q.w - L.ci)));
-          m = __funnelshift_l(__float_as_uint(d), m, 1);
-        }
+        prefilter8(m, sbase + 16u * c0, L.nx, L.ny, L.nz, L.ci);
       }
       m <<= (32 - c0);
       if (cnt < 32) m &= ~(0xFFFFFFFFu >> cnt);

@@ -200,13 +200,15 @@ __device__ __forceinline__ int group_exclusive_scan(int v, int rank, int* scratc
 
 // Sorts the cnt particles of one cell by key.  `grp` threads (a warp, or the
 // whole block when kBlock) with ranks 0..grp-1 cooperate.  Arrays:
-//   orig[cnt] (tie break), key[cnt], out[cnt] (sorted cell-local indices),
-//   bucket[B] (B a power of two >= grp), scratch[32] (block scan).
-// Buckets are monotone in the key, so after the counting sort only the order
-// inside a bucket remains; it is fixed by insertion on (key, caller index).
-template <bool kBlock>
-__device__ void sort_axis(int cnt, const int* orig, const float* key, int* out, int* bucket,
-                          int* scratch, int B, int rank, int grp, float kmin, float kmax) {
+//   orig[cnt] (tie break), key[cnt], tmp[cnt] and out[cnt] (cell-local
+//   indices), bucket[B] (B a power of two >= grp), scratch[32] (block scan).
+// Buckets are monotone in the key: a counting sort by bucket leaves only the
+// order inside each bucket, which every element then settles by counting the
+// members of its bucket that precede it in (key, caller index) order.
+template <bool kBlock, typename Idx>
+__device__ void sort_axis(int cnt, const int* orig, const float* key, Idx* tmp, Idx* out,
+                          int* bucket, int* scratch, int B, int rank, int grp, float kmin,
+                          float kmax) {
   const float scale = kmax > kmin ? (float)B / (kmax - kmin) : 0.0f;
   for (int b = rank; b < B; b += grp) bucket[b] = 0;
   group_sync<kBlock>();
@@ -229,35 +231,33 @@ __device__ void sort_axis(int cnt, const int* orig, const float* key, int* out, 
   group_sync<kBlock>();
   for (int t = rank; t < cnt; t += grp) {
     const int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
-    out[atomicAdd(&bucket[b], 1)] = t;
+    tmp[atomicAdd(&bucket[b], 1)] = (Idx)t;
   }
   group_sync<kBlock>();
-  // bucket[b] is now the end of bucket b: insertion sort by (key, orig)
-  for (int b = rank; b < B; b += grp) {
+  // bucket[b] is now the end of bucket b (= the start of bucket b+1)
+  for (int t = rank; t < cnt; t += grp) {
+    const int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
     const int s0 = b ? bucket[b - 1] : 0, s1 = bucket[b];
-    for (int i = s0 + 1; i < s1; i++) {
-      const int v = out[i];
-      const float kv = key[v];
-      const int ov = orig[v];
-      int j = i - 1;
-      while (j >= s0 && key_less(kv, ov, key[out[j]], orig[out[j]])) {
-        out[j + 1] = out[j];
-        j--;
-      }
-      out[j + 1] = v;
+    const float kt = key[t];
+    const int ot = orig[t];
+    int r = 0;
+    for (int u = s0; u < s1; u++) {
+      const int v = tmp[u];
+      r += key_less(key[v], orig[v], kt, ot) ? 1 : 0;
     }
+    out[s0 + r] = (Idx)t;
   }
   group_sync<kBlock>();
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
   extern __shared__ float4 smem4[];
-  float4* s_x = smem4;                                            // [512]
-  int* s_orig = reinterpret_cast<int*>(s_x + kSortSmallMax);       // [512]
-  float* s_key = reinterpret_cast<float*>(s_orig + kSortSmallMax); // [13][512]
-  int* s_out = reinterpret_cast<int*>(s_key + kNDir * kSortSmallMax);  // [13][512]
-  int* s_bkt = s_out + kNDir * kSortSmallMax;                      // [13][512 + 32]
-  // per warp: buckets [512], then 32 ints of scan scratch
+  float4* s_x = smem4;                                                 // [512]
+  int* s_orig = reinterpret_cast<int*>(s_x + kSortSmallMax);            // [512]
+  float* s_key = reinterpret_cast<float*>(s_orig + kSortSmallMax);      // [13][512]
+  int* s_bkt = reinterpret_cast<int*>(s_key + kNDir * kSortSmallMax);   // [13][512]
+  uint16_t* s_out = reinterpret_cast<uint16_t*>(s_bkt + kNDir * kSortSmallMax);  // [13][512]
+  uint16_t* s_tmp = s_out + kNDir * kSortSmallMax;                     // [13][512]
   const int c = blockIdx.x;
   const int cnt = g.cell_count[c];
   if (cnt == 0 || cnt > kSortSmallMax) return;
@@ -271,8 +271,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
   float ux, uy, uz;
   axis_u(k, ux, uy, uz);
   float* key = s_key + k * kSortSmallMax;
-  int* out = s_out + k * kSortSmallMax;
-  int* bkt = s_bkt + k * (kSortSmallMax + 32);
+  uint16_t* out = s_out + k * kSortSmallMax;
+  uint16_t* tmp = s_tmp + k * kSortSmallMax;
+  int* bkt = s_bkt + k * kSortSmallMax;
   float kmin = 3.0e38f, kmax = -3.0e38f;
   for (int t = lane; t < cnt; t += 32) {
     float d = project(s_x[t], ux, uy, uz);
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
   }
   int B = 32;
   while (B < cnt) B <<= 1;
-  sort_axis<false>(cnt, s_orig, key, out, bkt, nullptr, B, lane, 32, kmin, kmax);
+  sort_axis<false>(cnt, s_orig, key, tmp, out, bkt, nullptr, B, lane, 32, kmin, kmax);
   const size_t base = (size_t)k * g.n + cs;
   for (int t = lane; t < cnt; t += 32) {
     int v = out[t];
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
   }
 }
 
-__global__ void __launch_bounds__(1024) k_sort_big(GridDev g) {
+__global__ void __launch_bounds__(1024, 1) k_sort_big(GridDev g) {
   __shared__ float s_red[2][32];
   __shared__ int s_chunk[32];
   const int nbig = *g.n_big;
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(1024) k_sort_big(GridDev g) {
     while (B < cnt) B <<= 1;
     float* key = g.skey + cs;
     int* out = g.sbuf + cs;
+    int* tmp = g.stmp + cs;
     // buckets: B <= 2 cnt slots of the cell's own range [2 cs, 2 cs + 2 cnt)
     // (cnt > 512 and B = max(1024, next power of two >= cnt))
     int* bkt = g.sbucket + 2 * (size_t)cs;
@@ -336,8 +338,8 @@ __global__ void __launch_bounds__(1024) k_sort_big(GridDev g) {
         kmax = fmaxf(kmax, s_red[1][w]);
       }
       __syncthreads();
-      sort_axis<true>(cnt, g.orig + cs, key, out, bkt, s_chunk, B, threadIdx.x, blockDim.x, kmin,
-                      kmax);
+      sort_axis<true>(cnt, g.orig + cs, key, tmp, out, bkt, s_chunk, B, threadIdx.x, blockDim.x,
+                      kmin, kmax);
       const size_t base = (size_t)k * g.n + cs;
       for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         int v = out[t];
@@ -373,8 +375,7 @@ cudaError_t launch_scatter(const GridDev& g, const double* pos, const float* h, 
 cudaError_t launch_sort(const GridDev& g, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
   const size_t smem = kSortSmallMax * (sizeof(float4) + sizeof(int)) +
-                      kNDir * kSortSmallMax * (sizeof(float) + sizeof(int)) +
-                      kNDir * (kSortSmallMax + 32) * sizeof(int);
+                      kNDir * kSortSmallMax * (sizeof(float) + sizeof(int) + 2 * sizeof(uint16_t));
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -70,6 +70,7 @@ struct GridDev {
   // sort scratch for big cells (cell order)
   float* skey;
   int32_t* sbuf;
+  int32_t* stmp;
   int32_t* sbucket;  // [2N]
   // density accumulators (cell order), fixed point
   long long* acc;    // [3][N]: rho, drho/dh (2^36 scale), n
@@ -157,6 +158,47 @@ __device__ __forceinline__ void atomic_max_nonneg(float* p, float v) {
   atomicMax(reinterpret_cast<int*>(p), __float_as_int(v));
 }
 
+// Pre-filter of 8 consecutive staged particles (float4 {x, y, z, |x|^2} at
+// shared-memory byte address `saddr`) for one particle i: shifts the sign of
+// |x_j|^2 - 2 x_i.x_j - ci (nx, ny, nz = -2 x_i) into `m`, first candidate
+// first (one load, one subtract, three fused multiply-adds and one funnel
+// shift per candidate).
+__device__ __forceinline__ void prefilter8(unsigned& m, unsigned saddr, float nx, float ny,
+                                           float nz, float ci) {
+  asm volatile(
+      "{\n\t.reg .f32 a<4>, b<4>, d, e;\n\t"
+      "ld.shared.v4.f32 {a0,a1,a2,a3}, [%1];\n\t"
+      "ld.shared.v4.f32 {b0,b1,b2,b3}, [%1+16];\n\t"
+      "sub.f32 d, a3, %5;\n\tfma.rn.f32 d, %4, a2, d;\n\tfma.rn.f32 d, %3, a1, d;\n\t"
+      "fma.rn.f32 d, %2, a0, d;\n\t"
+      "sub.f32 e, b3, %5;\n\tfma.rn.f32 e, %4, b2, e;\n\tfma.rn.f32 e, %3, b1, e;\n\t"
+      "fma.rn.f32 e, %2, b0, e;\n\t"
+      "shf.l.wrap.b32 %0, d, %0, 1;\n\tshf.l.wrap.b32 %0, e, %0, 1;\n\t"
+      "ld.shared.v4.f32 {a0,a1,a2,a3}, [%1+32];\n\t"
+      "ld.shared.v4.f32 {b0,b1,b2,b3}, [%1+48];\n\t"
+      "sub.f32 d, a3, %5;\n\tfma.rn.f32 d, %4, a2, d;\n\tfma.rn.f32 d, %3, a1, d;\n\t"
+      "fma.rn.f32 d, %2, a0, d;\n\t"
+      "sub.f32 e, b3, %5;\n\tfma.rn.f32 e, %4, b2, e;\n\tfma.rn.f32 e, %3, b1, e;\n\t"
+      "fma.rn.f32 e, %2, b0, e;\n\t"
+      "shf.l.wrap.b32 %0, d, %0, 1;\n\tshf.l.wrap.b32 %0, e, %0, 1;\n\t"
+      "ld.shared.v4.f32 {a0,a1,a2,a3}, [%1+64];\n\t"
+      "ld.shared.v4.f32 {b0,b1,b2,b3}, [%1+80];\n\t"
+      "sub.f32 d, a3, %5;\n\tfma.rn.f32 d, %4, a2, d;\n\tfma.rn.f32 d, %3, a1, d;\n\t"
+      "fma.rn.f32 d, %2, a0, d;\n\t"
+      "sub.f32 e, b3, %5;\n\tfma.rn.f32 e, %4, b2, e;\n\tfma.rn.f32 e, %3, b1, e;\n\t"
+      "fma.rn.f32 e, %2, b0, e;\n\t"
+      "shf.l.wrap.b32 %0, d, %0, 1;\n\tshf.l.wrap.b32 %0, e, %0, 1;\n\t"
+      "ld.shared.v4.f32 {a0,a1,a2,a3}, [%1+96];\n\t"
+      "ld.shared.v4.f32 {b0,b1,b2,b3}, [%1+112];\n\t"
+      "sub.f32 d, a3, %5;\n\tfma.rn.f32 d, %4, a2, d;\n\tfma.rn.f32 d, %3, a1, d;\n\t"
+      "fma.rn.f32 d, %2, a0, d;\n\t"
+      "sub.f32 e, b3, %5;\n\tfma.rn.f32 e, %4, b2, e;\n\tfma.rn.f32 e, %3, b1, e;\n\t"
+      "fma.rn.f32 e, %2, b0, e;\n\t"
+      "shf.l.wrap.b32 %0, d, %0, 1;\n\tshf.l.wrap.b32 %0, e, %0, 1;\n\t}"
+      : "+r"(m)
+      : "r"(saddr), "f"(nx), "f"(ny), "f"(nz), "f"(ci));
+}
+
 // sqrt with the hardware approximation (about 1 ulp; 0 -> 0)
 __device__ __forceinline__ float sqrt_approx(float x) {
   float r;
@@ -228,7 +270,7 @@ __device__ __forceinline__ float guard_band(float H, float edge) {
 
 // FP64 re-decision of r_ij < H_i for a pair in the guard band, from the
 // wrapped FP64 positions with the minimum-image convention.
-static __device__ __noinline__ bool guard_inside(const double* __restrict__ pos64, int si,
+static __device__ __forceinline__ bool guard_inside(const double* __restrict__ pos64, int si,
                                                  int sj, double L, double inv_L, double Hd) {
   double r2 = 0.0;
 #pragma unroll
