@@ -180,6 +180,8 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
   for (int seg = lo; seg < hi; seg += 32 * kMaskChunks) {
     const int seg_end = min(hi, seg + 32 * kMaskChunks);
     const int nk = (seg_end - seg + 31) >> 5;
+    unsigned nz = 0;
+    int tot = 0;
     for (int k = 0; k < nk; k++) {
       const int base = seg + 32 * k;
       const int cnt = min(32, seg_end - base);
@@ -187,59 +189,53 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
       int c0 = 0;
       const unsigned sbase = (unsigned)__cvta_generic_to_shared(Sx + base);
 #pragma unroll 1
-      for (; c0 < cnt; c0 += 8) {
-        prefilter8(m, sbase + 16u * c0, L.nx, L.ny, L.nz, L.ci);
-      }
-      m <<= (32 - c0);
-      if (cnt < 32) m &= ~(0xFFFFFFFFu >> cnt);
+      for (; c0 < cnt; c0 += 8) prefilter8(m, sbase + 16u * c0, L.nx, L.ny, L.nz, L.ci);
+      m = __brev(m) >> (32 - c0);
+      if (cnt < 32) m &= (1u << cnt) - 1u;
       M[k * 32 + lane] = m;
+      nz |= (m != 0u ? 1u : 0u) << k;
+      tot += __popc(m);
     }
-    int nh = 0;
-    for (int k = 0; k < nk; k++) nh += __popc(M[k * 32 + lane]);
-    for (int s = 16; s > 0; s >>= 1) nh = max(nh, __shfl_xor_sync(0xffffffffu, nh, s));
+    for (int s = 16; s > 0; s >>= 1) tot = max(tot, __shfl_xor_sync(0xffffffffu, tot, s));
     int k = 0;
-    unsigned m = M[lane];
-    for (int round = 0; round < nh; round++) {
-      while (m == 0u && k + 1 < nk) {
-        k++;
+    unsigned m = 0;
+    for (int round = 0; round < tot; round++) {
+      if (m == 0u && nz != 0u) {
+        k = __ffs(nz) - 1;
+        nz &= nz - 1u;
         m = M[k * 32 + lane];
       }
-      if (m == 0u) continue;
-      const int c = __clz(m);
-      m ^= 0x80000000u >> c;
-      const int j = seg + 32 * k + c;
+      const int c = __ffs(m) - 1;
+      m &= m - 1u;
+      const int j = seg + 32 * k + max(c, 0);
       const float4 q = Sx[j];
       const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       const float4 aj = Sa[j];  // m_j, G_j, K_j, H_j
       const float gbj = guard_band(aj.w, B.edge_f);
       const float Ej = fmaf(aj.w, aj.w, gbj);
-      bool own = r2 < L.Hsq_hi;
-      bool trans = r2 < Ej;
-      if (!(own || trans)) continue;
+      bool own = (c >= 0) && (r2 < L.Hsq_hi);
+      bool trans = (c >= 0) && (r2 < Ej);
       const bool gown = own && r2 >= L.Hsq_lo;
       const bool gtr = trans && r2 >= Ej - 2.0f * gbj;
-      if (gown || gtr) {  // within rounding of a cut-off: decide in FP64
-        const int sj = jidx(j);
-        if (gown) own = guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, L.Hd);
-        if (gtr)
-          trans = guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, g.gamma_d * (double)g.hs[sj]);
+      if (__any_sync(0xffffffffu, gown || gtr)) {  // within rounding of a cut-off: FP64
+        if (gown || gtr) {
+          const int sj = jidx(j);
+          if (gown) own = guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, L.Hd);
+          if (gtr)
+            trans = guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, g.gamma_d * (double)g.hs[sj]);
+        }
       }
       const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
       const float r = r2 * rinv;
-      float cc = 0.0f;
-      if (own) {
-        float th, uh, vr, vh;
-        spline_bwd(r * L.Hinv, L.H * rinv, th, uh, vr, vh);
-        L.Sth = fmaf(aj.x, th, L.Sth);
-        L.Suh = fmaf(aj.x, uh, L.Suh);
-        cc = aj.x * fmaf(L.G, vr, -L.K * vh);
-      }
-      if (trans) {
-        float vr, vh;
-        spline_bwd_v(r / aj.w, aj.w * rinv, vr, vh);
-        cc = fmaf(L.m, fmaf(aj.y, vr, -aj.z * vh), cc);
-      }
+      float th, uh, vr, vh, vrj, vhj;
+      spline_bwd(r * L.Hinv, L.H * rinv, th, uh, vr, vh);
+      spline_bwd_v(r * __fdividef(1.0f, aj.w), aj.w * rinv, vrj, vhj);
+      const float mo = own ? aj.x : 0.0f;
+      L.Sth = fmaf(mo, th, L.Sth);
+      L.Suh = fmaf(mo, uh, L.Suh);
+      const float mt = trans ? L.m : 0.0f;
+      const float cc = fmaf(mo, fmaf(L.G, vr, -L.K * vh), mt * fmaf(aj.y, vrj, -aj.z * vhj));
       L.gx = fmaf(cc, dx, L.gx);
       L.gy = fmaf(cc, dy, L.gy);
       L.gz = fmaf(cc, dz, L.gz);

@@ -241,6 +241,8 @@ __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ S
   for (int seg = lo; seg < hi; seg += 32 * kMaskChunks) {
     const int seg_end = min(hi, seg + 32 * kMaskChunks);
     const int nk = (seg_end - seg + 31) >> 5;
+    unsigned nz = 0;  // chunks of this lane with at least one hit
+    int tot = 0;      // hits of this lane in the segment
     for (int k = 0; k < nk; k++) {
       const int base = seg + 32 * k;
       const int cnt = min(32, seg_end - base);
@@ -248,45 +250,45 @@ __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ S
       int c0 = 0;
       const unsigned sbase = (unsigned)__cvta_generic_to_shared(Sx + base);
 #pragma unroll 1
-      for (; c0 < cnt; c0 += 8) {
-        prefilter8(m, sbase + 16u * c0, L.nx, L.ny, L.nz, L.ci);
-      }
-      m <<= (32 - c0);                                   // candidate c at bit 31 - c
-      if (cnt < 32) m &= ~(0xFFFFFFFFu >> cnt);
+      for (; c0 < cnt; c0 += 8) prefilter8(m, sbase + 16u * c0, L.nx, L.ny, L.nz, L.ci);
+      m = __brev(m) >> (32 - c0);                        // candidate c at bit c
+      if (cnt < 32) m &= (1u << cnt) - 1u;
       M[k * 32 + lane] = m;
+      nz |= (m != 0u ? 1u : 0u) << k;
+      tot += __popc(m);
     }
-    // pass 2: as many rounds as the busiest lane has hits
-    int nh = 0;
-    for (int k = 0; k < nk; k++) nh += __popc(M[k * 32 + lane]);
-    for (int s = 16; s > 0; s >>= 1) nh = max(nh, __shfl_xor_sync(0xffffffffu, nh, s));
+    // pass 2: as many rounds as the busiest lane has hits; no divergent
+    // branches except the (warp-uniform) FP64 re-decision near the cut-off
+    for (int s = 16; s > 0; s >>= 1) tot = max(tot, __shfl_xor_sync(0xffffffffu, tot, s));
     int k = 0;
-    unsigned m = M[lane];
-    for (int round = 0; round < nh; round++) {
-      while (m == 0u && k + 1 < nk) {
-        k++;
+    unsigned m = 0;
+    for (int round = 0; round < tot; round++) {
+      if (m == 0u && nz != 0u) {
+        k = __ffs(nz) - 1;
+        nz &= nz - 1u;
         m = M[k * 32 + lane];
       }
-      if (m == 0u) continue;
-      const int c = __clz(m);
-      m ^= 0x80000000u >> c;
-      const int j = seg + 32 * k + c;
+      const int c = __ffs(m) - 1;  // -1: this lane has no hit left
+      m &= m - 1u;
+      const int j = seg + 32 * k + max(c, 0);
       const float4 q = Sx[j];
       const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      bool in = r2 < L.Hsq_lo;
-      if (!in && r2 < L.Hsq_hi) {  // within rounding of the cut-off: decide in FP64
-        in = guard_inside(g.pos64, L.si, jidx(j), B.L, B.inv_L, L.Hd);
-        guards++;
+      bool in = (c >= 0) && (r2 < L.Hsq_hi);
+      const bool grd = in && (r2 >= L.Hsq_lo);
+      if (__any_sync(0xffffffffu, grd)) {  // within rounding of the cut-off: FP64
+        if (grd) {
+          in = guard_inside(g.pos64, L.si, jidx(j), B.L, B.inv_L, L.Hd);
+          guards++;
+        }
       }
-      if (in) {
-        const float qq = sqrt_approx(r2 * L.Hinv2);
-        float wh, th;
-        spline_half(qq, wh, th);
-        const float mj = Sm[j];
-        L.rho = fmaf(mj, wh, L.rho);
-        L.D = fmaf(mj, th, L.D);
-        L.n++;
-      }
+      const float qq = sqrt_approx(r2 * L.Hinv2);
+      float wh, th;
+      spline_half(qq, wh, th);
+      const float mj = in ? Sm[j] : 0.0f;
+      L.rho = fmaf(mj, wh, L.rho);
+      L.D = fmaf(mj, th, L.D);
+      L.n += in ? 1 : 0;
     }
   }
 }
