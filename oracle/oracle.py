@@ -57,6 +57,8 @@ def _load():
         lib.or_backward_brute.argtypes = [i64, p, p, p, d, d, p, p, p, p, i32]
         lib.or_backward_cells.restype = i32
         lib.or_backward_cells.argtypes = [i64, p, p, p, d, i32, d, p, p, p, p, i32]
+        lib.or_adjoint_counts.restype = i32
+        lib.or_adjoint_counts.argtypes = [i64, p, p, d, i32, d, p, i32]
         lib.or_fd_loss.restype = d
         lib.or_fd_loss.argtypes = [i64, p, p, p, d, d, p, p, i64, i32, d]
         _lib = lib
@@ -214,3 +216,15 @@ def fd_loss_grad(pos, h, m, w_weights, v_weights, p, comp, delta=1e-6, L=1.0,
     wv = _f64(w_weights); vv = _f64(v_weights)
     return float(_load().or_fd_loss(n, _ptr(pos), _ptr(h), _ptr(m), float(L), float(gamma),
                                     _ptr(wv), _ptr(vv), int(p), int(comp), float(delta)))
+
+
+def adjoint_counts(pos, h, L=1.0, nc=3, gamma=GAMMA_DEFAULT, threads=0):
+    """(candidates, pairs) of the adjoint sweep: window and pair cut-off max(H_i, H_j)."""
+    pos = _f64(pos, (-1, 3)); n = pos.shape[0]
+    h = _f64(h)
+    out = np.zeros(2, np.int64)
+    rc = _load().or_adjoint_counts(n, _ptr(pos), _ptr(h), float(L), int(nc), float(gamma),
+                                   _ptr(out), int(threads))
+    if rc:
+        raise ValueError(f"oracle adjoint_counts: {_ERR.get(rc, rc)}")
+    return int(out[0]), int(out[1])

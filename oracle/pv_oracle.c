@@ -667,3 +667,70 @@ double or_fd_loss(int64_t n, const double* pos, const double* h, const double* m
   free(A);
   return (f[0] - f[1]) / (2.0 * delta);
 }
+
+/* ------------------------------------------------------------------------ */
+/* 7. Counts of the adjoint sweep: per particle i and neighbour cell, the    */
+/*    particles j of the sorted window with projected distance below         */
+/*    max(H_i, H_j) ("candidates") and the pairs with r_ij < max(H_i, H_j)   */
+/*    (j = i included).  out[0] = candidates, out[1] = pairs.                */
+/* ------------------------------------------------------------------------ */
+
+int or_adjoint_counts(int64_t n, const double* pos, const double* h, double L, int nc,
+                      double gamma, int64_t* out, int nthreads) {
+  if (nc < 3) return -2;
+  set_threads(nthreads);
+  or_grid g;
+  if (grid_build(&g, n, pos, h, L, nc, gamma, 1)) return -1;
+  for (int64_t c = 0; c < g.ncell; c++) /* the 27-cell stencil needs H <= edge */
+    if (g.Hmax[c] * (1.0 + OR_BAND) > g.edge) { grid_free(&g); return -3; }
+  int64_t cand = 0, pairs = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : cand, pairs)
+  for (int64_t a = 0; a < g.ncell; a++) {
+    int ca[3];
+    cell_coords(&g, a, ca);
+    int64_t a0 = g.start[a], na = g.start[a + 1] - a0;
+    for (int k = 0; k < OR_NDIR; k++) {
+      int v2 = OR_V[k][0] * OR_V[k][0] + OR_V[k][1] * OR_V[k][1] + OR_V[k][2] * OR_V[k][2];
+      double shift = sqrt((double)v2) * g.edge;
+      for (int s = 1; s >= -1; s -= 2) {
+        int o[3] = {s * OR_V[k][0], s * OR_V[k][1], s * OR_V[k][2]};
+        int64_t b = cell_id(&g, ca[0] + o[0], ca[1] + o[1], ca[2] + o[2]);
+        int64_t b0 = g.start[b], nb = g.start[b + 1] - b0;
+        for (int64_t t = 0; t < na; t++) {
+          int64_t pa = s > 0 ? a0 + t : a0 + na - 1 - t;
+          int64_t si = g.sidx[k][pa], i = g.member[si];
+          double di = s * g.dist[k][pa], Hi = gamma * h[i];
+          for (int64_t u = 0; u < nb; u++) {
+            int64_t pb = s > 0 ? b0 + u : b0 + nb - 1 - u;
+            double dj = s * g.dist[k][pb] + shift;
+            if (dj - di >= g.Hmax[b] && dj - di >= Hi) break;
+            int64_t sj = g.sidx[k][pb], j = g.member[sj];
+            double R = fmax(Hi, gamma * h[j]);
+            if (dj - di < R) {
+              cand++;
+              if (pair_r(&g, si, sj, o) < R) pairs++;
+            }
+          }
+        }
+      }
+    }
+    /* self cell: two-sided window on axis (0,0,1) */
+    const int o0[3] = {0, 0, 0};
+    for (int64_t t = 0; t < na; t++) {
+      int64_t si = g.sidx[0][a0 + t], i = g.member[si];
+      double di = g.dist[0][a0 + t], Hi = gamma * h[i];
+      for (int64_t u = 0; u < na; u++) {
+        int64_t sj = g.sidx[0][a0 + u], j = g.member[sj];
+        double R = fmax(Hi, gamma * h[j]);
+        if (fabs(g.dist[0][a0 + u] - di) < R) {
+          cand++;
+          if (pair_r(&g, si, sj, o0) < R) pairs++;
+        }
+      }
+    }
+  }
+  out[0] = cand;
+  out[1] = pairs;
+  grid_free(&g);
+  return 0;
+}

@@ -319,3 +319,24 @@ def test_adjoint_matches_finite_differences(oracle_lib, kind):
             assert fd == pytest.approx(gp[p, comp], abs=1e-6 * scale_x, rel=1e-5)
         fd = O.fd_loss_grad(b.pos, b.h, b.m, w, v, p, 3, 1e-6)
         assert fd == pytest.approx(gh[p], abs=1e-6 * scale_h, rel=1e-5)
+
+
+def test_adjoint_counts_brute_force(oracle_lib):
+    """The adjoint sweep's pair count (cut-off max(H_i, H_j), j = i included)
+    equals a brute-force count with minimum-image distances; its window counts
+    lie between the pairs and the 27-cell stencil."""
+    O = oracle_lib
+    for box in (I.uniform(3000, 5, nc=5), I.clustered(3000, 6, nc=3)):
+        H = G * box.h.astype(np.float64)
+        d = box.pos[:, None, :] - box.pos[None, :, :]
+        d -= np.round(d / box.L) * box.L
+        r = np.sqrt((d * d).sum(-1))
+        brute = int((r < np.maximum(H[:, None], H[None, :])).sum())
+        cand, pairs = O.adjoint_counts(box.pos, box.h, box.L, box.nc)
+        assert pairs == brute
+        cells = np.floor(box.pos / box.L * box.nc).astype(int) % box.nc
+        dc = (cells[:, None, :] - cells[None, :, :]) % box.nc
+        stencil = int(np.all((dc <= 1) | (dc == box.nc - 1), axis=-1).sum())
+        assert pairs < cand < stencil
+    with pytest.raises(ValueError):
+        O.adjoint_counts(box.pos, box.h * 1.5, box.L, box.nc)
