@@ -33,7 +33,45 @@ WORKLOAD = "uniform N=1048576, 15^3 cells, h=1.2348 N^-1/3 U(0.9,1.1), sort+dens
 # algorithmic FP32 work: flops per window candidate and per
 # in-range pair of the forward sweep, per candidate and per pair of the adjoint
 FWD_FLOP_CAND, FWD_FLOP_PAIR = 9, 23
+BWD_FLOP_CAND, BWD_FLOP_OWN, BWD_FLOP_TRANS, BWD_FLOP_PAIR = 10, 24, 11, 6
 FP32_LANES_PER_SM = 128
+CSRC = os.path.join(ROOT, "paper_1804_06231_gb300", "csrc")
+# sweep kernel -> (ncu summary under profiles/, sources whose hash it was taken on)
+PROFILED = {
+    "k_backward_cells": ("backward_cells_uniform1m.md", ("pv_backward.cu", "pv_internal.cuh")),
+    "k_density_cells": ("density_cells_uniform1m.md", ("pv_density.cu", "pv_internal.cuh")),
+}
+
+
+def sources_sha256(files):
+    import hashlib
+    hs = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            hs.update(fh.read())
+    return hs.hexdigest()
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes (read + write) per launch of `kernel` on the default workload,
+    from its ncu summary, or None when the summary is missing or was taken on
+    other kernel sources than the current ones."""
+    name, files = PROFILED[kernel]
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.split(":", 1)[0].strip() in ("dram_bytes_per_launch",
+                                                             "sources_sha256"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("sources_sha256") != sources_sha256(files):
+        return None
+    try:
+        return int(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def parse():
@@ -175,17 +213,18 @@ def run_reference(args, ws, rank):
     cores = host_cores()
     box = cpu_sample(0)
     steps, warmup = max(1, args.steps), max(0, args.warmup)
-    # bound the total: each step is ~1-3 s on 16 cores; cap the count
-    steps = min(steps, 20)
-    warmup = min(warmup, 2)
+    # bound the total: each step is ~1-2 s on 16 cores; cap the counts
+    steps = min(steps, 40)
+    warmup = min(warmup, 10)
     inter, times = time_oracle(box, steps, warmup, cores)
     t = statistics.mean(times)
     value = inter / t
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": len(times), "warmup": warmup, "ms_per_step": 1e3 * t,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": box.name},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": box.name, "device": "host CPU cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": box.name + "; FP64 pseudo-Verlet density + cell-list adjoint"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -243,6 +282,8 @@ def main():
     st0 = grid.stats()
     interactions = st0.interactions
     candidates = grid.count_candidates()
+    st_c = grid.stats()
+    cand_adj, pairs_adj = st_c.candidates_adjoint, st_c.pairs_adjoint
 
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
@@ -259,6 +300,7 @@ def main():
         clocks.start()
         time.sleep(0.4)
     launches0 = grid.stats().kernel_launches
+    grid.time_sweeps(True)  # CUDA events around the two sweep kernels
     wall0 = time.perf_counter()
     for k in range(K):
         flush.zero_()  # evict the previous step's data from L2 (outside the events)
@@ -276,6 +318,8 @@ def main():
         dist.barrier()
     clk = clocks.stop() if clocks else None
     launches = grid.stats().kernel_launches - launches0
+    k_dens, k_bwd = grid.sweep_times()  # ms per launch of k_density_cells / k_backward_cells
+    grid.time_sweeps(False)
     t_sort = sum(e[0].elapsed_time(e[1]) for e in ev) / K
     t_dens = sum(e[1].elapsed_time(e[2]) for e in ev) / K
     t_bwd = sum(e[2].elapsed_time(e[3]) for e in ev) / K
@@ -335,18 +379,27 @@ def main():
         e2e = {"value": tot_inter / (t_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": t_e2e}
 
-    # ---- roofline of the forward density sweep (FP32 ALU bound)
+    # ---- rooflines of the two sweep kernels (FP32 ALU bound); the adjoint
+    # sweep is the dominant kernel of the step
     peaks = measured_peaks()
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    peak_src = f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
+    default_size = not (args.particles or args.cells)
     pairs = interactions + n  # in-range pairs evaluated, including j = i
     fwd_flops = FWD_FLOP_CAND * candidates + FWD_FLOP_PAIR * pairs
-    achieved = fwd_flops / (t_dens * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "pv_density (plan + sweep + finalize)",
-                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
-                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-                               f"{sm_max:.0f} MHz"}
+    bwd_flops = (BWD_FLOP_CAND * cand_adj + (BWD_FLOP_OWN + BWD_FLOP_TRANS) * interactions
+                 + BWD_FLOP_PAIR * (pairs_adj - n))
+
+    def roof(kernel, flops, ms):
+        a = flops / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": kernel, "achieved": a, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": a / peak_tflops,
+                "traffic": profiled_traffic(kernel) if default_size else None,
+                "flop_per_launch": flops, "ms_per_launch": ms, "peak_source": peak_src}
+
+    roofline = roof("k_backward_cells", bwd_flops, k_bwd)
+    roofline_fwd = roof("k_density_cells", fwd_flops, k_dens)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -373,12 +426,15 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches,
             "roofline": roofline,
+            "roofline_forward": roofline_fwd,
             "cpu_baseline": cpu,
             "clocks": clk,
-            "breakdown_ms": {"sort": t_sort, "density": t_dens, "backward": t_bwd},
+            "breakdown_ms": {"sort": t_sort, "density": t_dens, "backward": t_bwd,
+                             "density_sweep_kernel": k_dens, "backward_sweep_kernel": k_bwd},
             "density_interactions_per_s": interactions / (t_dens * 1e-3),
             "fwd_bwd_over_fwd": (t_dens + t_bwd) / t_dens,
             "candidates": candidates, "interactions": interactions,
+            "candidates_adjoint": cand_adj, "pairs_adjoint": pairs_adj,
             "candidates_per_interaction": candidates / max(interactions, 1),
             "guard_pairs": st.guard_pairs, "wall_s_timed_loop": wall,
         }

@@ -86,6 +86,8 @@ typedef struct {
   int64_t candidates;       /* distance tests inside the sorted windows (pv_count_candidates) */
   int64_t device_bytes;     /* scratch device memory owned by the grid */
   int64_t kernel_launches;  /* kernels this grid has launched since it was created */
+  int64_t candidates_adjoint; /* adjoint windows: j with projected distance < max(H_i, H_j) */
+  int64_t pairs_adjoint;      /* pairs with r_ij < max(H_i, H_j), j = i included */
 } pv_stats;
 
 /* Allocates a grid for the given boxes (cudaMalloc on the current device).
@@ -138,7 +140,9 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
 /* Counts the distance tests of the sorted windows of the method (the
    "candidates": self-cell two-sided windows plus the pair windows of
    Section 2) for the particles sorted by the last pv_sort_cells, into
-   pv_stats.candidates.  A diagnostic pass; not needed for pv_density. */
+   pv_stats.candidates, and the corresponding counts of the adjoint sweep
+   (window and cut-off max(H_i, H_j)) into pv_stats.candidates_adjoint and
+   pv_stats.pairs_adjoint.  A diagnostic pass; not needed for the others. */
 pv_status pv_count_candidates(pv_grid* g, void* stream);
 
 /* Waits for the grid's work on `stream` and returns PV_ERR_DEVICE if a kernel
@@ -148,6 +152,22 @@ pv_status pv_grid_sync(pv_grid* g, void* stream);
 /* Fills *out (host pointer).  Synchronises the device.  Returns
    PV_ERR_DEVICE when device_flags is non-zero (out is still filled). */
 pv_status pv_grid_stats(pv_grid* g, pv_stats* out);
+
+/* Per-kernel timing of the two sweeps (a measurement aid; the paper has no
+   counterpart).  With enable != 0, every later pv_density and
+   pv_density_backward call records a pair of CUDA events on its stream
+   around its cell-centric sweep kernel (the kernel that evaluates the pair
+   windows of Section 2 for the cells that fit on chip), which adds no device
+   work.  enable = 0 stops recording; both calls reset the totals.  Creates its
+   events on the first call.  Errors: PV_ERR_INVALID_ARGUMENT for g == NULL,
+   PV_ERR_CUDA if an event cannot be created. */
+pv_status pv_grid_time_sweeps(pv_grid* g, int enable);
+
+/* Waits for the recorded event pairs (host-synchronous) and returns, per
+   sweep (index 0: density, 1: adjoint), the summed kernel time in
+   milliseconds in ms[2] and the number of timed launches in launches[2]
+   (host arrays; either may be NULL).  The totals then restart from zero. */
+pv_status pv_grid_sweep_times(pv_grid* g, double* ms, int64_t* launches);
 
 /* No-allocation variant of pv_sort_cells + pv_density for ONE periodic box.
    The paper has no counterpart; this exists for callers that may not

@@ -21,6 +21,13 @@ struct pv_grid {
   bool sorted = false;
   size_t bytes = 0;
   int64_t launches = 0;  // kernels launched by this grid so far
+  // sweep timing (pv_grid_time_sweeps): a ring of event pairs per sweep kind
+  static constexpr int kRing = 64;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;      // 2 kinds x kRing x {start, stop}
+  int head[2] = {0, 0}, pending[2] = {0, 0};
+  double ms[2] = {0.0, 0.0};
+  int64_t timed[2] = {0, 0};
 };
 
 namespace {
@@ -57,9 +64,38 @@ pv_status dev_alloc(pv_grid* g, T** p, size_t count) {
     if (s_ != PV_OK) return s_;     \
   } while (0)
 
+// Folds the oldest pending event pair of `kind` into the totals.
+pv_status retire_oldest(pv_grid* g, int kind) {
+  const int slot = (g->head[kind] - g->pending[kind] + pv_grid::kRing) % pv_grid::kRing;
+  cudaEvent_t a = g->ev[(kind * pv_grid::kRing + slot) * 2];
+  cudaEvent_t b = g->ev[(kind * pv_grid::kRing + slot) * 2 + 1];
+  PV_CUDA(cudaEventSynchronize(b));
+  float t = 0.0f;
+  PV_CUDA(cudaEventElapsedTime(&t, a, b));
+  g->ms[kind] += t;
+  g->timed[kind] += 1;
+  g->pending[kind] -= 1;
+  return PV_OK;
+}
+
+// The next event pair of `kind` (nullptrs when timing is off).
+pv_status next_pair(pv_grid* g, int kind, cudaEvent_t* a, cudaEvent_t* b) {
+  *a = *b = nullptr;
+  if (!g->timing) return PV_OK;
+  if (g->pending[kind] == pv_grid::kRing) PV_TRY(retire_oldest(g, kind));
+  const int slot = g->head[kind];
+  *a = g->ev[(kind * pv_grid::kRing + slot) * 2];
+  *b = g->ev[(kind * pv_grid::kRing + slot) * 2 + 1];
+  g->head[kind] = (slot + 1) % pv_grid::kRing;
+  g->pending[kind] += 1;
+  return PV_OK;
+}
+
 void free_all(pv_grid* g) {
   for (void* p : g->allocs) cudaFree(p);
   g->allocs.clear();
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  g->ev.clear();
 }
 
 pv_status build(pv_grid* g, const pv_grid_desc* desc) {
@@ -157,10 +193,10 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   d.ccell_next = sc + 7;
   d.n_tcells = sc + 8;
   unsigned long long* cnt;
-  PV_TRY(dev_alloc(g, &cnt, 4));
+  PV_TRY(dev_alloc(g, &cnt, 8));
   d.counters = cnt;
   PV_CUDA(cudaMemset(sc, 0, 16 * sizeof(int32_t)));
-  PV_CUDA(cudaMemset(cnt, 0, 4 * sizeof(unsigned long long)));
+  PV_CUDA(cudaMemset(cnt, 0, 8 * sizeof(unsigned long long)));
   if (N) {
     PV_CUDA(cudaMemset(d.acc, 0, 3 * N * sizeof(long long)));
     PV_CUDA(cudaMemset(d.gacc, 0, 5 * N * sizeof(long long)));
@@ -250,7 +286,9 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
   // ntask, task_next, n_ccells, ccell_next, n_tcells
   PV_CUDA(cudaMemsetAsync(d.ntask, 0, 5 * sizeof(int32_t), st));
   PV_CUDA(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned long long), st));
-  PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, st));
+  cudaEvent_t t0, t1;
+  PV_TRY(next_pair(g, 0, &t0, &t1));
+  PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, st, t0, t1));
   g->launches += g->n > 0 ? 5 : 0;  // plan_slots, plan_cells, cells, tasks, finalize_t
   return PV_OK;
 }
@@ -263,7 +301,9 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GridDev& d = g->d;
   PV_CUDA(cudaMemsetAsync(d.ntask, 0, 5 * sizeof(int32_t), st));
-  PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, st));
+  cudaEvent_t t0, t1;
+  PV_TRY(next_pair(g, 1, &t0, &t1));
+  PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, st, t0, t1));
   g->launches += g->n > 0 ? 6 : 0;  // prep, plan_slots, plan_cells, cells, tasks, finalize_t
   return PV_OK;
 }
@@ -272,9 +312,9 @@ pv_status pv_count_candidates(pv_grid* g, void* stream) {
   if (!g) return PV_ERR_INVALID_ARGUMENT;
   if (!g->sorted) return PV_ERR_NOT_SORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  PV_CUDA(cudaMemsetAsync(g->d.counters + 2, 0, sizeof(unsigned long long), st));
+  PV_CUDA(cudaMemsetAsync(g->d.counters + 2, 0, 3 * sizeof(unsigned long long), st));
   PV_CUDA(pv::launch_count_candidates(g->d, st));
-  g->launches += 1;
+  g->launches += 2;
   return PV_OK;
 }
 
@@ -290,7 +330,7 @@ pv_status pv_grid_stats(pv_grid* g, pv_stats* out) {
   if (!g || !out) return PV_ERR_INVALID_ARGUMENT;
   PV_CUDA(cudaDeviceSynchronize());
   int32_t sc[4];
-  unsigned long long cnt[4];
+  unsigned long long cnt[8];
   PV_CUDA(cudaMemcpy(sc, g->d.flags, sizeof(sc), cudaMemcpyDeviceToHost));
   PV_CUDA(cudaMemcpy(cnt, g->d.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
   std::memset(out, 0, sizeof(*out));
@@ -301,9 +341,46 @@ pv_status pv_grid_stats(pv_grid* g, pv_stats* out) {
   out->interactions = (int64_t)cnt[0];
   out->guard_pairs = (int64_t)cnt[1];
   out->candidates = (int64_t)cnt[2];
+  out->candidates_adjoint = (int64_t)cnt[3];
+  out->pairs_adjoint = (int64_t)cnt[4];
   out->device_bytes = (int64_t)g->bytes;
   out->kernel_launches = g->launches;
   return out->device_flags ? PV_ERR_DEVICE : PV_OK;
+}
+
+pv_status pv_grid_time_sweeps(pv_grid* g, int enable) {
+  if (!g) return PV_ERR_INVALID_ARGUMENT;
+  if (enable && g->ev.empty()) {
+    g->ev.assign(2 * pv_grid::kRing * 2, nullptr);
+    for (auto& e : g->ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) {
+        for (auto& f : g->ev)
+          if (f) cudaEventDestroy(f);
+        g->ev.clear();
+        return cuda_fail(r, "cudaEventCreate");
+      }
+    }
+  }
+  for (int k = 0; k < 2; k++)
+    while (g->pending[k]) PV_TRY(retire_oldest(g, k));
+  g->timing = enable != 0 && !g->ev.empty();
+  g->ms[0] = g->ms[1] = 0.0;
+  g->timed[0] = g->timed[1] = 0;
+  return PV_OK;
+}
+
+pv_status pv_grid_sweep_times(pv_grid* g, double* ms, int64_t* launches) {
+  if (!g) return PV_ERR_INVALID_ARGUMENT;
+  for (int k = 0; k < 2; k++)
+    while (g->pending[k]) PV_TRY(retire_oldest(g, k));
+  for (int k = 0; k < 2; k++) {
+    if (ms) ms[k] = g->ms[k];
+    if (launches) launches[k] = g->timed[k];
+    g->ms[k] = 0.0;
+    g->timed[k] = 0;
+  }
+  return PV_OK;
 }
 
 }  // extern "C"

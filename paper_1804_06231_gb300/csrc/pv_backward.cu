@@ -522,7 +522,8 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
 }  // namespace
 
 cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g_drho_dh,
-                            float* g_pos, float* g_h, int num_sms, cudaStream_t st) {
+                            float* g_pos, float* g_h, int num_sms, cudaStream_t st,
+                            cudaEvent_t t0, cudaEvent_t t1) {
   if (g.n == 0) return cudaSuccess;
   static bool attr_set = false;
   if (!attr_set) {
@@ -537,8 +538,10 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   if (e != cudaSuccess) return e;
   if ((e = launch_plan(g, 1, kCellSmem - kCellFixedSmem, kElemJ, kElemA, st)) != cudaSuccess)
     return e;
+  if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
   k_backward_cells<<<num_sms * 2, kCellThreads, kCellSmem, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
   k_backward_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_bwd_finalize_t<<<num_sms * 2, 256, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);

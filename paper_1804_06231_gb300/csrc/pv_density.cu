@@ -639,6 +639,66 @@ __global__ void k_count_candidates(GridDev g) {
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&g.counters[2], cnt);
 }
 
+// Counts of the adjoint sweep (diagnostic): one warp per (cell a, slot o),
+// lanes over the particles of a.  For each particle i, the particles j of the
+// sorted window whose projected distance is below max(H_i, H_j)
+// ("candidates", counters[3]) and those with r_ij < max(H_i, H_j) (counters[4]),
+// j = i included.
+__global__ void k_count_adjoint(GridDev g) {
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  unsigned long long cand = 0, pairs = 0;
+  if (wid < g.ncell * kNSlot && !*g.flags) {
+    const int a = wid / kNSlot, o = wid % kNSlot;
+    const int na = g.cell_count[a];
+    const int b = na ? neighbour_cell(g, a, o) : a;
+    const int nb = g.cell_count[b];
+    if (na && nb) {
+      const BoxDev& B = g.boxes[g.cell_box[a]];
+      const Slot sl = slot_info(o);
+      const int ca = g.cell_start[a], cb = g.cell_start[b];
+      const size_t kb = (size_t)sl.k * g.n;
+      const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
+      const float Hmb = g.cell_Hmax[b];
+      for (int p = lane; p < na; p += 32) {
+        const int pos = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
+        const int si = ca + g.perm[kb + ca + pos];
+        const float Hi = g.gamma * g.hs[si];
+        const float di = sl.s * g.dist[kb + ca + pos];
+        const float4 xi = g.xm[si];
+        const float x = xi.x - sl.ox * B.edge_f, y = xi.y - sl.oy * B.edge_f,
+                    z = xi.z - sl.oz * B.edge_f;
+        const float R0 = fmaxf(Hi, Hmb);
+        int j = 0, j1 = nb;
+        if (o == kSelfSlot) {
+          j = upper_bound_f(g.dist + cb, nb, di - R0);
+          j1 = lower_bound_f(g.dist + cb, nb, di + R0);
+        }
+        for (; j < j1; j++) {
+          const float dj = proj_asc(g, sl.k, sl.s, cb, nb, j, off);
+          if (dj - di >= R0) break;
+          const int sj = cb + g.perm[kb + cb + order_pos(sl.s, j, nb)];
+          const float R = fmaxf(Hi, g.gamma * g.hs[sj]);
+          if (fabsf(dj - di) < R) {
+            cand++;
+            const float4 xj = g.xm[sj];
+            const float dx = x - xj.x, dy = y - xj.y, dz = z - xj.z;
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R * R) pairs++;
+          }
+        }
+      }
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    cand += __shfl_xor_sync(0xffffffffu, cand, s);
+    pairs += __shfl_xor_sync(0xffffffffu, pairs, s);
+  }
+  if (lane == 0) {
+    if (cand) atomicAdd(&g.counters[3], cand);
+    if (pairs) atomicAdd(&g.counters[4], pairs);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
@@ -656,7 +716,7 @@ int64_t max_tasks_for(int64_t n, int64_t ncell) {
 }
 
 cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t* n_ngb,
-                           int num_sms, cudaStream_t st) {
+                           int num_sms, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
   if (g.n == 0) return cudaSuccess;
   static bool attr_set = false;
   if (!attr_set) {
@@ -667,8 +727,10 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
   }
   cudaError_t e = launch_plan(g, 0, kCellSmem - kCellFixedSmem, kCellElemJ, kCellElemA, st);
   if (e != cudaSuccess) return e;
+  if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
   k_density_cells<<<num_sms * 3, kCellThreads, kCellSmem, st>>>(g, rho, drho_dh, n_ngb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
   k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_finalize_t<<<num_sms * 2, 256, 0, st>>>(g, rho, drho_dh, n_ngb);
@@ -679,6 +741,9 @@ cudaError_t launch_count_candidates(const GridDev& g, cudaStream_t st) {
   const int nthr = g.ncell * kNSlot;
   if (nthr == 0) return cudaSuccess;
   k_count_candidates<<<(nthr + 255) / 256, 256, 0, st>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_count_adjoint<<<(nthr * 32 + 255) / 256, 256, 0, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -94,7 +94,8 @@ struct GridDev {
   uint32_t* flags;
   float* m_max;     // [n_boxes] largest mass of each box (mass unit of the accumulators)
   int32_t* max_count;
-  unsigned long long* counters;  // [0] interactions, [1] guard pairs, [2] candidates
+  unsigned long long* counters;  // [0] interactions, [1] guard pairs, [2] candidates,
+                                 // [3] adjoint candidates, [4] adjoint pairs
 };
 
 // ---- direction slots ------------------------------------------------------
@@ -295,10 +296,14 @@ cudaError_t launch_sort(const GridDev& g, cudaStream_t st);
 cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
                         cudaStream_t st);
 int64_t max_tasks_for(int64_t n, int64_t ncell);
+// t0/t1 (optional): events recorded on `st` just before and after the
+// cell-centric sweep kernel.
 cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t* n_ngb,
-                           int num_sms, cudaStream_t st);
+                           int num_sms, cudaStream_t st, cudaEvent_t t0 = nullptr,
+                           cudaEvent_t t1 = nullptr);
 cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g_drho_dh,
-                            float* g_pos, float* g_h, int num_sms, cudaStream_t st);
+                            float* g_pos, float* g_h, int num_sms, cudaStream_t st,
+                            cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 cudaError_t launch_count_candidates(const GridDev& g, cudaStream_t st);
 
 }  // namespace pv

@@ -30,7 +30,8 @@ GAMMA = 1.825742
 #: Every symbol ``include/pv.h`` declares.
 EXPORTS = ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
            "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
-           "pv_status_str", "pv_last_cuda_error", "pv_density_static")
+           "pv_status_str", "pv_last_cuda_error", "pv_density_static", "pv_grid_time_sweeps",
+           "pv_grid_sweep_times")
 STATIC_MAX_PARTICLES = 65536
 STATIC_MAX_CELLS = 4096
 
@@ -59,7 +60,8 @@ class pv_stats(ctypes.Structure):
                 ("max_cell_count", ctypes.c_int32), ("device_flags", ctypes.c_uint32),
                 ("interactions", ctypes.c_int64), ("guard_pairs", ctypes.c_int64),
                 ("candidates", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("candidates_adjoint", ctypes.c_int64),
+                ("pairs_adjoint", ctypes.c_int64)]
 
 
 _lib = None
@@ -83,8 +85,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pv_count_candidates.argtypes = [vp, vp]
     lib.pv_grid_sync.argtypes = [vp, vp]
     lib.pv_grid_stats.argtypes = [vp, ctypes.POINTER(pv_stats)]
+    lib.pv_grid_time_sweeps.argtypes = [vp, i32]
+    lib.pv_grid_sweep_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64)]
     for name in ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
-                 "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats"):
+                 "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
+                 "pv_grid_time_sweeps", "pv_grid_sweep_times"):
         getattr(lib, name).restype = i32
     lib.pv_status_str.argtypes = [i32]
     lib.pv_status_str.restype = ctypes.c_char_p
@@ -160,6 +166,18 @@ def pv_density_static(pos: int, h: int, m: int | None, m_uniform: float, n: int,
                                             n_ngb, flags_out, stream), "pv_density_static")
 
 
+def pv_grid_time_sweeps(grid: int, enable: bool) -> None:
+    _check(load_library().pv_grid_time_sweeps(grid, 1 if enable else 0), "pv_grid_time_sweeps")
+
+
+def pv_grid_sweep_times(grid: int):
+    """((ms density, ms adjoint), (launches density, launches adjoint)) since the last reset."""
+    ms = (ctypes.c_double * 2)()
+    nl = (ctypes.c_int64 * 2)()
+    _check(load_library().pv_grid_sweep_times(grid, ms, nl), "pv_grid_sweep_times")
+    return (ms[0], ms[1]), (nl[0], nl[1])
+
+
 @dataclass
 class Stats:
     n_particles: int
@@ -171,6 +189,8 @@ class Stats:
     candidates: int
     device_bytes: int
     kernel_launches: int
+    candidates_adjoint: int
+    pairs_adjoint: int
 
 
 def pv_grid_stats(grid: int, raise_on_flags: bool = True) -> Stats:
@@ -281,6 +301,15 @@ class Grid:
 
     def sync(self, stream=None) -> None:
         pv_grid_sync(self.handle, self._stream(stream))
+
+    def time_sweeps(self, enable: bool = True) -> None:
+        """Start (or stop) timing the sweep kernels with CUDA events; resets the totals."""
+        pv_grid_time_sweeps(self.handle, enable)
+
+    def sweep_times(self):
+        """Mean sweep-kernel time in ms per launch: (density, adjoint); NaN if none."""
+        (a, b), (na, nb) = pv_grid_sweep_times(self.handle)
+        return (a / na if na else float("nan"), b / nb if nb else float("nan"))
 
     def stats(self, raise_on_flags: bool = True) -> Stats:
         return pv_grid_stats(self.handle, raise_on_flags)

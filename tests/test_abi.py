@@ -44,7 +44,7 @@ def test_struct_layout_matches_header():
     assert ctypes.sizeof(pv.pv_box_desc) == 32
     assert pv.pv_box_desc.nc.offset == 24
     assert ctypes.sizeof(pv.pv_grid_desc) == 32
-    assert ctypes.sizeof(pv.pv_stats) == 64
+    assert ctypes.sizeof(pv.pv_stats) == 80
 
 
 def test_argument_errors_return_before_device_work(lib):
@@ -68,6 +68,8 @@ def test_argument_errors_return_before_device_work(lib):
     assert lib.pv_count_candidates(None, None) == 1
     assert lib.pv_grid_sync(None, None) == 1
     assert lib.pv_grid_stats(None, None) == 1
+    assert lib.pv_grid_time_sweeps(None, 1) == 1
+    assert lib.pv_grid_sweep_times(None, None, None) == 1
     assert lib.pv_grid_destroy(None) == 0
 
 

@@ -5,6 +5,8 @@ Bar: rho within 1e-5 relative; drho/dh within 1e-4 of S_i = sum_j m_j |dW/dh|
 ill-conditioned); n_i bit-exact except where the oracle finds a pair within
 1e-6 relative of the cut-off, where the difference is bounded by that count.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -142,6 +144,16 @@ def test_candidates_match_oracle_windows(oracle_lib):
     assert cand == pytest.approx(int(ref.counters[:, 0].sum()), rel=1e-5)
 
 
+def test_adjoint_counts_match_oracle(oracle_lib):
+    """The adjoint window and pair counts (cut-off max(H_i, H_j)) of the
+    diagnostic pass equal the oracle's, up to pairs at the FP32 boundary."""
+    for box in (I.uniform(30000, 8, nc=8), I.clustered(20000, 9, nc=3)):
+        _, _, _, st, _ = run_density(box, count_candidates=True)
+        cand, pairs = oracle_lib.adjoint_counts(box.pos, box.h, 1.0, box.nc)
+        assert st.candidates_adjoint == pytest.approx(cand, rel=1e-5)
+        assert st.pairs_adjoint == pytest.approx(pairs, rel=1e-5)
+
+
 @pytest.mark.slow
 def test_uniform_1m_headline_sampled(oracle_lib):
     """N = 1,048,576 at 15^3 cells (the benchmark's launch configuration): all
@@ -152,3 +164,32 @@ def test_uniform_1m_headline_sampled(oracle_lib):
     check_density(rho, D, n, ref)
     assert st.interactions == int(ref.n_ngb.sum()) or \
         abs(st.interactions - int(ref.n_ngb.sum())) <= int(ref.band.sum())
+
+
+def test_sweep_timing_hooks():
+    """pv_grid_time_sweeps records one event pair per sweep call; the per-launch
+    times are positive and below the time of the whole call sequence."""
+    import time
+    import torch
+    from paper_1804_06231_gb300.pv import Grid
+    box = I.uniform(100000, 31, nc=10)
+    dev = torch.device("cuda", 0)
+    pos = torch.from_numpy(box.pos).to(dev)
+    h = torch.from_numpy(box.h).to(dev)
+    gr = torch.ones(box.n, device=dev)
+    with Grid((box.n, 1.0, box.nc)) as g:
+        g.sort(pos, h, None, float(box.m[0]))
+        g.time_sweeps(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(70):  # more calls than the event ring holds
+            g.density()
+            g.backward(gr, gr)
+        torch.cuda.synchronize()
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        td, tb = g.sweep_times()
+        assert 0 < td and 0 < tb and 70 * (td + tb) < wall_ms
+        assert all(math.isnan(t) for t in g.sweep_times())  # totals were reset
+        g.time_sweeps(False)
+        g.density()
+        assert all(math.isnan(t) for t in g.sweep_times())
