@@ -246,6 +246,7 @@ def main():
 
     from paper_1804_06231_gb300 import build as B
     B.build_library()
+    from paper_1804_06231_gb300 import shard
     from paper_1804_06231_gb300.pv import Grid
 
     if ws > 1:
@@ -327,15 +328,9 @@ def main():
     st = grid.stats()
     assert st.device_flags == 0
 
-    t_max = t_step
-    tot_inter = interactions
-    if ws > 1:
-        t = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        c = torch.tensor([interactions], device=dev, dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        tot_inter = int(c.item())
+    # one independent box per rank: only the totals are reduced
+    tot_inter, t_max = shard.step_totals(interactions, t_step, dev)
+    tot_inter = int(tot_inter)
     value = tot_inter / (t_max * 1e-3)
 
     # ---- end to end through the C ABI with host buffers (pinned)
@@ -371,11 +366,7 @@ def main():
             b.synchronize()
             if k >= 2:
                 times.append(a.elapsed_time(b))
-        t_e2e = statistics.mean(times)
-        if ws > 1:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = shard.step_totals(0, statistics.mean(times), dev)[1]
         e2e = {"value": tot_inter / (t_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "ms_per_step": t_e2e}
 
