@@ -82,34 +82,36 @@ __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
   g.ghh[s] = make_float2(1.0f / H, H);
 }
 
+// Half-scaled kernel factors of the adjoint, without branches.  With
+// s = max(1 - q, 0) and t = max(1/2 - q, 0) the cubic spline is
+// w = s^3 - 4 t^3 (half-scaled), so every factor is a piece in s minus four
+// times the same piece in t:
+//   th = 3w + q w'                = s^2 (3 - 6q) - t^2 (6 - 24q)
+//   uh = 12w + 8q w' + q^2 w''    = A(s) - 4 A(t),  A(x) = x (12x^2 - 24qx + 6q^2)
+//   vr = w'/q                     = (12 t^2 - 3 s^2) / q
+//   vh = (4w' + q w'')/q          = 4 vr + 6s - 24t
+// For q < 1/2 the numerator of vr is formed as q (9q - 6) (the same
+// polynomial), which keeps vr accurate as q -> 0.
+__device__ __forceinline__ float vr_half(float q, float qinv, float s) {
+  const float core = q < 0.5f ? q * fmaf(9.0f, q, -6.0f) : -3.0f * s * s;
+  return core * qinv;
+}
+
 __device__ __forceinline__ void spline_bwd(float q, float qinv, float& th, float& uh, float& vr,
                                            float& vh) {
-  const float q2 = q * q;
-  const float s = fmaxf(1.0f - q, 0.0f);
-  const float s2 = s * s;
-  if (q < 0.5f) {
-    th = fmaf(q2, fmaf(18.0f, q, -15.0f), 1.5f);
-    uh = fmaf(q2, fmaf(126.0f, q, -90.0f), 6.0f);
-    vr = fmaf(9.0f, q, -6.0f);
-    vh = fmaf(54.0f, q, -30.0f);
-  } else {
-    th = s2 * fmaf(-6.0f, q, 3.0f);
-    uh = 6.0f * s * fmaf(7.0f * s, s, fmaf(-6.0f, s, 1.0f));
-    vr = -3.0f * s2 * qinv;
-    vh = fmaf(-12.0f * s2, qinv, 6.0f * s);
-  }
+  const float s = fmaxf(1.0f - q, 0.0f), t = fmaxf(0.5f - q, 0.0f);
+  const float s2 = s * s, t2 = t * t;
+  th = fmaf(s2, fmaf(-6.0f, q, 3.0f), -t2 * fmaf(-24.0f, q, 6.0f));
+  const float q6 = 6.0f * q * q;
+  uh = fmaf(s, fmaf(12.0f * s, s - 2.0f * q, q6), -4.0f * t * fmaf(12.0f * t, t - 2.0f * q, q6));
+  vr = vr_half(q, qinv, s);
+  vh = fmaf(4.0f, vr, fmaf(6.0f, s, -24.0f * t));
 }
 
 __device__ __forceinline__ void spline_bwd_v(float q, float qinv, float& vr, float& vh) {
-  const float s = fmaxf(1.0f - q, 0.0f);
-  const float s2 = s * s;
-  if (q < 0.5f) {
-    vr = fmaf(9.0f, q, -6.0f);
-    vh = fmaf(54.0f, q, -30.0f);
-  } else {
-    vr = -3.0f * s2 * qinv;
-    vh = fmaf(-12.0f * s2, qinv, 6.0f * s);
-  }
+  const float s = fmaxf(1.0f - q, 0.0f), t = fmaxf(0.5f - q, 0.0f);
+  vr = vr_half(q, qinv, s);
+  vh = fmaf(4.0f, vr, fmaf(6.0f, s, -24.0f * t));
 }
 
 __device__ __forceinline__ float warp_min_b(float v) {
@@ -166,6 +168,23 @@ __device__ __forceinline__ void laneb_set(LaneB& L, const GridDev& g, const BoxD
 
 constexpr int kMaskChunks = 8;  // 32-candidate chunks per segment of the sweep
 
+// Adds the own (scaled by mo = m_j or 0) and transposed (mt = m_i or 0) terms
+// of the pair (i, j) to lane i's five sums.
+__device__ __forceinline__ void bwd_pair(LaneB& L, float dx, float dy, float dz, float r2,
+                                         float4 aj, float mo, float mt) {
+  const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+  const float r = r2 * rinv;
+  float th, uh, vr, vh, vrj, vhj;
+  spline_bwd(r * L.Hinv, L.H * rinv, th, uh, vr, vh);
+  spline_bwd_v(r * __fdividef(1.0f, aj.w), aj.w * rinv, vrj, vhj);
+  L.Sth = fmaf(mo, th, L.Sth);
+  L.Suh = fmaf(mo, uh, L.Suh);
+  const float cc = fmaf(mo, fmaf(L.G, vr, -L.K * vh), mt * fmaf(aj.y, vrj, -aj.z * vhj));
+  L.gx = fmaf(cc, dx, L.gx);
+  L.gy = fmaf(cc, dy, L.gy);
+  L.gz = fmaf(cc, dz, L.gz);
+}
+
 // Adjoint sweep over staged particles [lo, hi): Sx {x,y,z,|x|^2}, Sa {m_j, G_j,
 // K_j, H_j}; jidx(e) gives the cell-order index of staged particle e (read
 // only for FP64 re-decisions near a cut-off).  Same two passes as the forward
@@ -199,6 +218,7 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
     for (int s = 16; s > 0; s >>= 1) tot = max(tot, __shfl_xor_sync(0xffffffffu, tot, s));
     int k = 0;
     unsigned m = 0;
+    bool amb = false;
     for (int round = 0; round < tot; round++) {
       if (m == 0u && nz != 0u) {
         k = __ffs(nz) - 1;
@@ -214,31 +234,39 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
       const float4 aj = Sa[j];  // m_j, G_j, K_j, H_j
       const float gbj = guard_band(aj.w, B.edge_f);
       const float Ej = fmaf(aj.w, aj.w, gbj);
-      bool own = (c >= 0) && (r2 < L.Hsq_hi);
-      bool trans = (c >= 0) && (r2 < Ej);
-      const bool gown = own && r2 >= L.Hsq_lo;
-      const bool gtr = trans && r2 >= Ej - 2.0f * gbj;
-      if (__any_sync(0xffffffffu, gown || gtr)) {  // within rounding of a cut-off: FP64
-        if (gown || gtr) {
-          const int sj = jidx(j);
-          if (gown) own = guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, L.Hd);
-          if (gtr)
-            trans = guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, g.gamma_d * (double)g.hs[sj]);
+      // pairs within rounding of a cut-off count as in range here and are
+      // re-decided in FP64 after the rounds
+      const bool own = (c >= 0) && (r2 < L.Hsq_hi);
+      const bool trans = (c >= 0) && (r2 < Ej);
+      amb |= (own && r2 >= L.Hsq_lo) || (trans && r2 >= Ej - 2.0f * gbj);
+      bwd_pair(L, dx, dy, dz, r2, aj, own ? aj.x : 0.0f, trans ? L.m : 0.0f);
+    }
+    if (__any_sync(0xffffffffu, amb)) {
+      if (amb) {
+        for (int kk = 0; kk < nk; kk++) {
+          unsigned mm = M[kk * 32 + lane];
+          while (mm != 0u) {
+            const int j = seg + 32 * kk + __ffs(mm) - 1;
+            mm &= mm - 1u;
+            const float4 q = Sx[j];
+            const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float4 aj = Sa[j];
+            const float gbj = guard_band(aj.w, B.edge_f);
+            const float Ej = fmaf(aj.w, aj.w, gbj);
+            const bool gown = r2 < L.Hsq_hi && r2 >= L.Hsq_lo;
+            const bool gtr = r2 < Ej && r2 >= Ej - 2.0f * gbj;
+            if (gown || gtr) {
+              const int sj = jidx(j);
+              const bool out_o = gown && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, L.Hd);
+              const bool out_t = gtr && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L,
+                                                     g.gamma_d * (double)g.hs[sj]);
+              if (out_o || out_t)
+                bwd_pair(L, dx, dy, dz, r2, aj, out_o ? -aj.x : 0.0f, out_t ? -L.m : 0.0f);
+            }
+          }
         }
       }
-      const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-      const float r = r2 * rinv;
-      float th, uh, vr, vh, vrj, vhj;
-      spline_bwd(r * L.Hinv, L.H * rinv, th, uh, vr, vh);
-      spline_bwd_v(r * __fdividef(1.0f, aj.w), aj.w * rinv, vrj, vhj);
-      const float mo = own ? aj.x : 0.0f;
-      L.Sth = fmaf(mo, th, L.Sth);
-      L.Suh = fmaf(mo, uh, L.Suh);
-      const float mt = trans ? L.m : 0.0f;
-      const float cc = fmaf(mo, fmaf(L.G, vr, -L.K * vh), mt * fmaf(aj.y, vrj, -aj.z * vhj));
-      L.gx = fmaf(cc, dx, L.gx);
-      L.gy = fmaf(cc, dy, L.gy);
-      L.gz = fmaf(cc, dz, L.gz);
     }
   }
 }
@@ -280,17 +308,6 @@ constexpr int kCellFixedSmem = kCellWarps * kMaskChunks * 32 * 4;  // the warps'
 
 __device__ __forceinline__ float sproj(float4 x, float ux, float uy, float uz, int s, float off) {
   return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
-}
-
-__device__ __forceinline__ int sbound(const float4* S, int len, float v, bool strict, float ux,
-                                      float uy, float uz, int s, float off) {
-  int lo = 0, hi = len;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const float d = sproj(S[mid], ux, uy, uz, s, off);
-    if (strict ? (d <= v) : (d < v)) lo = mid + 1; else hi = mid;
-  }
-  return lo;
 }
 
 __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
@@ -366,7 +383,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
       if (lane == 0) it = atomicAdd(&cs.item_next, 1);
       it = __shfl_sync(0xffffffffu, it, 0);
       if (it >= nitems) break;
-      const int q = seg_of(cs.runs, kNSlot, it);
+      const int q = warp_seg_of(cs.runs, kNSlot, it, lane);
       const int o = c_border[q];
       const Slot sl = slot_info(o);
       float ux, uy, uz;
@@ -394,10 +411,13 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
       const float w_lo = warp_min_b(d_lo), w_hi = warp_max_b(d_hi);
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
       const float offv = cs.offv[q];
-      const int lo = s0 + ((o == kSelfSlot)
-                               ? sbound(Sx + s0, len, w_lo, true, ux, uy, uz, sl.s, offv)
-                               : 0);
-      const int hi = s0 + sbound(Sx + s0, len, w_hi, false, ux, uy, uz, sl.s, offv);
+      const int lo = s0 + ((o == kSelfSlot) ? warp_first_true(len, lane, [&](int e) {
+                             return sproj(Sx[s0 + e], ux, uy, uz, sl.s, offv) > w_lo;
+                           })
+                                            : 0);
+      const int hi = s0 + warp_first_true(len, lane, [&](int e) {
+                       return sproj(Sx[s0 + e], ux, uy, uz, sl.s, offv) >= w_hi;
+                     });
       const int J0q = cs.J0[q], nbq = cs.nb_[q], cbq = cs.cb_[q];
       const size_t kbq = (size_t)sl.k * g.n + cbq;
       auto jidx = [&](int j) {

@@ -222,6 +222,21 @@ __device__ __forceinline__ void lane_set(LaneI& L, const GridDev& g, const BoxDe
 
 constexpr int kMaskChunks = 8;  // 32-candidate chunks per segment of the sweep
 
+// exact FP32 r^2 between lane i and a staged particle {x, y, z, |x|^2}
+__device__ __forceinline__ float pair_r2(const LaneI& L, float4 q) {
+  const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// adds mj times the half-scaled kernel terms of the pair to lane i's sums
+__device__ __forceinline__ void fwd_pair(LaneI& L, float r2, float mj) {
+  const float qq = sqrt_approx(r2 * L.Hinv2);
+  float wh, th;
+  spline_half(qq, wh, th);
+  L.rho = fmaf(mj, wh, L.rho);
+  L.D = fmaf(mj, th, L.D);
+}
+
 // Sweeps the staged particles [lo, hi) for the warp's 32 particles.  Sx holds
 // {x, y, z, |x|^2} of each staged particle and Sm its mass; jidx(e) returns the
 // cell-order index of staged particle e (read only for the rare FP64
@@ -257,11 +272,13 @@ __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ S
       nz |= (m != 0u ? 1u : 0u) << k;
       tot += __popc(m);
     }
-    // pass 2: as many rounds as the busiest lane has hits; no divergent
-    // branches except the (warp-uniform) FP64 re-decision near the cut-off
+    // pass 2: as many rounds as the busiest lane has hits, without divergent
+    // branches.  A hit whose FP32 r^2 lies within rounding of H_i^2 is taken
+    // as in range here and re-decided in FP64 after the rounds.
     for (int s = 16; s > 0; s >>= 1) tot = max(tot, __shfl_xor_sync(0xffffffffu, tot, s));
     int k = 0;
     unsigned m = 0;
+    bool amb = false;
     for (int round = 0; round < tot; round++) {
       if (m == 0u && nz != 0u) {
         k = __ffs(nz) - 1;
@@ -271,24 +288,32 @@ __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ S
       const int c = __ffs(m) - 1;  // -1: this lane has no hit left
       m &= m - 1u;
       const int j = seg + 32 * k + max(c, 0);
-      const float4 q = Sx[j];
-      const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      bool in = (c >= 0) && (r2 < L.Hsq_hi);
-      const bool grd = in && (r2 >= L.Hsq_lo);
-      if (__any_sync(0xffffffffu, grd)) {  // within rounding of the cut-off: FP64
-        if (grd) {
-          in = guard_inside(g.pos64, L.si, jidx(j), B.L, B.inv_L, L.Hd);
-          guards++;
+      const float r2 = pair_r2(L, Sx[j]);
+      const bool in = (c >= 0) && (r2 < L.Hsq_hi);
+      amb |= in && (r2 >= L.Hsq_lo);
+      fwd_pair(L, r2, in ? Sm[j] : 0.0f);
+      L.n += in ? 1 : 0;
+    }
+    // FP64 re-decision of the hits near the cut-off (rare): a lane walks its
+    // hits of the segment again and takes back the pairs that are out of range
+    if (__any_sync(0xffffffffu, amb)) {
+      if (amb) {
+        for (int kk = 0; kk < nk; kk++) {
+          unsigned mm = M[kk * 32 + lane];
+          while (mm != 0u) {
+            const int j = seg + 32 * kk + __ffs(mm) - 1;
+            mm &= mm - 1u;
+            const float r2 = pair_r2(L, Sx[j]);
+            if (r2 < L.Hsq_hi && r2 >= L.Hsq_lo) {
+              guards++;
+              if (!guard_inside(g.pos64, L.si, jidx(j), B.L, B.inv_L, L.Hd)) {
+                fwd_pair(L, r2, -Sm[j]);
+                L.n -= 1;
+              }
+            }
+          }
         }
       }
-      const float qq = sqrt_approx(r2 * L.Hinv2);
-      float wh, th;
-      spline_half(qq, wh, th);
-      const float mj = in ? Sm[j] : 0.0f;
-      L.rho = fmaf(mj, wh, L.rho);
-      L.D = fmaf(mj, th, L.D);
-      L.n += in ? 1 : 0;
     }
   }
 }
@@ -342,18 +367,6 @@ struct CellShared {
 __device__ __forceinline__ float staged_proj(float4 x, float ux, float uy, float uz, int s,
                                              float off) {
   return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
-}
-
-// first e in [0, len) of the staged segment with projection >= v (> v if strict)
-__device__ __forceinline__ int staged_bound(const float4* S, int len, float v, bool strict,
-                                            float ux, float uy, float uz, int s, float off) {
-  int lo = 0, hi = len;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const float d = staged_proj(S[mid], ux, uy, uz, s, off);
-    if (strict ? (d <= v) : (d < v)) lo = mid + 1; else hi = mid;
-  }
-  return lo;
 }
 
 __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float* __restrict__ rho,
@@ -441,7 +454,7 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
       if (lane == 0) it = atomicAdd(&cs.item_next, 1);
       it = __shfl_sync(0xffffffffu, it, 0);
       if (it >= nitems) break;
-      const int q = seg_of(cs.runs, kNSlot, it);
+      const int q = warp_seg_of(cs.runs, kNSlot, it, lane);
       const int o = c_slot_order[q];
       const Slot sl = slot_info(o);
       float ux, uy, uz;
@@ -465,10 +478,13 @@ __global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float
       const float w_lo = warp_min(d_lo), w_hi = warp_max(d_hi);
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
       const float offv = cs.offv[q];
-      const int lo = s0 + ((o == kSelfSlot)
-                               ? staged_bound(Sx + s0, len, w_lo, true, ux, uy, uz, sl.s, offv)
-                               : 0);
-      const int hi = s0 + staged_bound(Sx + s0, len, w_hi, false, ux, uy, uz, sl.s, offv);
+      const int lo = s0 + ((o == kSelfSlot) ? warp_first_true(len, lane, [&](int e) {
+                             return staged_proj(Sx[s0 + e], ux, uy, uz, sl.s, offv) > w_lo;
+                           })
+                                            : 0);
+      const int hi = s0 + warp_first_true(len, lane, [&](int e) {
+                       return staged_proj(Sx[s0 + e], ux, uy, uz, sl.s, offv) >= w_hi;
+                     });
       const int J0q = cs.J0[q], nbq = cs.nb_[q], cbq = cs.cb_[q];
       const size_t kbq = (size_t)sl.k * g.n + cbq;
       auto jidx = [&](int j) {

@@ -217,6 +217,33 @@ __device__ __forceinline__ int seg_of(const int* a, int n, int v) {
   return lo;
 }
 
+// last t in [0, n) with a[t] <= v, for a ascending, a[0] <= v and n <= 32; the
+// whole warp calls it with the same v (one ballot instead of a search)
+__device__ __forceinline__ int warp_seg_of(const int* a, int n, int v, int lane) {
+  const bool le = lane < n && a[lane] <= v;
+  return __popc(__ballot_sync(0xffffffffu, le)) - 1;
+}
+
+// Warp-cooperative search: the first e in [0, len) with pred(e), for a
+// predicate that is false on a prefix and true after it (len if none).  The
+// whole warp calls it with the same arguments; each round probes 32 evenly
+// spaced points, so two rounds cover len <= 1024 and three len <= 32768.
+template <typename Pred>
+__device__ __forceinline__ int warp_first_true(int len, int lane, Pred pred) {
+  int lo = 0, hi = len;  // the answer lies in [lo, hi]
+  while (hi > lo) {
+    const int step = (hi - lo + 31) >> 5;
+    const int p = lo + lane * step;
+    const bool f = p < hi && !pred(p);
+    const int nf = __popc(__ballot_sync(0xffffffffu, f));  // probes before the answer
+    if (step == 1) return lo + nf;
+    if (nf == 0) return lo;
+    lo += (nf - 1) * step + 1;
+    hi = min(lo - 1 + step, hi);
+  }
+  return lo;
+}
+
 // first index t in [0, n) with a[t] >= x (a ascending), n if none
 __device__ __forceinline__ int lower_bound_f(const float* a, int n, float x) {
   int lo = 0, hi = n;
