@@ -153,6 +153,27 @@ pv_status pv_grid_sync(pv_grid* g, void* stream);
    PV_ERR_DEVICE when device_flags is non-zero (out is still filled). */
 pv_status pv_grid_stats(pv_grid* g, pv_stats* out);
 
+/* Launch shape of the two cell-centric sweep kernels (the paper has no
+   counterpart; its method is the same for every value).  The number of
+   resident CTAs per SM sets each kernel's shared memory, and with it which
+   cells are swept by the cell-centric kernel (their 27 windows fit) and which
+   by the task kernel: fewer CTAs = more shared memory per cell, more CTAs =
+   more warps to hide latency.  0 selects the default. */
+typedef struct {
+  int32_t density_ctas_per_sm;   /* 1..4 (default 3) */
+  int32_t backward_ctas_per_sm;  /* 1..2 (default 2) */
+  int32_t reserved[6];           /* must be 0 */
+} pv_tuning;
+
+/* Sets the launch shape used by later pv_density / pv_density_backward calls
+   of this grid.  Host-only, takes effect at the next call.  Errors:
+   PV_ERR_INVALID_ARGUMENT for NULL pointers, values out of range or non-zero
+   reserved fields (the grid is unchanged). */
+pv_status pv_grid_set_tuning(pv_grid* g, const pv_tuning* t);
+
+/* Writes the launch shape in use (defaults resolved) to *out (host). */
+pv_status pv_grid_get_tuning(const pv_grid* g, pv_tuning* out);
+
 /* Per-kernel timing of the two sweeps (a measurement aid; the paper has no
    counterpart).  With enable != 0, every later pv_density and
    pv_density_backward call records a pair of CUDA events on its stream

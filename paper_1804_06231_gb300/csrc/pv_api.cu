@@ -21,6 +21,7 @@ struct pv_grid {
   bool sorted = false;
   size_t bytes = 0;
   int64_t launches = 0;  // kernels launched by this grid so far
+  int ctas[2] = {pv::kDensityCtasDefault, pv::kBackwardCtasDefault};  // sweep CTAs per SM
   // sweep timing (pv_grid_time_sweeps): a ring of event pairs per sweep kind
   static constexpr int kRing = 64;
   bool timing = false;
@@ -288,7 +289,7 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
   PV_CUDA(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned long long), st));
   cudaEvent_t t0, t1;
   PV_TRY(next_pair(g, 0, &t0, &t1));
-  PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, st, t0, t1));
+  PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, g->ctas[0], st, t0, t1));
   g->launches += g->n > 0 ? 5 : 0;  // plan_slots, plan_cells, cells, tasks, finalize_t
   return PV_OK;
 }
@@ -303,7 +304,8 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
   PV_CUDA(cudaMemsetAsync(d.ntask, 0, 5 * sizeof(int32_t), st));
   cudaEvent_t t0, t1;
   PV_TRY(next_pair(g, 1, &t0, &t1));
-  PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, st, t0, t1));
+  PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, g->ctas[1], st, t0,
+                              t1));
   g->launches += g->n > 0 ? 6 : 0;  // prep, plan_slots, plan_cells, cells, tasks, finalize_t
   return PV_OK;
 }
@@ -346,6 +348,26 @@ pv_status pv_grid_stats(pv_grid* g, pv_stats* out) {
   out->device_bytes = (int64_t)g->bytes;
   out->kernel_launches = g->launches;
   return out->device_flags ? PV_ERR_DEVICE : PV_OK;
+}
+
+pv_status pv_grid_set_tuning(pv_grid* g, const pv_tuning* t) {
+  if (!g || !t) return PV_ERR_INVALID_ARGUMENT;
+  for (int r : t->reserved)
+    if (r != 0) return PV_ERR_INVALID_ARGUMENT;
+  const int d = t->density_ctas_per_sm ? t->density_ctas_per_sm : pv::kDensityCtasDefault;
+  const int b = t->backward_ctas_per_sm ? t->backward_ctas_per_sm : pv::kBackwardCtasDefault;
+  if (d < 1 || d > 4 || b < 1 || b > 2) return PV_ERR_INVALID_ARGUMENT;
+  g->ctas[0] = d;
+  g->ctas[1] = b;
+  return PV_OK;
+}
+
+pv_status pv_grid_get_tuning(const pv_grid* g, pv_tuning* out) {
+  if (!g || !out) return PV_ERR_INVALID_ARGUMENT;
+  std::memset(out, 0, sizeof(*out));
+  out->density_ctas_per_sm = g->ctas[0];
+  out->backward_ctas_per_sm = g->ctas[1];
+  return PV_OK;
 }
 
 pv_status pv_grid_time_sweeps(pv_grid* g, int enable) {

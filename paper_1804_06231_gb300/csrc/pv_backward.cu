@@ -39,9 +39,11 @@ namespace {
 constexpr int kBlkI = 128;   // must match the plan kernel
 constexpr int kTileJ = 512;
 constexpr int kCellThreads = 256;
-constexpr int kCellSmem = 100 * 1024;
+// dynamic shared memory of k_backward_cells for 1 or 2 resident CTAs per SM
+// (2 by default; its registers allow no more)
+constexpr int kCellSmemFor[3] = {0, 200 * 1024, 110 * 1024};
 constexpr int kPad = 32;
-constexpr int kElemJ = 32;   // staged bytes per particle of a window: {x,y,z,|x|^2}, {m,G,K,H}
+constexpr int kElemJ = 36;   // staged bytes per particle of a window: {x,y,z,|x|^2}, {m,G,K,H}, E
 constexpr int kElemA = 40;   // bytes per particle of the cell: five FP64 sums
 
 __constant__ int8_t c_border[kNSlot] = {13, 4,  10, 12, 14, 16, 22, 1,  3,  5,  7,  9, 11, 15,
@@ -185,15 +187,32 @@ __device__ __forceinline__ void bwd_pair(LaneB& L, float dx, float dy, float dz,
   L.gz = fmaf(cc, dz, L.gz);
 }
 
+// Pre-filter of 8 staged candidates for the adjoint: shifts the sign of
+// |x_j|^2 - 2 x_i.x_j - max(ci, di + E_j) into `m`, first candidate first, so
+// a hit is a pair with r < max(H_i, H_j) up to the FP32 margin (ci covers
+// H_i^2 + guard, E_j = H_j^2 + guard_j).
+__device__ __forceinline__ void prefilter8_bwd(unsigned& m, const float4* __restrict__ X,
+                                               const float* __restrict__ E, const LaneB& L) {
+#pragma unroll
+  for (int c = 0; c < 8; c++) {
+    const float4 q = X[c];
+    const float t = fmaxf(L.ci, L.di + E[c]);
+    const float d = fmaf(L.nx, q.x, fmaf(L.ny, q.y, fmaf(L.nz, q.z, q.w - t)));
+    m = __funnelshift_l(__float_as_uint(d), m, 1);
+  }
+}
+
 // Adjoint sweep over staged particles [lo, hi): Sx {x,y,z,|x|^2}, Sa {m_j, G_j,
-// K_j, H_j}; jidx(e) gives the cell-order index of staged particle e (read
-// only for FP64 re-decisions near a cut-off).  Same two passes as the forward
-// sweep: the pre-filter bound L.ci covers r < max(H_i, H_max of the other
-// cell), then each lane walks its own hits and applies the exact own (r < H_i)
-// and transposed (r < H_j) tests.
+// K_j, H_j}, Se {H_j^2 + guard_j}; jidx(e) gives the cell-order index of
+// staged particle e (read only for FP64 re-decisions near a cut-off).  Same
+// two passes as the forward sweep: the pre-filter keeps the candidates with
+// r < max(H_i, H_j) (the windows themselves reach max(H_i, H_max of the other
+// cell)), then each lane walks its own hits and applies the exact own
+// (r < H_i) and transposed (r < H_j) tests.
 template <typename JIndex>
 __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ Sx,
-                                          const float4* __restrict__ Sa, int lo, int hi,
+                                          const float4* __restrict__ Sa,
+                                          const float* __restrict__ Se, int lo, int hi,
                                           unsigned* __restrict__ M, int lane, const GridDev& g,
                                           const BoxDev& B, JIndex jidx) {
   for (int seg = lo; seg < hi; seg += 32 * kMaskChunks) {
@@ -206,9 +225,8 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
       const int cnt = min(32, seg_end - base);
       unsigned m = 0;
       int c0 = 0;
-      const unsigned sbase = (unsigned)__cvta_generic_to_shared(Sx + base);
 #pragma unroll 1
-      for (; c0 < cnt; c0 += 8) prefilter8(m, sbase + 16u * c0, L.nx, L.ny, L.nz, L.ci);
+      for (; c0 < cnt; c0 += 8) prefilter8_bwd(m, Sx + base + c0, Se + base + c0, L);
       m = __brev(m) >> (32 - c0);
       if (cnt < 32) m &= (1u << cnt) - 1u;
       M[k * 32 + lane] = m;
@@ -363,6 +381,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
     float4* Sx = var;                                  // [total + kPad] {x,y,z,|x|^2}
     float4* Sa = Sx + total + kPad;                    // [total + kPad] {m, G, K, H}
     double* acc = reinterpret_cast<double*>(Sa + total + kPad);  // [5][na]
+    float* Se = reinterpret_cast<float*>(acc + 5 * na);          // [total + kPad] E_j
     for (int f = tid; f < total; f += kCellThreads) {
       const int q = seg_of(cs.off, kNSlot, f);  // cs.off[q] <= f < cs.off[q+1]
       const int o = c_border[q];
@@ -374,6 +393,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
       const float4 ak = g.gk[sj];
       Sx[f] = staged_b(xj);
       Sa[f] = make_float4(xj.w, ak.x, ak.y, g.ghh[sj].y);
+      Se[f] = ak.z;  // H_j^2 + guard_j
     }
     for (int t = tid; t < 5 * na; t += kCellThreads) acc[t] = 0.0;
     __syncthreads();
@@ -404,9 +424,6 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
         const float reach = fmaxf(L.H, Hmb) + B.pad;
         d_lo = di - reach;
         d_hi = di + reach;
-        // one pre-filter bound for both cut-offs: r < max(H_i, H_max of b)
-        const float Hb = fmaxf(L.H, Hmb);
-        L.ci = fmaxf(L.ci, L.di + Hb * Hb + guard_band(Hb, B.edge_f));
       }
       const float w_lo = warp_min_b(d_lo), w_hi = warp_max_b(d_hi);
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
@@ -423,7 +440,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
       auto jidx = [&](int j) {
         return cbq + (int)g.perm[kbq + order_pos(sl.s, J0q + j - s0, nbq)];
       };
-      sweep_bwd(L, Sx, Sa, lo, hi, Mw, lane, g, B, jidx);
+      sweep_bwd(L, Sx, Sa, Se, lo, hi, Mw, lane, g, B, jidx);
       if (valid) {
         atomicAdd(&acc[0 * na + il], (double)L.Sth);
         atomicAdd(&acc[1 * na + il], (double)L.Suh);
@@ -442,9 +459,10 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
 
 // ---- task kernel (cells too dense for the cell-centric kernel) ----------------------
 
-__global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
+__global__ void __launch_bounds__(kBlkI, 4) k_backward_tasks(GridDev g) {
   __shared__ float4 s_x[kTileJ + kPad];
   __shared__ float4 s_a[kTileJ + kPad];
+  __shared__ float s_e[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
   __shared__ int s_j[kTileJ + kPad];
   __shared__ unsigned s_mask[kBlkI / 32][kMaskChunks * 32];
@@ -481,8 +499,6 @@ __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
       const float reach = fmaxf(L.H, Hmax_b) + B.pad;
       d_lo = di - reach;
       d_hi = di + reach;
-      const float Hb = fmaxf(L.H, Hmax_b);
-      L.ci = fmaxf(L.ci, L.di + Hb * Hb + guard_band(Hb, B.edge_f));
     }
     const float w_lo = warp_min_b(d_lo), w_hi = warp_max_b(d_hi);
     for (int j0 = tk.j0; j0 < tk.j1; j0 += kTileJ) {
@@ -494,6 +510,7 @@ __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
         const float4 ak = g.gk[sj];
         s_x[e] = staged_b(xj);
         s_a[e] = make_float4(xj.w, ak.x, ak.y, g.ghh[sj].y);
+        s_e[e] = ak.z;
         s_d[e] = sl.s * g.dist[kbase + cb + pos_j] + off;
         s_j[e] = sj;
       }
@@ -502,7 +519,7 @@ __global__ void __launch_bounds__(kBlkI) k_backward_tasks(GridDev g) {
         const int lo = (o == kSelfSlot) ? upper_bound_f(s_d, len, w_lo) : 0;
         const int hi = lower_bound_f(s_d, len, w_hi);
         auto jidx = [&](int j) { return s_j[j]; };
-        sweep_bwd(L, s_x, s_a, lo, hi, s_mask[warp], lane, g, B, jidx);
+        sweep_bwd(L, s_x, s_a, s_e, lo, hi, s_mask[warp], lane, g, B, jidx);
       }
       __syncthreads();
     }
@@ -542,24 +559,22 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
 }  // namespace
 
 cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g_drho_dh,
-                            float* g_pos, float* g_h, int num_sms, cudaStream_t st,
-                            cudaEvent_t t0, cudaEvent_t t1) {
+                            float* g_pos, float* g_h, int num_sms, int ctas_per_sm,
+                            cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
   if (g.n == 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_backward_cells,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kCellSmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  if (ctas_per_sm < 1 || ctas_per_sm > 2) return cudaErrorInvalidValue;
+  static std::atomic<unsigned long long> smem_done{0};
+  cudaError_t e = set_max_dynamic_smem(smem_done, reinterpret_cast<const void*>(&k_backward_cells),
+                                       kCellSmemFor[1]);
+  if (e != cudaSuccess) return e;
+  const int smem = kCellSmemFor[ctas_per_sm];
   const int nb = (g.n + 255) / 256;
   k_bwd_prep<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if ((e = launch_plan(g, 1, kCellSmem - kCellFixedSmem, kElemJ, kElemA, st)) != cudaSuccess)
-    return e;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_plan(g, 1, smem - kCellFixedSmem, kElemJ, kElemA, st)) != cudaSuccess) return e;
   if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
-  k_backward_cells<<<num_sms * 2, kCellThreads, kCellSmem, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
+  k_backward_cells<<<num_sms * ctas_per_sm, kCellThreads, smem, st>>>(g, g_rho, g_drho_dh, g_pos,
+                                                                       g_h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
   k_backward_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);

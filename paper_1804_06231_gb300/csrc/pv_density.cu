@@ -40,7 +40,10 @@ namespace {
 constexpr int kBlkI = 128;       // particles of a per task (task path)
 constexpr int kTileJ = 1024;     // particles of b per tile (task path)
 constexpr int kCellThreads = 256;
-constexpr int kCellSmem = 72 * 1024;  // dynamic shared memory of k_density_cells (3 per SM)
+// dynamic shared memory of k_density_cells for 1..4 resident CTAs per SM (the
+// SM's 228 KB less 1 KB reserved and the static part per CTA); 3 by default
+constexpr int kCellSmemFor[5] = {0, 200 * 1024, 110 * 1024, 72 * 1024, 54 * 1024};
+constexpr int kCellSmem = kCellSmemFor[3];
 constexpr int kPad = 32;         // slack after staged arrays for the 32-wide sweep
 
 // slots ordered by expected cost: self, faces, edges, corners
@@ -369,7 +372,7 @@ __device__ __forceinline__ float staged_proj(float4 x, float ux, float uy, float
   return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
 }
 
-__global__ void __launch_bounds__(kCellThreads) k_density_cells(GridDev g, float* __restrict__ rho,
+__global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, float* __restrict__ rho,
                                                                 float* __restrict__ drho_dh,
                                                                 int32_t* __restrict__ n_ngb) {
   extern __shared__ float4 dsm[];
@@ -732,19 +735,19 @@ int64_t max_tasks_for(int64_t n, int64_t ncell) {
 }
 
 cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t* n_ngb,
-                           int num_sms, cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
+                           int num_sms, int ctas_per_sm, cudaStream_t st, cudaEvent_t t0,
+                           cudaEvent_t t1) {
   if (g.n == 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_density_cells,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kCellSmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  cudaError_t e = launch_plan(g, 0, kCellSmem - kCellFixedSmem, kCellElemJ, kCellElemA, st);
+  if (ctas_per_sm < 1 || ctas_per_sm > 4) return cudaErrorInvalidValue;
+  static std::atomic<unsigned long long> smem_done{0};
+  cudaError_t e = set_max_dynamic_smem(smem_done, reinterpret_cast<const void*>(&k_density_cells),
+                                       kCellSmemFor[1]);
   if (e != cudaSuccess) return e;
+  const int smem = kCellSmemFor[ctas_per_sm];
+  if ((e = launch_plan(g, 0, smem - kCellFixedSmem, kCellElemJ, kCellElemA, st)) != cudaSuccess)
+    return e;
   if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
-  k_density_cells<<<num_sms * 3, kCellThreads, kCellSmem, st>>>(g, rho, drho_dh, n_ngb);
+  k_density_cells<<<num_sms * ctas_per_sm, kCellThreads, smem, st>>>(g, rho, drho_dh, n_ngb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
   k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);

@@ -19,6 +19,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdint.h>
 
 #include "pv.h"
@@ -323,14 +325,32 @@ cudaError_t launch_sort(const GridDev& g, cudaStream_t st);
 cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
                         cudaStream_t st);
 int64_t max_tasks_for(int64_t n, int64_t ncell);
-// t0/t1 (optional): events recorded on `st` just before and after the
-// cell-centric sweep kernel.
+// ctas_per_sm: resident CTAs of the cell-centric sweep kernel per SM (1..4
+// forward, 1..2 adjoint); it sets the kernel's shared memory and so which
+// cells the plan routes to it.  t0/t1 (optional): events recorded on `st`
+// just before and after that kernel.
 cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t* n_ngb,
-                           int num_sms, cudaStream_t st, cudaEvent_t t0 = nullptr,
-                           cudaEvent_t t1 = nullptr);
+                           int num_sms, int ctas_per_sm, cudaStream_t st,
+                           cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g_drho_dh,
-                            float* g_pos, float* g_h, int num_sms, cudaStream_t st,
-                            cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
+                            float* g_pos, float* g_h, int num_sms, int ctas_per_sm,
+                            cudaStream_t st, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
+constexpr int kDensityCtasDefault = 3, kBackwardCtasDefault = 2;
+
+// Raises `func`'s dynamic shared-memory limit to `bytes` the first time it is
+// called on a device (bit `dev` of `done` records it; devices >= 64 set it on
+// every call).  Kept off CUDA-graph captures by the eager first launch.
+inline cudaError_t set_max_dynamic_smem(std::atomic<unsigned long long>& done, const void* func,
+                                        int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load() & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
 cudaError_t launch_count_candidates(const GridDev& g, cudaStream_t st);
 
 }  // namespace pv

@@ -204,7 +204,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   if ((e = pv::launch_scatter(d, pos, h, m, m_uniform, st)) != cudaSuccess)
     return fail(e, "scatter");
   if ((e = pv::launch_sort(d, st)) != cudaSuccess) return fail(e, "sort");
-  if ((e = pv::launch_density(d, rho, drho_dh, n_ngb, num_sms, st)) != cudaSuccess)
+  if ((e = pv::launch_density(d, rho, drho_dh, n_ngb, num_sms, pv::kDensityCtasDefault, st)) != cudaSuccess)
     return fail(e, "density");
   if (flags_out &&
       (e = cudaMemcpyAsync(flags_out, d.flags, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st)) !=

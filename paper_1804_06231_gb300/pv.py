@@ -31,7 +31,7 @@ GAMMA = 1.825742
 EXPORTS = ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
            "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
            "pv_status_str", "pv_last_cuda_error", "pv_density_static", "pv_grid_time_sweeps",
-           "pv_grid_sweep_times")
+           "pv_grid_sweep_times", "pv_grid_set_tuning", "pv_grid_get_tuning")
 STATIC_MAX_PARTICLES = 65536
 STATIC_MAX_CELLS = 4096
 
@@ -64,6 +64,11 @@ class pv_stats(ctypes.Structure):
                 ("pairs_adjoint", ctypes.c_int64)]
 
 
+class pv_tuning(ctypes.Structure):
+    _fields_ = [("density_ctas_per_sm", ctypes.c_int32), ("backward_ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
 _lib = None
 
 
@@ -86,11 +91,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pv_grid_sync.argtypes = [vp, vp]
     lib.pv_grid_stats.argtypes = [vp, ctypes.POINTER(pv_stats)]
     lib.pv_grid_time_sweeps.argtypes = [vp, i32]
+    lib.pv_grid_set_tuning.argtypes = [vp, ctypes.POINTER(pv_tuning)]
+    lib.pv_grid_get_tuning.argtypes = [vp, ctypes.POINTER(pv_tuning)]
     lib.pv_grid_sweep_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64)]
     for name in ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
                  "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
-                 "pv_grid_time_sweeps", "pv_grid_sweep_times"):
+                 "pv_grid_time_sweeps", "pv_grid_sweep_times", "pv_grid_set_tuning",
+                 "pv_grid_get_tuning"):
         getattr(lib, name).restype = i32
     lib.pv_status_str.argtypes = [i32]
     lib.pv_status_str.restype = ctypes.c_char_p
@@ -164,6 +172,18 @@ def pv_density_static(pos: int, h: int, m: int | None, m_uniform: float, n: int,
     _check(load_library().pv_density_static(pos, h, m, ctypes.c_float(m_uniform), int(n),
                                             float(L), int(nc), float(gamma), rho, drho_dh,
                                             n_ngb, flags_out, stream), "pv_density_static")
+
+
+def pv_grid_set_tuning(grid: int, density_ctas_per_sm: int = 0,
+                       backward_ctas_per_sm: int = 0) -> None:
+    t = pv_tuning(int(density_ctas_per_sm), int(backward_ctas_per_sm))
+    _check(load_library().pv_grid_set_tuning(grid, ctypes.byref(t)), "pv_grid_set_tuning")
+
+
+def pv_grid_get_tuning(grid: int) -> tuple[int, int]:
+    t = pv_tuning()
+    _check(load_library().pv_grid_get_tuning(grid, ctypes.byref(t)), "pv_grid_get_tuning")
+    return t.density_ctas_per_sm, t.backward_ctas_per_sm
 
 
 def pv_grid_time_sweeps(grid: int, enable: bool) -> None:
@@ -301,6 +321,13 @@ class Grid:
 
     def sync(self, stream=None) -> None:
         pv_grid_sync(self.handle, self._stream(stream))
+
+    def set_tuning(self, density_ctas_per_sm: int = 0, backward_ctas_per_sm: int = 0) -> None:
+        """CTAs per SM of the two cell-centric sweep kernels (0 = default)."""
+        pv_grid_set_tuning(self.handle, density_ctas_per_sm, backward_ctas_per_sm)
+
+    def tuning(self) -> tuple[int, int]:
+        return pv_grid_get_tuning(self.handle)
 
     def time_sweeps(self, enable: bool = True) -> None:
         """Start (or stop) timing the sweep kernels with CUDA events; resets the totals."""

@@ -45,6 +45,7 @@ def test_struct_layout_matches_header():
     assert pv.pv_box_desc.nc.offset == 24
     assert ctypes.sizeof(pv.pv_grid_desc) == 32
     assert ctypes.sizeof(pv.pv_stats) == 80
+    assert ctypes.sizeof(pv.pv_tuning) == 32
 
 
 def test_argument_errors_return_before_device_work(lib):
@@ -69,6 +70,9 @@ def test_argument_errors_return_before_device_work(lib):
     assert lib.pv_grid_sync(None, None) == 1
     assert lib.pv_grid_stats(None, None) == 1
     assert lib.pv_grid_time_sweeps(None, 1) == 1
+    t = pv.pv_tuning(3, 2)
+    assert lib.pv_grid_set_tuning(None, ctypes.byref(t)) == 1
+    assert lib.pv_grid_get_tuning(None, ctypes.byref(t)) == 1
     assert lib.pv_grid_sweep_times(None, None, None) == 1
     assert lib.pv_grid_destroy(None) == 0
 

@@ -116,3 +116,49 @@ def test_cuda_graph_replay_matches_eager():
     assert torch.equal(ref[0], rho) and torch.equal(ref[1], D) and torch.equal(ref[2], nn)
     assert torch.isfinite(gp).all() and gp.abs().sum() > 0
     grid.close()
+
+
+def test_launch_shapes_meet_parity_and_autotune(oracle_lib, tmp_path):
+    """Every launch shape of the sweep kernels (which moves dense cells between
+    the cell-centric and the task kernels) meets the parity bar against the
+    oracle; the autotuner picks one of them, sets it and caches it."""
+    import torch
+    from paper_1804_06231_gb300 import tune
+    from paper_1804_06231_gb300.pv import Grid
+    from gpu_util import check_density  # noqa: E402
+    box = I.clustered(60000, 31)
+    dev = torch.device("cuda", 0)
+    pos = torch.from_numpy(box.pos).to(dev)
+    h = torch.from_numpy(box.h).to(dev)
+    m = torch.from_numpy(box.m).to(dev)
+    ref = oracle_lib.density_cells(box.pos, box.h, box.m, box.L, box.nc)
+    w, v = I.loss_weights(box.n, 5)
+    g_up, k_up = oracle_lib.loss_upstream(ref.rho, w, v)
+    gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g_up, k_up, box.L, box.nc)
+    gr = torch.from_numpy(np.asarray(g_up, np.float32)).to(dev)
+    gd = torch.from_numpy(np.asarray(k_up, np.float32)).to(dev)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    with Grid((box.n, box.L, box.nc)) as g:
+        g.sort(pos, h, m)
+        assert g.tuning() == tune.DEFAULT
+        for d, b in ((2, 1), (3, 2), (4, 2), (4, 1)):
+            g.set_tuning(d, b)
+            assert g.tuning() == (d, b)
+            rho, D, n = g.density()
+            gp, gh = g.backward(gr, gd)
+            g.sync()
+            check_density(rho.cpu().numpy().astype(np.float64),
+                          D.cpu().numpy().astype(np.float64), n.cpu().numpy(), ref)
+            assert rel(gp.cpu().numpy().astype(np.float64), gp0) <= 1e-4
+            assert rel(gh.cpu().numpy().astype(np.float64), gh0) <= 1e-4
+        from paper_1804_06231_gb300.pv import PvError
+        with pytest.raises(PvError):
+            g.set_tuning(5, 2)
+        with pytest.raises(PvError):
+            g.set_tuning(3, 3)
+        path = str(tmp_path / "tuning.json")
+        r1 = tune.autotune(g, gr, gd, reps=2, cache_path=path)
+        assert r1["source"] == "timed"
+        assert g.tuning() == (r1["density_ctas_per_sm"], r1["backward_ctas_per_sm"])
+        r2 = tune.autotune(g, gr, gd, reps=2, cache_path=path)
+        assert r2["source"] == "cache" and r2["signature"] == r1["signature"]
