@@ -82,6 +82,7 @@ def parse():
     p.add_argument("--impl", default="pv", choices=["pv", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     # smaller uniform workloads with the same h rule, for profiler captures
     p.add_argument("--particles", type=int, default=0)
     p.add_argument("--cells", type=int, default=0)
@@ -277,6 +278,13 @@ def main():
         grid.density(rho, drho, nngb)
         grid.backward(g_rho, g_d, gpos, gh)
 
+    tuning = None
+    step()  # first sort, so that the autotuner sees the sorted grid
+    if not args.no_tune:
+        from paper_1804_06231_gb300 import tune
+        tr = tune.autotune(grid, g_rho, g_d, reps=5)
+        tuning = {"density_ctas_per_sm": tr["density_ctas_per_sm"],
+                  "backward_ctas_per_sm": tr["backward_ctas_per_sm"], "source": tr["source"]}
     for _ in range(max(args.warmup, 3)):
         step()
     grid.sync()
@@ -413,6 +421,8 @@ def main():
             "config": {"workload": WORKLOAD if not args.particles else
                        f"uniform N={n}, {box.nc}^3 cells (profiling size)", "n_particles_per_gpu": n, "cells": box.nc ** 3,
                        "l2": "flushed between steps (512 MiB write)",
+                       "launch_shape": tuning or {"density_ctas_per_sm": 3,
+                                                  "backward_ctas_per_sm": 2, "source": "default"},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "e2e": e2e,
             "gpu_launches": launches,

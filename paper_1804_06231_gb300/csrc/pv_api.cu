@@ -166,10 +166,6 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_TRY(dev_alloc(g, &d.pos64, 3 * N));
   PV_TRY(dev_alloc(g, &d.perm, pv::kNDir * N));
   PV_TRY(dev_alloc(g, &d.dist, pv::kNDir * N));
-  PV_TRY(dev_alloc(g, &d.skey, N));
-  PV_TRY(dev_alloc(g, &d.sbuf, N));
-  PV_TRY(dev_alloc(g, &d.stmp, N));
-  PV_TRY(dev_alloc(g, &d.sbucket, 2 * N));
   PV_TRY(dev_alloc(g, &d.acc, 3 * N));
   PV_TRY(dev_alloc(g, &d.gacc, 5 * N));
   PV_TRY(dev_alloc(g, &d.gk, N));
@@ -290,7 +286,7 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
   cudaEvent_t t0, t1;
   PV_TRY(next_pair(g, 0, &t0, &t1));
   PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, g->ctas[0], st, t0, t1));
-  g->launches += g->n > 0 ? 5 : 0;  // plan_slots, plan_cells, cells, tasks, finalize_t
+  g->launches += g->n > 0 ? 6 : 0;  // plan_slots, plan_cells, plan_tasks, cells, tasks, finalize_t
   return PV_OK;
 }
 
@@ -306,7 +302,7 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
   PV_TRY(next_pair(g, 1, &t0, &t1));
   PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, g->ctas[1], st, t0,
                               t1));
-  g->launches += g->n > 0 ? 6 : 0;  // prep, plan_slots, plan_cells, cells, tasks, finalize_t
+  g->launches += g->n > 0 ? 7 : 0;  // prep, plan x3, cells, tasks, finalize_t
   return PV_OK;
 }
 

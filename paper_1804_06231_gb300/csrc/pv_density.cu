@@ -128,15 +128,16 @@ __global__ void k_plan_slots(GridDev g, int wide) {
 }
 
 // One thread per cell: route the cell to the cell-centric kernel when its
-// staged windows fit `smem_budget`, else expand it into tasks of kBlkI
-// particles with their own windows.
-__global__ void k_plan_cells(GridDev g, int wide, int smem_budget, int elem_j, int elem_a) {
+// staged windows fit `smem_budget`, else to the task kernel, reserving one
+// task of kBlkI particles per block of each slot (the first task's index goes
+// to plan.w; k_plan_tasks fills the tasks in).
+__global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a) {
   if (*g.flags) return;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= g.ncell) return;
   const int na = g.cell_count[a];
   if (na == 0) return;
-  const int4* pl = g.plan + (size_t)a * kNSlot;
+  int4* pl = g.plan + (size_t)a * kNSlot;
   int total = 0;
   for (int o = 0; o < kNSlot; o++) total += pl[o].z - pl[o].y;
   if (elem_j * (total + kPad) + elem_a * na <= smem_budget) {
@@ -144,25 +145,44 @@ __global__ void k_plan_cells(GridDev g, int wide, int smem_budget, int elem_j, i
     return;
   }
   g.tcells[atomicAdd(g.n_tcells, 1)] = a;
-  const BoxDev& B = g.boxes[g.cell_box[a]];
-  const int ca = g.cell_start[a];
   for (int o = 0; o < kNSlot; o++) {
     const int nI = pl[o].x;
     if (nI == 0) continue;
-    const int b = neighbour_cell(g, a, o);
-    const int nb = g.cell_count[b], cb = g.cell_start[b];
-    const Slot sl = slot_info(o);
-    float reach = g.cell_Hmax[a];
-    if (wide) reach = fmaxf(reach, g.cell_Hmax[b]);
-    reach += B.pad;
-    const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
     const int nblk = (nI + kBlkI - 1) / kBlkI;
     const int base = atomicAdd(g.ntask, nblk);
     if (base + nblk > g.max_tasks) {  // cannot happen with the allocated bound
       atomicOr(g.flags, PV_FLAG_CELL_OVERFLOW);
       return;
     }
-    for (int bk = 0; bk < nblk; bk++) {
+    pl[o].w = base;
+  }
+}
+
+// One warp per (task cell, slot), lanes over its blocks of kBlkI particles:
+// each task gets its particles [p0, p1) of a in the slot's order and the
+// window [j0, j1) of b that they can reach.
+__global__ void k_plan_tasks(GridDev g, int wide) {
+  if (*g.flags) return;
+  const int nt = *g.n_tcells;
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int pair = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pair < nt * kNSlot;
+       pair += nw) {
+    const int a = g.tcells[pair / kNSlot], o = pair % kNSlot;
+    const int4 pl = g.plan[(size_t)a * kNSlot + o];
+    const int nI = pl.x;
+    if (nI == 0) continue;
+    const int na = g.cell_count[a], ca = g.cell_start[a];
+    const int b = neighbour_cell(g, a, o);
+    const int nb = g.cell_count[b], cb = g.cell_start[b];
+    const BoxDev& B = g.boxes[g.cell_box[a]];
+    const Slot sl = slot_info(o);
+    float reach = g.cell_Hmax[a];
+    if (wide) reach = fmaxf(reach, g.cell_Hmax[b]);
+    reach += B.pad;
+    const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
+    const int nblk = (nI + kBlkI - 1) / kBlkI;
+    for (int bk = lane; bk < nblk; bk += 32) {
       const int p0 = bk * kBlkI, p1 = min(nI, p0 + kBlkI);
       int j0, j1;
       if (o == kSelfSlot) {
@@ -174,7 +194,7 @@ __global__ void k_plan_cells(GridDev g, int wide, int smem_budget, int elem_j, i
         j0 = 0;
         j1 = count_below(g, sl.k, sl.s, cb, nb, off, dmax + reach);
       }
-      g.tasks[base + bk] = make_int4(a, o, (int)((unsigned)p0 | ((unsigned)p1 << 16)),
+      g.tasks[pl.w + bk] = make_int4(a, o, (int)((unsigned)p0 | ((unsigned)p1 << 16)),
                                      (int)((unsigned)j0 | ((unsigned)j1 << 16)));
     }
   }
@@ -726,7 +746,9 @@ cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j,
   k_plan_slots<<<(nthr + 255) / 256, 256, 0, st>>>(g, wide);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_plan_cells<<<(g.ncell + 127) / 128, 128, 0, st>>>(g, wide, smem_budget, elem_j, elem_a);
+  k_plan_cells<<<(g.ncell + 127) / 128, 128, 0, st>>>(g, smem_budget, elem_j, elem_a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_plan_tasks<<<512, 256, 0, st>>>(g, wide);
   return cudaGetLastError();
 }
 

@@ -296,58 +296,92 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
   }
 }
 
-__global__ void __launch_bounds__(1024, 1) k_sort_big(GridDev g) {
+// One CTA per (cell of more than kSortSmallMax particles, axis), the same
+// bucket sort with the buckets in shared memory.  It needs no scratch beyond
+// the axis's own outputs: the bucket-grouped indices go into dist[k] (as int
+// bits) until the exact ranks have been written to perm[k], then dist[k]
+// receives the keys, which are recomputed from xm wherever they are needed
+// (the same FP32 expression each time, so the same values).
+constexpr int kSortBigThreads = 1024;
+constexpr int kSortBigBuckets = 8192;
+
+__global__ void __launch_bounds__(kSortBigThreads) k_sort_big(GridDev g) {
+  __shared__ int s_bkt[kSortBigBuckets];
   __shared__ float s_red[2][32];
-  __shared__ int s_chunk[32];
+  __shared__ int s_scan[32];
+  if (*g.flags) return;
   const int nbig = *g.n_big;
-  for (int idx = blockIdx.x; idx < nbig; idx += gridDim.x) {
-    const int c = g.big_cells[idx];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int idx = blockIdx.x; idx < nbig * kNDir; idx += gridDim.x) {
+    const int c = g.big_cells[idx / kNDir], k = idx % kNDir;
     const int cnt = min(g.cell_count[c], PV_MAX_CELL_COUNT);
     const int cs = g.cell_start[c];
-    int B = 1024;  // >= the block size, and >= cnt
-    while (B < cnt) B <<= 1;
-    float* key = g.skey + cs;
-    int* out = g.sbuf + cs;
-    int* tmp = g.stmp + cs;
-    // buckets: B <= 2 cnt slots of the cell's own range [2 cs, 2 cs + 2 cnt)
-    // (cnt > 512 and B = max(1024, next power of two >= cnt))
-    int* bkt = g.sbucket + 2 * (size_t)cs;
-    for (int k = 0; k < kNDir; k++) {
-      float ux, uy, uz;
-      axis_u(k, ux, uy, uz);
-      float kmin = 3.0e38f, kmax = -3.0e38f;
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        float d = project(g.xm[cs + t], ux, uy, uz);
-        key[t] = d;
-        kmin = fminf(kmin, d);
-        kmax = fmaxf(kmax, d);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-      }
-      if ((threadIdx.x & 31) == 0) {
-        s_red[0][threadIdx.x >> 5] = kmin;
-        s_red[1][threadIdx.x >> 5] = kmax;
-      }
-      __syncthreads();
-      kmin = s_red[0][0];
-      kmax = s_red[1][0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
-        kmin = fminf(kmin, s_red[0][w]);
-        kmax = fmaxf(kmax, s_red[1][w]);
-      }
-      __syncthreads();
-      sort_axis<true>(cnt, g.orig + cs, key, tmp, out, bkt, s_chunk, B, threadIdx.x, blockDim.x,
-                      kmin, kmax);
-      const size_t base = (size_t)k * g.n + cs;
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        int v = out[t];
-        g.perm[base + t] = (uint16_t)v;
-        g.dist[base + t] = key[v];
-      }
-      __syncthreads();
+    int B = kSortBigThreads;
+    while (B < cnt && B < kSortBigBuckets) B <<= 1;
+    float ux, uy, uz;
+    axis_u(k, ux, uy, uz);
+    const float4* X = g.xm + cs;
+    const int* O = g.orig + cs;
+    const size_t base = (size_t)k * g.n + cs;
+    int* tmp = reinterpret_cast<int*>(g.dist + base);
+    uint16_t* out = g.perm + base;
+    float kmin = 3.0e38f, kmax = -3.0e38f;
+    for (int t = tid; t < cnt; t += nthr) {
+      const float d = project(X[t], ux, uy, uz);
+      kmin = fminf(kmin, d);
+      kmax = fmaxf(kmax, d);
     }
+    for (int o = 16; o > 0; o >>= 1) {
+      kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+      kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    if ((tid & 31) == 0) {
+      s_red[0][tid >> 5] = kmin;
+      s_red[1][tid >> 5] = kmax;
+    }
+    for (int b = tid; b < B; b += nthr) s_bkt[b] = 0;
+    __syncthreads();
+    kmin = s_red[0][0];
+    kmax = s_red[1][0];
+    for (int w = 1; w < (nthr >> 5); w++) {
+      kmin = fminf(kmin, s_red[0][w]);
+      kmax = fmaxf(kmax, s_red[1][w]);
+    }
+    const float scale = kmax > kmin ? (float)B / (kmax - kmin) : 0.0f;
+    auto bucket_of = [&](float d) { return min(B - 1, max(0, (int)((d - kmin) * scale))); };
+    for (int t = tid; t < cnt; t += nthr)
+      atomicAdd(&s_bkt[bucket_of(project(X[t], ux, uy, uz))], 1);
+    __syncthreads();
+    // exclusive scan: each thread owns B / nthr consecutive buckets
+    const int per = B / nthr, b0 = tid * per;
+    int sum = 0;
+    for (int b = b0; b < b0 + per; b++) sum += s_bkt[b];
+    int run = group_exclusive_scan<true>(sum, tid, s_scan);
+    for (int b = b0; b < b0 + per; b++) {
+      const int v = s_bkt[b];
+      s_bkt[b] = run;
+      run += v;
+    }
+    __syncthreads();
+    for (int t = tid; t < cnt; t += nthr)
+      tmp[atomicAdd(&s_bkt[bucket_of(project(X[t], ux, uy, uz))], 1)] = t;
+    __syncthreads();
+    // s_bkt[b] is now the end of bucket b; rank each particle inside its bucket
+    for (int t = tid; t < cnt; t += nthr) {
+      const float kt = project(X[t], ux, uy, uz);
+      const int b = bucket_of(kt);
+      const int s0 = b ? s_bkt[b - 1] : 0, s1 = s_bkt[b];
+      const int ot = O[t];
+      int r = 0;
+      for (int u = s0; u < s1; u++) {
+        const int v = tmp[u];
+        r += key_less(project(X[v], ux, uy, uz), O[v], kt, ot) ? 1 : 0;
+      }
+      out[s0 + r] = (uint16_t)t;
+    }
+    __syncthreads();
+    for (int t = tid; t < cnt; t += nthr) g.dist[base + t] = project(X[out[t]], ux, uy, uz);
+    __syncthreads();
   }
 }
 
@@ -386,7 +420,7 @@ cudaError_t launch_sort(const GridDev& g, cudaStream_t st) {
   k_sort_small<<<g.ncell, kSortThreads, smem, st>>>(g);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_sort_big<<<256, 1024, 0, st>>>(g);
+  k_sort_big<<<512, kSortBigThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 

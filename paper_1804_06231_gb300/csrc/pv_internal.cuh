@@ -69,11 +69,6 @@ struct GridDev {
   double* pos64;
   uint16_t* perm;  // [13][N]
   float* dist;     // [13][N]
-  // sort scratch for big cells (cell order)
-  float* skey;
-  int32_t* sbuf;
-  int32_t* stmp;
-  int32_t* sbucket;  // [2N]
   // density accumulators (cell order), fixed point
   long long* acc;    // [3][N]: rho, drho/dh (2^36 scale), n
   // backward accumulators (cell order), FP64 [5][N]: sum m th, sum m uh, gx, gy, gz

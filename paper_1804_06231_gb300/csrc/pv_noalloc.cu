@@ -39,8 +39,7 @@ constexpr size_t scratch_bytes(int64_t n, int64_t c) {
          align_up(N * sizeof(float4)) + align_up(N * sizeof(float)) +
          align_up(N * sizeof(int32_t)) + align_up(3 * N * sizeof(double)) +
          align_up(pv::kNDir * N * sizeof(uint16_t)) + align_up(pv::kNDir * N * sizeof(float)) +
-         align_up(N * sizeof(float)) + 2 * align_up(N * sizeof(int32_t)) +
-         align_up(2 * N * sizeof(int32_t)) + align_up(3 * N * sizeof(long long)) +
+         align_up(3 * N * sizeof(long long)) +
          align_up((size_t)((int64_t)pv::kNSlot * (n / 128 + c) + 64) * sizeof(int4)) +
          align_up(16 * sizeof(int32_t)) + align_up(8 * sizeof(unsigned long long));
 }
@@ -146,10 +145,6 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.pos64 = carve<double>(cur, 3 * N);
   d.perm = carve<uint16_t>(cur, pv::kNDir * N);
   d.dist = carve<float>(cur, pv::kNDir * N);
-  d.skey = carve<float>(cur, N);
-  d.sbuf = carve<int32_t>(cur, N);
-  d.stmp = carve<int32_t>(cur, N);
-  d.sbucket = carve<int32_t>(cur, 2 * N);
   d.acc = carve<long long>(cur, 3 * N);
   d.max_tasks = (int32_t)pv::max_tasks_for(n, ncell);
   d.tasks = carve<int4>(cur, (size_t)d.max_tasks);
