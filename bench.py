@@ -83,6 +83,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the 4M clustered and 64-box workloads (extra keys)")
     # smaller uniform workloads with the same h rule, for profiler captures
     p.add_argument("--particles", type=int, default=0)
     p.add_argument("--cells", type=int, default=0)
@@ -165,6 +167,161 @@ def workload(seed: int, particles: int = 0, cells: int = 0):
     if particles:
         return I.uniform(particles, seed, nc=cells or None)
     return I.cfg1(seed)
+
+
+def timed_steps(step, flush, K: int, W: int = 3) -> float:
+    """Median CUDA-event time (ms) of `step` over K runs after W warm-ups, L2
+    flushed before each run (outside the events)."""
+    import torch
+    for _ in range(W):
+        step()
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(K):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def workload_extras(dev, flush, K: int = 5) -> dict:
+    """The other two throughput workloads of the method: 4,194,304 clustered
+    particles on the finest grid (one box), and the 64-box mix as one batched
+    grid, as 64 separate grids, and as a CUDA-graph replay of the batched step.
+    Each is sort + density + backward with an autotuned launch shape."""
+    import torch
+    from paper_1804_06231_gb300 import inputs as I, tune
+    from paper_1804_06231_gb300.pv import Grid
+
+    def tensors(boxes):
+        pos = torch.from_numpy(np.concatenate([b.pos for b in boxes])).to(dev)
+        h = torch.from_numpy(np.concatenate([b.h for b in boxes])).to(dev)
+        m = torch.from_numpy(np.concatenate([b.m for b in boxes])).to(dev)
+        rng = np.random.default_rng(7)
+        n = pos.shape[0]
+        gr = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
+        gd = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
+        outs = (torch.empty(n, device=dev), torch.empty(n, device=dev),
+                torch.empty(n, device=dev, dtype=torch.int32),
+                torch.empty((n, 3), device=dev), torch.empty(n, device=dev))
+        return pos, h, m, gr, gd, outs
+
+    out = {}
+    box = I.cfg2()
+    pos, h, m, gr, gd, (rho, D, nn, gp, gh) = tensors([box])
+    with Grid((box.n, box.L, box.nc)) as g:
+        def step():
+            g.sort(pos, h, m)
+            g.density(rho, D, nn)
+            g.backward(gr, gd, gp, gh)
+        step()
+        tr = tune.autotune(g, gr, gd, reps=3)
+        t = timed_steps(step, flush, K)
+        inter = g.stats().interactions
+        out["clustered_4m"] = {
+            "workload": f"clustered N={box.n}, {box.nc}^3 cells, 64 Gaussians + 20% uniform",
+            "ms_per_step": t, "value": inter / (t * 1e-3), "unit": UNIT,
+            "launch_shape": [tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"]],
+            "max_cell_count": g.stats().max_cell_count}
+    del pos, h, m, gr, gd, rho, D, nn, gp, gh
+    torch.cuda.empty_cache()
+
+    boxes = I.multibox()
+    pos, h, m, gr, gd, (rho, D, nn, gp, gh) = tensors(boxes)
+    gb = Grid([(b.n, b.L, b.nc) for b in boxes])
+
+    def step_b():
+        gb.sort(pos, h, m)
+        gb.density(rho, D, nn)
+        gb.backward(gr, gd, gp, gh)
+    step_b()
+    tr = tune.autotune(gb, gr, gd, reps=3)
+    t_b = timed_steps(step_b, flush, K)
+    inter = gb.stats().interactions
+    views, first = [], 0
+    for b in boxes:
+        sl = slice(first, first + b.n)
+        gg = Grid((b.n, b.L, b.nc))
+        gg.set_tuning(tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"])
+        views.append((gg, pos[sl], h[sl], m[sl], gr[sl], gd[sl], rho[sl], D[sl], nn[sl],
+                      gp[sl], gh[sl]))
+        first += b.n
+
+    def step_p():
+        for gg, p_, h_, m_, gr_, gd_, r_, d_, n_, gp_, gh_ in views:
+            gg.sort(p_, h_, m_)
+            gg.density(r_, d_, n_)
+            gg.backward(gr_, gd_, gp_, gh_)
+    t_p = timed_steps(step_p, flush, K)
+    for v in views:
+        v[0].close()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step_b()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_b()
+    t_g = timed_steps(graph.replay, flush, K)
+    gb.close()
+    out["multibox_64"] = {
+        "workload": f"64 boxes, N={sum(b.n for b in boxes)} (per box log-uniform in "
+                    "[4096, 524288], uniform or clustered)",
+        "ms_per_step_batched": t_b, "ms_per_step_per_box": t_p, "ms_per_step_graph": t_g,
+        "value": inter / (t_g * 1e-3), "unit": UNIT,
+        "launch_shape": [tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"]]}
+    return out
+
+
+def raw_ceiling(dev, props, peak_tflops: float) -> dict:
+    """The interaction arithmetic alone (pv_raw_interactions): 1024 particles
+    per SM against 2560 others (the paper's first experiment uses 2560), all
+    pairs in range, every lane busy."""
+    import torch
+    from paper_1804_06231_gb300.pv import raw_interactions
+    g = torch.Generator(device="cpu").manual_seed(5)
+    H = 0.05
+
+    def ball(n):
+        v = torch.randn((n, 3), generator=g, dtype=torch.float64)
+        r = 0.45 * H * torch.rand(n, generator=g, dtype=torch.float64) ** (1.0 / 3.0)
+        v = v * (r / v.norm(dim=1))[:, None]
+        m = torch.full((n, 1), 1.0 / n, dtype=torch.float64)
+        return torch.cat([v, m], dim=1).float().to(dev)
+    ni, nj, reps = props.multi_processor_count * 1024, 2560, 8
+    xi, xj = ball(ni), ball(nj)
+    out = torch.empty((ni, 2), device=dev)
+    ms = timed_steps(lambda: raw_interactions(xi, xj, H, reps, out), torch.empty(0, device=dev),
+                     5, 2)
+    rate = ni * nj * reps / (ms * 1e-3)
+    tf = rate * FWD_FLOP_PAIR / 1e12
+    return {"interactions_per_s": rate, "n_i": ni, "n_j": nj, "reps": reps, "ms": ms,
+            "tflops": tf, "frac_of_fp32_peak": tf / peak_tflops,
+            "flop_per_interaction": FWD_FLOP_PAIR}
+
+
+def orientation_breakdown(grid, st, flush, density, K: int = 5) -> dict:
+    """Density pass restricted to each neighbour orientation class in turn
+    (slot masks): time, window distance tests and interactions per class."""
+    from paper_1804_06231_gb300.pv import SLOT_MASK_ALL, slot_mask_of_class
+    ms = []
+    for c in range(4):
+        grid.set_slot_mask(slot_mask_of_class(c))
+        ms.append(timed_steps(density, flush, K))
+    grid.set_slot_mask(SLOT_MASK_ALL)
+    tot = sum(ms)
+    cand = [st.orientation[c][0] for c in range(4)]
+    inter = [st.orientation[c][1] for c in range(4)]
+    return {"classes": ["self", "face", "edge", "corner"], "density_ms": ms,
+            "time_share": [t / tot for t in ms], "candidates": cand, "interactions": inter,
+            "in_range_fraction": [i / max(c, 1) for c, i in zip(cand, inter)]}
 
 
 def cpu_sample(seed: int):
@@ -400,6 +557,13 @@ def main():
     roofline = roof("k_backward_cells", bwd_flops, k_bwd)
     roofline_fwd = roof("k_density_cells", fwd_flops, k_dens)
 
+    extras = None
+    if rank == 0 and ws == 1 and not args.no_extras and not args.particles:
+        extras = {"orientation_breakdown": orientation_breakdown(
+                      grid, st_c, flush, lambda: grid.density(rho, drho, nngb)),
+                  "raw_interaction_ceiling": raw_ceiling(dev, props, peak_tflops)}
+        extras.update(workload_extras(dev, flush))
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         import oracle
@@ -433,12 +597,16 @@ def main():
             "breakdown_ms": {"sort": t_sort, "density": t_dens, "backward": t_bwd,
                              "density_sweep_kernel": k_dens, "backward_sweep_kernel": k_bwd},
             "density_interactions_per_s": interactions / (t_dens * 1e-3),
-            "fwd_bwd_over_fwd": (t_dens + t_bwd) / t_dens,
+            # forward = sort + density (what a forward pass needs); fwd+bwd = the step
+            "fwd_bwd_over_fwd": t_step / (t_sort + t_dens),
+            "backward_over_density": t_bwd / t_dens,
             "candidates": candidates, "interactions": interactions,
             "candidates_adjoint": cand_adj, "pairs_adjoint": pairs_adj,
             "candidates_per_interaction": candidates / max(interactions, 1),
             "guard_pairs": st.guard_pairs, "wall_s_timed_loop": wall,
         }
+        if extras:
+            line.update(extras)
         print(json.dumps(line), flush=True)
     grid.close()
     if ws > 1:

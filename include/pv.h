@@ -88,6 +88,10 @@ typedef struct {
   int64_t kernel_launches;  /* kernels this grid has launched since it was created */
   int64_t candidates_adjoint; /* adjoint windows: j with projected distance < max(H_i, H_j) */
   int64_t pairs_adjoint;      /* pairs with r_ij < max(H_i, H_j), j = i included */
+  int64_t orientation[4][2];  /* per class of neighbour (0 self, 1 face, 2 edge,
+                                 3 corner): [0] window distance tests (self
+                                 windows include j = i), [1] pairs j != i with
+                                 r_ij < H_i (pv_count_candidates) */
 } pv_stats;
 
 /* Allocates a grid for the given boxes (cudaMalloc on the current device).
@@ -142,7 +146,9 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
    Section 2) for the particles sorted by the last pv_sort_cells, into
    pv_stats.candidates, and the corresponding counts of the adjoint sweep
    (window and cut-off max(H_i, H_j)) into pv_stats.candidates_adjoint and
-   pv_stats.pairs_adjoint.  A diagnostic pass; not needed for the others. */
+   pv_stats.pairs_adjoint, and the per-orientation counts of the forward
+   windows into pv_stats.orientation.  A diagnostic pass; not needed for the
+   others. */
 pv_status pv_count_candidates(pv_grid* g, void* stream);
 
 /* Waits for the grid's work on `stream` and returns PV_ERR_DEVICE if a kernel
@@ -173,6 +179,33 @@ pv_status pv_grid_set_tuning(pv_grid* g, const pv_tuning* t);
 
 /* Writes the launch shape in use (defaults resolved) to *out (host). */
 pv_status pv_grid_get_tuning(const pv_grid* g, pv_tuning* out);
+
+/* Restricts later pv_density / pv_density_backward calls of this grid to the
+   neighbour slots whose bit is set in `mask` (bit o for the neighbour at
+   offset (ox, oy, oz) in {-1,0,1}^3, o = 9 (ox+1) + 3 (oy+1) + (oz+1); bit 13
+   is the cell itself).  A measurement aid with no counterpart in the paper's
+   method (it times the contribution of each neighbour orientation); with a
+   partial mask the outputs are partial sums.  PV_SLOT_MASK_ALL restores the
+   method.  Errors: PV_ERR_INVALID_ARGUMENT for g == NULL or bits above 26. */
+#define PV_SLOT_MASK_ALL 0x7ffffffu
+pv_status pv_grid_set_slot_mask(pv_grid* g, uint32_t mask);
+
+/* Raw interaction throughput, the GPU counterpart of the paper's first
+   experiment (Section 4: one particle against 2560, all SIMD lanes busy).
+   For every i < n_i it sums over all j < n_j, `reps` times, m_j wh(q) and
+   m_j th(q), q = |x_i - x_j| / H, the half-scaled kernel terms of pv_density
+   (wh = (1-q)^3 - 4 max(1/2-q, 0)^3, th = (1-q)^2 (3-6q) - max(1/2-q, 0)^2
+   (6-24q)), with no window, no mask and no cut-off test, so every pair must
+   have |x_i - x_j| < H.  It is a measurement of the interaction arithmetic
+   alone, not part of the method.
+   xi: device float [n_i][4] {x, y, z, m}; xj: device float [n_j][4]; out:
+   device float [n_i][2] {sum m wh, sum m th} (over all repetitions); all
+   three 16-byte aligned.  Asynchronous on `stream`.  Errors:
+   PV_ERR_INVALID_ARGUMENT (negative sizes, reps < 1, H not finite and > 0,
+   NULL or misaligned pointers), PV_ERR_TOO_LARGE (sizes above 2^31 - 1),
+   PV_ERR_CUDA (launch failure). */
+pv_status pv_raw_interactions(const float* xi, int64_t n_i, const float* xj, int64_t n_j,
+                              float H, int32_t reps, float* out, void* stream);
 
 /* Per-kernel timing of the two sweeps (a measurement aid; the paper has no
    counterpart).  With enable != 0, every later pv_density and

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -176,6 +177,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   const int64_t mt = pv::max_tasks_for(n, ncell);
   if (mt > 0x7fffffffLL) return PV_ERR_TOO_LARGE;
   d.max_tasks = (int32_t)mt;
+  d.slot_mask = pv::kAllSlots;
   PV_TRY(dev_alloc(g, &d.tasks, (size_t)d.max_tasks));
   // scalars in one allocation
   int32_t* sc;
@@ -190,10 +192,10 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   d.ccell_next = sc + 7;
   d.n_tcells = sc + 8;
   unsigned long long* cnt;
-  PV_TRY(dev_alloc(g, &cnt, 8));
+  PV_TRY(dev_alloc(g, &cnt, 16));
   d.counters = cnt;
   PV_CUDA(cudaMemset(sc, 0, 16 * sizeof(int32_t)));
-  PV_CUDA(cudaMemset(cnt, 0, 8 * sizeof(unsigned long long)));
+  PV_CUDA(cudaMemset(cnt, 0, 16 * sizeof(unsigned long long)));
   if (N) {
     PV_CUDA(cudaMemset(d.acc, 0, 3 * N * sizeof(long long)));
     PV_CUDA(cudaMemset(d.gacc, 0, 5 * N * sizeof(long long)));
@@ -310,9 +312,9 @@ pv_status pv_count_candidates(pv_grid* g, void* stream) {
   if (!g) return PV_ERR_INVALID_ARGUMENT;
   if (!g->sorted) return PV_ERR_NOT_SORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  PV_CUDA(cudaMemsetAsync(g->d.counters + 2, 0, 3 * sizeof(unsigned long long), st));
+  PV_CUDA(cudaMemsetAsync(g->d.counters + 2, 0, 14 * sizeof(unsigned long long), st));
   PV_CUDA(pv::launch_count_candidates(g->d, st));
-  g->launches += 2;
+  g->launches += 3;
   return PV_OK;
 }
 
@@ -328,7 +330,7 @@ pv_status pv_grid_stats(pv_grid* g, pv_stats* out) {
   if (!g || !out) return PV_ERR_INVALID_ARGUMENT;
   PV_CUDA(cudaDeviceSynchronize());
   int32_t sc[4];
-  unsigned long long cnt[8];
+  unsigned long long cnt[16];
   PV_CUDA(cudaMemcpy(sc, g->d.flags, sizeof(sc), cudaMemcpyDeviceToHost));
   PV_CUDA(cudaMemcpy(cnt, g->d.counters, sizeof(cnt), cudaMemcpyDeviceToHost));
   std::memset(out, 0, sizeof(*out));
@@ -341,6 +343,10 @@ pv_status pv_grid_stats(pv_grid* g, pv_stats* out) {
   out->candidates = (int64_t)cnt[2];
   out->candidates_adjoint = (int64_t)cnt[3];
   out->pairs_adjoint = (int64_t)cnt[4];
+  for (int c = 0; c < 4; c++) {
+    out->orientation[c][0] = (int64_t)cnt[8 + 2 * c];
+    out->orientation[c][1] = (int64_t)cnt[9 + 2 * c];
+  }
   out->device_bytes = (int64_t)g->bytes;
   out->kernel_launches = g->launches;
   return out->device_flags ? PV_ERR_DEVICE : PV_OK;
@@ -363,6 +369,28 @@ pv_status pv_grid_get_tuning(const pv_grid* g, pv_tuning* out) {
   std::memset(out, 0, sizeof(*out));
   out->density_ctas_per_sm = g->ctas[0];
   out->backward_ctas_per_sm = g->ctas[1];
+  return PV_OK;
+}
+
+pv_status pv_raw_interactions(const float* xi, int64_t n_i, const float* xj, int64_t n_j,
+                              float H, int32_t reps, float* out, void* stream) {
+  if (n_i < 0 || n_j < 0 || reps < 1 || !(H > 0.0f) || !std::isfinite(H))
+    return PV_ERR_INVALID_ARGUMENT;
+  if (n_i > 0x7fffffff || n_j > 0x7fffffff) return PV_ERR_TOO_LARGE;
+  if (n_i > 0 && (!xi || !out || (n_j > 0 && !xj))) return PV_ERR_INVALID_ARGUMENT;
+  if ((reinterpret_cast<uintptr_t>(xi) | reinterpret_cast<uintptr_t>(xj) |
+       reinterpret_cast<uintptr_t>(out)) & 15u)
+    return PV_ERR_INVALID_ARGUMENT;
+  PV_CUDA(pv::launch_raw_density(reinterpret_cast<const float4*>(xi), (int)n_i,
+                                 reinterpret_cast<const float4*>(xj), (int)n_j, H, reps,
+                                 reinterpret_cast<float2*>(out),
+                                 static_cast<cudaStream_t>(stream)));
+  return PV_OK;
+}
+
+pv_status pv_grid_set_slot_mask(pv_grid* g, uint32_t mask) {
+  if (!g || (mask & ~pv::kAllSlots)) return PV_ERR_INVALID_ARGUMENT;
+  g->d.slot_mask = mask;
   return PV_OK;
 }
 

@@ -289,6 +289,13 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
   }
 }
 
+// per-particle data a staged window element is built from
+struct StagedB {
+  float4 x;  // xm
+  float4 k;  // gk: G, K, H^2 + guard, H^2 - guard
+  float H;
+};
+
 __device__ __forceinline__ float4 staged_b(float4 x) {
   return make_float4(x.x, x.y, x.z, fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z)));
 }
@@ -382,19 +389,20 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
     float4* Sa = Sx + total + kPad;                    // [total + kPad] {m, G, K, H}
     double* acc = reinterpret_cast<double*>(Sa + total + kPad);  // [5][na]
     float* Se = reinterpret_cast<float*>(acc + 5 * na);          // [total + kPad] E_j
-    for (int f = tid; f < total; f += kCellThreads) {
-      const int q = seg_of(cs.off, kNSlot, f);  // cs.off[q] <= f < cs.off[q+1]
-      const int o = c_border[q];
-      const Slot sl = slot_info(o);
-      const int nb = cs.nb_[q], cb = cs.cb_[q];
-      const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], nb);
-      const int sj = cb + g.perm[(size_t)sl.k * g.n + cb + pos];
-      const float4 xj = g.xm[sj];
-      const float4 ak = g.gk[sj];
-      Sx[f] = staged_b(xj);
-      Sa[f] = make_float4(xj.w, ak.x, ak.y, g.ghh[sj].y);
-      Se[f] = ak.z;  // H_j^2 + guard_j
-    }
+    stage_flat<4>(
+        cs.off, total, tid, kCellThreads,
+        [&](int f, int q) {
+          const Slot sl = slot_info(c_border[q]);
+          const int cb = cs.cb_[q];
+          const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], cs.nb_[q]);
+          return cb + (int)g.perm[(size_t)sl.k * g.n + cb + pos];
+        },
+        [&](int sj) { return StagedB{g.xm[sj], g.gk[sj], g.ghh[sj].y}; },
+        [&](int f, const StagedB& v) {
+          Sx[f] = staged_b(v.x);
+          Sa[f] = make_float4(v.x.w, v.k.x, v.k.y, v.H);
+          Se[f] = v.k.z;  // H_j^2 + guard_j
+        });
     for (int t = tid; t < 5 * na; t += kCellThreads) acc[t] = 0.0;
     __syncthreads();
     const int nitems = cs.runs[kNSlot];
@@ -441,7 +449,9 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
         return cbq + (int)g.perm[kbq + order_pos(sl.s, J0q + j - s0, nbq)];
       };
       sweep_bwd(L, Sx, Sa, Se, lo, hi, Mw, lane, g, B, jidx);
-      if (valid) {
+      // lanes whose windows held no pair in range have nothing to add
+      if (valid && (L.Sth != 0.0f || L.Suh != 0.0f || L.gx != 0.0f || L.gy != 0.0f ||
+                    L.gz != 0.0f)) {
         atomicAdd(&acc[0 * na + il], (double)L.Sth);
         atomicAdd(&acc[1 * na + il], (double)L.Suh);
         atomicAdd(&acc[2 * na + il], (double)L.gx);
@@ -523,7 +533,8 @@ __global__ void __launch_bounds__(kBlkI, 4) k_backward_tasks(GridDev g) {
       }
       __syncthreads();
     }
-    if (valid) {
+    if (valid && (L.Sth != 0.0f || L.Suh != 0.0f || L.gx != 0.0f || L.gy != 0.0f ||
+                  L.gz != 0.0f)) {
       double* acc = reinterpret_cast<double*>(g.gacc);
       const size_t N = (size_t)g.n;
       atomicAdd(&acc[L.si], (double)L.Sth);

@@ -95,7 +95,7 @@ __global__ void k_plan_slots(GridDev g, int wide) {
   const int a = idx / kNSlot, o = idx % kNSlot;
   const int na = g.cell_count[a];
   int4 pl = make_int4(0, 0, 0, 0);
-  if (na > 0) {
+  if (na > 0 && ((g.slot_mask >> o) & 1u)) {
     const int b = neighbour_cell(g, a, o);
     const int nb = g.cell_count[b];
     if (nb > 0) {
@@ -451,17 +451,19 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
     float* Ah = Sm + total + kPad;                             // [na]
     int* acc_n = reinterpret_cast<int*>(Ah + na);              // [na]
     // stage the 27 windows in sorted order, and cell a in cell order
-    for (int f = tid; f < total; f += kCellThreads) {
-      const int q = seg_of(cs.off, kNSlot, f);  // cs.off[q] <= f < cs.off[q+1]
-      const int o = c_slot_order[q];
-      const Slot sl = slot_info(o);
-      const int nb = cs.nb_[q], cb = cs.cb_[q];
-      const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], nb);
-      const int jl = g.perm[(size_t)sl.k * g.n + cb + pos];
-      const float4 xj = g.xm[cb + jl];
-      Sx[f] = staged(xj);
-      Sm[f] = xj.w;
-    }
+    stage_flat<3>(
+        cs.off, total, tid, kCellThreads,
+        [&](int f, int q) {
+          const Slot sl = slot_info(c_slot_order[q]);
+          const int cb = cs.cb_[q];
+          const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], cs.nb_[q]);
+          return cb + (int)g.perm[(size_t)sl.k * g.n + cb + pos];
+        },
+        [&](int sj) { return g.xm[sj]; },
+        [&](int f, float4 x) {
+          Sx[f] = staged(x);
+          Sm[f] = x.w;
+        });
     for (int t = tid; t < na; t += kCellThreads) {
       Ax[t] = g.xm[ca + t];
       Ah[t] = g.hs[ca + t];
@@ -738,6 +740,65 @@ __global__ void k_count_adjoint(GridDev g) {
   }
 }
 
+// Per orientation class (self, face, edge, corner) of the slot: the distance
+// tests of the method's sorted windows (self: |d_j - d_i| < H_i, j = i
+// included; pairs: d_j < d_i + H_i) into counters[8 + 2c], and the pairs
+// j != i with r < H_i into counters[9 + 2c].  One warp per (cell, slot), lanes
+// over the particles of the cell (diagnostic).
+__global__ void k_count_classes(GridDev g) {
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  unsigned long long cand = 0, inter = 0;
+  int cls = 0;
+  if (wid < g.ncell * kNSlot && !*g.flags) {
+    const int a = wid / kNSlot, o = wid % kNSlot;
+    const int na = g.cell_count[a];
+    const int b = na ? neighbour_cell(g, a, o) : a;
+    const int nb = g.cell_count[b];
+    const Slot sl = slot_info(o);
+    cls = sl.v2;
+    if (na && nb) {
+      const BoxDev& B = g.boxes[g.cell_box[a]];
+      const int ca = g.cell_start[a], cb = g.cell_start[b];
+      const size_t kb = (size_t)sl.k * g.n;
+      const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
+      for (int p = lane; p < na; p += 32) {
+        const int pos = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
+        const int si = ca + g.perm[kb + ca + pos];
+        const float Hi = g.gamma * g.hs[si];
+        const float di = sl.s * g.dist[kb + ca + pos];
+        const float4 xi = g.xm[si];
+        const float x = xi.x - sl.ox * B.edge_f, y = xi.y - sl.oy * B.edge_f,
+                    z = xi.z - sl.oz * B.edge_f;
+        int j = 0, j1 = nb;
+        if (o == kSelfSlot) {
+          j = upper_bound_f(g.dist + cb, nb, di - Hi);
+          j1 = lower_bound_f(g.dist + cb, nb, di + Hi);
+        }
+        for (; j < j1; j++) {
+          const float dj = proj_asc(g, sl.k, sl.s, cb, nb, j, off);
+          if (dj - di >= Hi) break;
+          cand++;
+          const int sj = cb + g.perm[kb + cb + order_pos(sl.s, j, nb)];
+          if (sj == si) continue;
+          const float4 xj = g.xm[sj];
+          const float dx = x - xj.x, dy = y - xj.y, dz = z - xj.z;
+          if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < Hi * Hi) inter++;
+        }
+      }
+    }
+  }
+  // the lanes of a warp share (cell, slot), so one class per warp
+  for (int s = 16; s > 0; s >>= 1) {
+    cand += __shfl_xor_sync(0xffffffffu, cand, s);
+    inter += __shfl_xor_sync(0xffffffffu, inter, s);
+  }
+  if (lane == 0) {
+    if (cand) atomicAdd(&g.counters[8 + 2 * cls], cand);
+    if (inter) atomicAdd(&g.counters[9 + 2 * cls], inter);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
@@ -785,6 +846,8 @@ cudaError_t launch_count_candidates(const GridDev& g, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_count_adjoint<<<(nthr * 32 + 255) / 256, 256, 0, st>>>(g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_count_classes<<<(nthr * 32 + 255) / 256, 256, 0, st>>>(g);
   return cudaGetLastError();
 }
 

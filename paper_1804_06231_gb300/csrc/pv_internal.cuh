@@ -30,6 +30,7 @@ namespace pv {
 constexpr int kNDir = 13;   // distinct axes joining neighbouring cell centres
 constexpr int kNSlot = 27;  // neighbour offsets (ox,oy,oz) in {-1,0,1}^3
 constexpr int kSelfSlot = 13;
+constexpr uint32_t kAllSlots = (1u << 27) - 1u;
 constexpr int kFixShift = 36;                       // fixed-point scale 2^36
 constexpr double kFixScale = 68719476736.0;         // 2^36
 constexpr double kFixInv = 1.0 / 68719476736.0;
@@ -87,12 +88,15 @@ struct GridDev {
   int32_t* ntask;
   int32_t* task_next;
   int32_t max_tasks;
+  uint32_t slot_mask;  // neighbour slots the sweeps visit (bit o of slot o; all 27 normally)
   // scalars
   uint32_t* flags;
   float* m_max;     // [n_boxes] largest mass of each box (mass unit of the accumulators)
   int32_t* max_count;
   unsigned long long* counters;  // [0] interactions, [1] guard pairs, [2] candidates,
-                                 // [3] adjoint candidates, [4] adjoint pairs
+                                 // [3] adjoint candidates, [4] adjoint pairs,
+                                 // [8 + 2c], [9 + 2c]: candidates, interactions of
+                                 // orientation class c (self, face, edge, corner)
 };
 
 // ---- direction slots ------------------------------------------------------
@@ -307,6 +311,37 @@ static __device__ __forceinline__ bool guard_inside(const double* __restrict__ p
   return r2 < Hd * Hd;
 }
 
+// Stages the windows of a cell, one flat range [0, total) with window q at
+// [off[q], off[q+1]): thread t takes elements t, t + nthr, ... (so every warp
+// stays full across window boundaries), follows its window index forward
+// instead of searching for it, and keeps U elements in flight: index(f, q)
+// for U elements (the sorted-order lookups), then fetch(sj) for the U (the
+// particle data), then put(f, value).
+template <int U, typename Index, typename Fetch, typename Put>
+__device__ __forceinline__ void stage_flat(const int* off, int total, int tid, int nthr,
+                                           Index index, Fetch fetch, Put put) {
+  int q = 0;
+  for (int f0 = tid; f0 < total; f0 += U * nthr) {
+    int sj[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int f = f0 + u * nthr;
+      sj[u] = -1;
+      if (f < total) {
+        while (off[q + 1] <= f) q++;
+        sj[u] = index(f, q);
+      }
+    }
+    decltype(fetch(0)) v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (sj[u] >= 0) v[u] = fetch(sj[u]);
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (sj[u] >= 0) put(f0 + u * nthr, v[u]);
+  }
+}
+
 // ---- host-side launchers (defined in the .cu files) ------------------------
 cudaError_t launch_bin(const GridDev& g, const double* pos, const float* h, const float* m,
                        float m_uniform, cudaStream_t st);
@@ -347,5 +382,7 @@ inline cudaError_t set_max_dynamic_smem(std::atomic<unsigned long long>& done, c
   return e;
 }
 cudaError_t launch_count_candidates(const GridDev& g, cudaStream_t st);
+cudaError_t launch_raw_density(const float4* xi, int ni, const float4* xj, int nj, float H,
+                               int reps, float2* out, cudaStream_t st);
 
 }  // namespace pv

@@ -41,7 +41,7 @@ constexpr size_t scratch_bytes(int64_t n, int64_t c) {
          align_up(pv::kNDir * N * sizeof(uint16_t)) + align_up(pv::kNDir * N * sizeof(float)) +
          align_up(3 * N * sizeof(long long)) +
          align_up((size_t)((int64_t)pv::kNSlot * (n / 128 + c) + 64) * sizeof(int4)) +
-         align_up(16 * sizeof(int32_t)) + align_up(8 * sizeof(unsigned long long));
+         align_up(16 * sizeof(int32_t)) + align_up(16 * sizeof(unsigned long long));
 }
 
 constexpr size_t kScratchBytes = scratch_bytes(kMaxParticles, kMaxCells);
@@ -147,9 +147,10 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.dist = carve<float>(cur, pv::kNDir * N);
   d.acc = carve<long long>(cur, 3 * N);
   d.max_tasks = (int32_t)pv::max_tasks_for(n, ncell);
+  d.slot_mask = pv::kAllSlots;
   d.tasks = carve<int4>(cur, (size_t)d.max_tasks);
   int32_t* sc = carve<int32_t>(cur, 16);
-  d.counters = carve<unsigned long long>(cur, 8);
+  d.counters = carve<unsigned long long>(cur, 16);
   if ((size_t)(cur - static_cast<unsigned char*>(base)) > kScratchBytes) return PV_ERR_TOO_LARGE;
   d.flags = reinterpret_cast<uint32_t*>(sc + 0);
   d.m_max = reinterpret_cast<float*>(sc + 1);  // one box
@@ -191,7 +192,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   if ((e = cudaMemsetAsync(d.cell_count, 0, C * sizeof(int32_t), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(d.cell_Hmax, 0, C * sizeof(float), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(sc, 0, 16 * sizeof(int32_t), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(d.counters, 0, 8 * sizeof(unsigned long long), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(d.counters, 0, 16 * sizeof(unsigned long long), st)) != cudaSuccess ||
       (N && (e = cudaMemsetAsync(d.acc, 0, 3 * N * sizeof(long long), st)) != cudaSuccess))
     return fail(e, "cudaMemsetAsync");
   if ((e = pv::launch_bin(d, pos, h, m, m_uniform, st)) != cudaSuccess) return fail(e, "bin");

@@ -1,0 +1,60 @@
+// pv_raw.cu -- raw interaction throughput: every particle of one set against
+// every particle of another, all lanes busy, with no window, no mask and no
+// cut-off test.  The GPU counterpart of the paper's first experiment (Section
+// 4: one particle against 2560, scalar against SIMD): it measures the cost of
+// the interaction arithmetic of the density sweep on its own, the ceiling
+// that the sorted sweeps are compared with.
+#include <cuda_runtime.h>
+
+#include "pv_internal.cuh"
+
+namespace pv {
+namespace {
+
+constexpr int kRawThreads = 256;
+constexpr int kRawTile = 1024;
+
+// One thread per i; the j set is staged in tiles of kRawTile.  The per-pair
+// arithmetic is that of the sweep's evaluation pass: r^2, q by approximate
+// square root, the half-scaled kernel terms and two accumulations.
+__global__ void __launch_bounds__(kRawThreads) k_raw_density(const float4* __restrict__ xi,
+                                                             int ni,
+                                                             const float4* __restrict__ xj,
+                                                             int nj, float Hinv2, int reps,
+                                                             float2* __restrict__ out) {
+  __shared__ float4 s[kRawTile];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const float4 x = i < ni ? xi[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  float rho = 0.0f, D = 0.0f;
+  for (int rep = 0; rep < reps; rep++) {
+    for (int j0 = 0; j0 < nj; j0 += kRawTile) {
+      const int len = min(kRawTile, nj - j0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < len; e += blockDim.x) s[e] = xj[j0 + e];
+      __syncthreads();
+#pragma unroll 4
+      for (int e = 0; e < len; e++) {
+        const float4 q = s[e];
+        const float dx = x.x - q.x, dy = x.y - q.y, dz = x.z - q.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float wh, th;
+        spline_half(sqrt_approx(r2 * Hinv2), wh, th);
+        rho = fmaf(q.w, wh, rho);
+        D = fmaf(q.w, th, D);
+      }
+    }
+  }
+  if (i < ni) out[i] = make_float2(rho, D);
+}
+
+}  // namespace
+
+cudaError_t launch_raw_density(const float4* xi, int ni, const float4* xj, int nj, float H,
+                               int reps, float2* out, cudaStream_t st) {
+  if (ni == 0) return cudaSuccess;
+  k_raw_density<<<(ni + kRawThreads - 1) / kRawThreads, kRawThreads, 0, st>>>(
+      xi, ni, xj, nj, 1.0f / (H * H), reps, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pv

@@ -31,7 +31,8 @@ GAMMA = 1.825742
 EXPORTS = ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
            "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
            "pv_status_str", "pv_last_cuda_error", "pv_density_static", "pv_grid_time_sweeps",
-           "pv_grid_sweep_times", "pv_grid_set_tuning", "pv_grid_get_tuning")
+           "pv_grid_sweep_times", "pv_grid_set_tuning", "pv_grid_get_tuning",
+           "pv_grid_set_slot_mask", "pv_raw_interactions")
 STATIC_MAX_PARTICLES = 65536
 STATIC_MAX_CELLS = 4096
 
@@ -61,7 +62,7 @@ class pv_stats(ctypes.Structure):
                 ("interactions", ctypes.c_int64), ("guard_pairs", ctypes.c_int64),
                 ("candidates", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("candidates_adjoint", ctypes.c_int64),
-                ("pairs_adjoint", ctypes.c_int64)]
+                ("pairs_adjoint", ctypes.c_int64), ("orientation", (ctypes.c_int64 * 2) * 4)]
 
 
 class pv_tuning(ctypes.Structure):
@@ -91,6 +92,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pv_grid_sync.argtypes = [vp, vp]
     lib.pv_grid_stats.argtypes = [vp, ctypes.POINTER(pv_stats)]
     lib.pv_grid_time_sweeps.argtypes = [vp, i32]
+    lib.pv_grid_set_slot_mask.argtypes = [vp, ctypes.c_uint32]
+    lib.pv_raw_interactions.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_float,
+                                        ctypes.c_int32, vp, vp]
     lib.pv_grid_set_tuning.argtypes = [vp, ctypes.POINTER(pv_tuning)]
     lib.pv_grid_get_tuning.argtypes = [vp, ctypes.POINTER(pv_tuning)]
     lib.pv_grid_sweep_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -98,7 +102,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
                  "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
                  "pv_grid_time_sweeps", "pv_grid_sweep_times", "pv_grid_set_tuning",
-                 "pv_grid_get_tuning"):
+                 "pv_grid_get_tuning", "pv_grid_set_slot_mask", "pv_raw_interactions"):
         getattr(lib, name).restype = i32
     lib.pv_status_str.argtypes = [i32]
     lib.pv_status_str.restype = ctypes.c_char_p
@@ -186,6 +190,44 @@ def pv_grid_get_tuning(grid: int) -> tuple[int, int]:
     return t.density_ctas_per_sm, t.backward_ctas_per_sm
 
 
+SLOT_MASK_ALL = (1 << 27) - 1
+
+
+def pv_raw_interactions(xi: int, n_i: int, xj: int, n_j: int, H: float, reps: int, out: int,
+                        stream: int = 0) -> None:
+    _check(load_library().pv_raw_interactions(xi, int(n_i), xj, int(n_j), ctypes.c_float(H),
+                                              int(reps), out, stream), "pv_raw_interactions")
+
+
+def raw_interactions(xi, xj, H: float, reps: int = 1, out=None, stream=None):
+    """Torch front end of pv_raw_interactions: xi [n_i, 4], xj [n_j, 4] float32
+    CUDA tensors {x, y, z, m}; returns [n_i, 2] {sum m wh, sum m th}."""
+    import torch
+    if out is None:
+        out = torch.empty((xi.shape[0], 2), dtype=torch.float32, device=xi.device)
+    for t, name in ((xi, "xi"), (xj, "xj"), (out, "out")):
+        Grid._dev(t, torch.float32, None, name)
+    st = torch.cuda.current_stream().cuda_stream if stream is None else \
+        getattr(stream, "cuda_stream", stream)
+    pv_raw_interactions(xi.data_ptr(), xi.shape[0], xj.data_ptr(), xj.shape[0], H, reps,
+                        out.data_ptr(), st)
+    return out
+
+
+def pv_grid_set_slot_mask(grid: int, mask: int) -> None:
+    _check(load_library().pv_grid_set_slot_mask(grid, int(mask)), "pv_grid_set_slot_mask")
+
+
+def slot_mask_of_class(cls: int) -> int:
+    """Mask of the slots of one orientation class (0 self, 1 face, 2 edge, 3 corner)."""
+    m = 0
+    for o in range(27):
+        ox, oy, oz = o // 9 - 1, (o // 3) % 3 - 1, o % 3 - 1
+        if ox * ox + oy * oy + oz * oz == cls:
+            m |= 1 << o
+    return m
+
+
 def pv_grid_time_sweeps(grid: int, enable: bool) -> None:
     _check(load_library().pv_grid_time_sweeps(grid, 1 if enable else 0), "pv_grid_time_sweeps")
 
@@ -211,12 +253,15 @@ class Stats:
     kernel_launches: int
     candidates_adjoint: int
     pairs_adjoint: int
+    orientation: list  # [4][2]: (self, face, edge, corner) x (candidates, interactions)
 
 
 def pv_grid_stats(grid: int, raise_on_flags: bool = True) -> Stats:
     st = pv_stats()
     status = load_library().pv_grid_stats(grid, ctypes.byref(st))
-    out = Stats(*(getattr(st, f) for f, _ in pv_stats._fields_))
+    vals = [getattr(st, f) for f, _ in pv_stats._fields_]
+    vals[-1] = [[int(st.orientation[c][0]), int(st.orientation[c][1])] for c in range(4)]
+    out = Stats(*vals)
     if status != PV_OK and (raise_on_flags or status != 6):
         raise PvError(status, "pv_grid_stats", f"device_flags={out.device_flags}")
     return out
@@ -328,6 +373,10 @@ class Grid:
 
     def tuning(self) -> tuple[int, int]:
         return pv_grid_get_tuning(self.handle)
+
+    def set_slot_mask(self, mask: int = SLOT_MASK_ALL) -> None:
+        """Visit only the neighbour slots in `mask` (measurement aid)."""
+        pv_grid_set_slot_mask(self.handle, mask)
 
     def time_sweeps(self, enable: bool = True) -> None:
         """Start (or stop) timing the sweep kernels with CUDA events; resets the totals."""

@@ -44,7 +44,7 @@ def test_struct_layout_matches_header():
     assert ctypes.sizeof(pv.pv_box_desc) == 32
     assert pv.pv_box_desc.nc.offset == 24
     assert ctypes.sizeof(pv.pv_grid_desc) == 32
-    assert ctypes.sizeof(pv.pv_stats) == 80
+    assert ctypes.sizeof(pv.pv_stats) == 144
     assert ctypes.sizeof(pv.pv_tuning) == 32
 
 
@@ -70,6 +70,10 @@ def test_argument_errors_return_before_device_work(lib):
     assert lib.pv_grid_sync(None, None) == 1
     assert lib.pv_grid_stats(None, None) == 1
     assert lib.pv_grid_time_sweeps(None, 1) == 1
+    assert lib.pv_grid_set_slot_mask(None, 1) == 1
+    assert lib.pv_raw_interactions(None, 4, None, 4, ctypes.c_float(1.0), 1, None, None) == 1
+    assert lib.pv_raw_interactions(None, -1, None, 4, ctypes.c_float(1.0), 1, None, None) == 1
+    assert lib.pv_raw_interactions(None, 0, None, 0, ctypes.c_float(0.0), 1, None, None) == 1
     t = pv.pv_tuning(3, 2)
     assert lib.pv_grid_set_tuning(None, ctypes.byref(t)) == 1
     assert lib.pv_grid_get_tuning(None, ctypes.byref(t)) == 1
@@ -84,3 +88,11 @@ def test_product_path_does_not_import_oracle():
         text = f.read_text()
         assert "import oracle" not in text and "from oracle" not in text, f
         assert "pv_oracle" not in text, f
+
+
+def test_slot_masks_of_classes():
+    from paper_1804_06231_gb300 import pv
+    masks = [pv.slot_mask_of_class(c) for c in range(4)]
+    assert [bin(m).count("1") for m in masks] == [1, 6, 12, 8]
+    assert masks[0] == 1 << 13
+    assert sum(masks) == pv.SLOT_MASK_ALL

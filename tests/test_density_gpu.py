@@ -193,3 +193,70 @@ def test_sweep_timing_hooks():
         g.time_sweeps(False)
         g.density()
         assert all(math.isnan(t) for t in g.sweep_times())
+
+
+def test_orientation_counts_match_oracle(oracle_lib):
+    """Per orientation class (self, face, edge, corner): the window distance
+    tests and the interactions of the diagnostic pass equal the oracle's
+    per-class counters (Section 2's statistics), up to FP32 boundary cases."""
+    box = I.uniform(30000, 8, nc=8)
+    _, _, _, st, _ = run_density(box, count_candidates=True)
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
+    band = int(ref.band.sum())
+    for c in range(4):
+        assert st.orientation[c][0] == pytest.approx(int(ref.counters[c, 0]), rel=1e-5)
+        assert abs(st.orientation[c][1] - int(ref.counters[c, 1])) <= band
+    assert abs(sum(st.orientation[c][1] for c in range(4)) - st.interactions) <= band
+
+
+def test_slot_mask_partial_sums_add_up():
+    """Masking the neighbour slots by orientation class splits rho and n into
+    partial sums that add up to the full pass."""
+    import torch
+    from paper_1804_06231_gb300.pv import Grid, SLOT_MASK_ALL, slot_mask_of_class
+    box = I.uniform(60000, 12, nc=9)
+    dev = torch.device("cuda", 0)
+    pos = torch.from_numpy(box.pos).to(dev)
+    h = torch.from_numpy(box.h).to(dev)
+    with Grid((box.n, 1.0, box.nc)) as g:
+        g.sort(pos, h, None, float(box.m[0]))
+        full = [t.cpu().numpy().astype(np.float64) for t in g.density()]
+        parts = []
+        for c in range(4):
+            g.set_slot_mask(slot_mask_of_class(c))
+            parts.append([t.cpu().numpy().astype(np.float64) for t in g.density()])
+        g.set_slot_mask(SLOT_MASK_ALL)
+        again = [t.cpu().numpy() for t in g.density()]
+        g.sync()
+    rho = sum(p[0] for p in parts)
+    assert np.abs(rho / full[0] - 1).max() < 1e-6
+    n = sum(p[2] + 1 for p in parts) - 1  # every pass reports pairs - 1 (the self pair)
+    assert np.array_equal(n, full[2])
+    assert np.array_equal(again[0], full[0].astype(np.float32))
+
+
+def test_raw_interactions_match_oracle_kernel(oracle_lib):
+    """pv_raw_interactions (every i against every j, no cut-off test) sums the
+    half-scaled kernel terms: sum m wh = (pi/16) H^3 sum m W and
+    sum m th = -(pi/16) h H^3 sum m dW/dh, per the oracle's kernel functions."""
+    import torch
+    from paper_1804_06231_gb300.pv import raw_interactions
+    rng = np.random.default_rng(9)
+    H = 0.05
+    def ball(n):
+        v = rng.standard_normal((n, 3))
+        v *= (0.45 * H * rng.random(n) ** (1 / 3) / np.linalg.norm(v, axis=1))[:, None]
+        return np.concatenate([v, rng.uniform(0.5, 1.5, (n, 1))], axis=1).astype(np.float32)
+    xi, xj = ball(64), ball(2560)
+    dev = torch.device("cuda", 0)
+    out = raw_interactions(torch.from_numpy(xi).to(dev), torch.from_numpy(xj).to(dev), H,
+                           reps=2).cpu().numpy().astype(np.float64) / 2
+    h = H / 1.825742
+    c = np.pi / 16 * H ** 3
+    for i in range(xi.shape[0]):
+        r = np.linalg.norm(xj[:, :3].astype(np.float64) - xi[i, :3], axis=1)
+        W = np.array([oracle_lib.W(x, H) for x in r])
+        Wh = np.array([oracle_lib.W_h(x, h) for x in r])
+        m = xj[:, 3].astype(np.float64)
+        assert out[i, 0] == pytest.approx(c * (m * W).sum(), rel=2e-5)
+        assert abs(out[i, 1] + c * h * (m * Wh).sum()) <= 1e-4 * c * h * (m * np.abs(Wh)).sum()
