@@ -307,6 +307,32 @@ def raw_ceiling(dev, props, peak_tflops: float) -> dict:
             "flop_per_interaction": FWD_FLOP_PAIR}
 
 
+def sort_reuse(grid, box, pos, h, m_uniform, flush, density, backward, dev, K: int = 5) -> dict:
+    """pv_update_positions against pv_sort_cells on the same workload: the
+    particles are moved by up to a quarter of the free skin (edge - H_max)/2
+    (seeded), then the step runs on the kept sort with widened windows."""
+    import torch
+    rng = np.random.default_rng(11)
+    edge = box.L / box.nc
+    skin = (edge - 1.825742 * float(box.h.max())) / 2
+    v = rng.standard_normal((box.n, 3))
+    v *= (0.25 * skin * rng.random(box.n) / np.linalg.norm(v, axis=1))[:, None]
+    npos = torch.from_numpy(np.mod(box.pos + v, box.L)).to(dev)
+    t_sort = timed_steps(lambda: grid.sort(pos, h, None, m_uniform), flush, K)
+    grid.sort(pos, h, None, m_uniform)
+    t_upd = timed_steps(lambda: grid.update(npos, h), flush, K)
+
+    def step():
+        grid.update(npos, h)
+        density()
+        backward()
+    t_step = timed_steps(step, flush, K)
+    t_dens = timed_steps(density, flush, K)
+    grid.sort(pos, h, None, m_uniform)
+    return {"sort_ms": t_sort, "update_ms": t_upd, "density_ms_after_update": t_dens,
+            "step_ms_with_update": t_step, "displacement": "<= skin/4, skin = (edge - H_max)/2"}
+
+
 def orientation_breakdown(grid, st, flush, density, K: int = 5) -> dict:
     """Density pass restricted to each neighbour orientation class in turn
     (slot masks): time, window distance tests and interactions per class."""
@@ -561,7 +587,10 @@ def main():
     if rank == 0 and ws == 1 and not args.no_extras and not args.particles:
         extras = {"orientation_breakdown": orientation_breakdown(
                       grid, st_c, flush, lambda: grid.density(rho, drho, nngb)),
-                  "raw_interaction_ceiling": raw_ceiling(dev, props, peak_tflops)}
+                  "raw_interaction_ceiling": raw_ceiling(dev, props, peak_tflops),
+                  "sort_reuse": sort_reuse(grid, box, pos, h, m_uniform, flush,
+                                           lambda: grid.density(rho, drho, nngb),
+                                           lambda: grid.backward(g_rho, g_d, gpos, gh), dev)}
         extras.update(workload_extras(dev, flush))
 
     cpu = None

@@ -53,6 +53,7 @@ typedef enum {
 #define PV_FLAG_BAD_POSITION 2u         /* non-finite position coordinate */
 #define PV_FLAG_BAD_SMOOTHING 4u        /* h_i not finite or not > 0, or m_i not finite */
 #define PV_FLAG_CELL_OVERFLOW 8u        /* a cell holds more than PV_MAX_CELL_COUNT particles */
+#define PV_FLAG_SKIN_EXCEEDED 16u       /* pv_update_positions: H_max + 2 x displacement > edge */
 
 /* Largest number of particles one cell may hold (cell-local indices are 16-bit). */
 #define PV_MAX_CELL_COUNT 65535
@@ -140,6 +141,21 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
    the outputs).  Requires a prior pv_sort_cells.  Masses are constants. */
 pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drho_dh,
                               float* g_pos, float* g_h, void* stream);
+
+/* Re-uses the last pv_sort_cells for new positions and smoothing lengths of
+   the same particles (the paper keeps the sorted lists while particles move
+   little, Section 2).  Every particle keeps the cell, the slot and the 13
+   sorted positions it had at that sort; its offset from that cell's centre
+   (nearest periodic image) and its support are updated, and the largest
+   displacement since the sort in each box, delta, widens every window by
+   2 delta, so the sweeps still visit every pair in range.  That holds while
+   H_max + 2 delta <= edge in every cell; otherwise PV_FLAG_SKIN_EXCEEDED is
+   latched (later calls return PV_ERR_DEVICE without touching their outputs)
+   and the caller must call pv_sort_cells again.  Masses are those of the
+   sort.  pos: device double [N][3], h: device float [N], caller order.
+   Asynchronous on `stream`.  Errors: PV_ERR_INVALID_ARGUMENT (g, pos or h
+   NULL with N > 0), PV_ERR_NOT_SORTED, PV_ERR_CUDA. */
+pv_status pv_update_positions(pv_grid* g, const double* pos, const float* h, void* stream);
 
 /* Counts the distance tests of the sorted windows of the method (the
    "candidates": self-cell two-sided windows plus the pair windows of

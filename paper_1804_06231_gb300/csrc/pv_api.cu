@@ -162,6 +162,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_TRY(dev_alloc(g, &d.pcell, N));
   PV_TRY(dev_alloc(g, &d.prank, N));
   PV_TRY(dev_alloc(g, &d.xm, N));
+  PV_TRY(dev_alloc(g, &d.xm_ref, N));
   PV_TRY(dev_alloc(g, &d.hs, N));
   PV_TRY(dev_alloc(g, &d.orig, N));
   PV_TRY(dev_alloc(g, &d.pos64, 3 * N));
@@ -184,6 +185,8 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_TRY(dev_alloc(g, &sc, 16));
   d.flags = reinterpret_cast<uint32_t*>(sc + 0);
   PV_TRY(dev_alloc(g, &d.m_max, hb.size()));
+  PV_TRY(dev_alloc(g, &d.box_disp, hb.size()));
+  PV_CUDA(cudaMemset(d.box_disp, 0, hb.size() * sizeof(float)));
   d.max_count = sc + 2;
   d.n_big = sc + 3;
   d.ntask = sc + 4;
@@ -267,12 +270,26 @@ pv_status pv_sort_cells(pv_grid* g, const double* pos, const float* h, const flo
   PV_CUDA(cudaMemsetAsync(d.cell_Hmax, 0, C * sizeof(float), st));
   PV_CUDA(cudaMemsetAsync(d.flags, 0, 4 * sizeof(int32_t), st));  // flags, -, max_count, n_big
   PV_CUDA(cudaMemsetAsync(d.m_max, 0, g->boxes.size() * sizeof(float), st));
+  PV_CUDA(cudaMemsetAsync(d.box_disp, 0, g->boxes.size() * sizeof(float), st));
   PV_CUDA(pv::launch_bin(d, pos, h, m, m_uniform, st));
   PV_CUDA(pv::launch_scan(d, st));
   PV_CUDA(pv::launch_scatter(d, pos, h, m, m_uniform, st));
   PV_CUDA(pv::launch_sort(d, st));
   g->launches += g->n > 0 ? 5 : 1;
   g->sorted = true;
+  return PV_OK;
+}
+
+pv_status pv_update_positions(pv_grid* g, const double* pos, const float* h, void* stream) {
+  if (!g) return PV_ERR_INVALID_ARGUMENT;
+  if (g->n > 0 && (!pos || !h)) return PV_ERR_INVALID_ARGUMENT;
+  if (!g->sorted) return PV_ERR_NOT_SORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GridDev& d = g->d;
+  PV_CUDA(cudaMemsetAsync(d.cell_Hmax, 0, (size_t)g->ncell * sizeof(float), st));
+  PV_CUDA(cudaMemsetAsync(d.box_disp, 0, g->boxes.size() * sizeof(float), st));
+  PV_CUDA(pv::launch_update(d, pos, h, st));
+  g->launches += g->n > 0 ? 2 : 0;  // update, update_check
   return PV_OK;
 }
 

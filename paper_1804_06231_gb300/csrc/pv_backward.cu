@@ -355,6 +355,10 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
     const int na = g.cell_count[a], ca = g.cell_start[a];
     const BoxDev B = g.boxes[g.cell_box[a]];
     const float mscale = munit * g.m_max[g.cell_box[a]];
+    const float padw = window_pad(g, B, g.cell_box[a]);
+    // after pv_update_positions the staged positions are no longer in sorted
+    // order: the window searches then read the sort's projections
+    const bool moved = g.box_disp[g.cell_box[a]] > 0.0f;
     const int4* pl = g.plan + (size_t)a * kNSlot;
     if (tid < kNSlot) {
       const int o = c_border[tid];
@@ -429,21 +433,22 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
         il = g.perm[kb];
         laneb_set(L, g, B, sl, ca + il, g.xm[ca + il]);
         const float di = sl.s * g.dist[kb];
-        const float reach = fmaxf(L.H, Hmb) + B.pad;
+        const float reach = fmaxf(L.H, Hmb) + padw;
         d_lo = di - reach;
         d_hi = di + reach;
       }
       const float w_lo = warp_min_b(d_lo), w_hi = warp_max_b(d_hi);
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
       const float offv = cs.offv[q];
-      const int lo = s0 + ((o == kSelfSlot) ? warp_first_true(len, lane, [&](int e) {
-                             return sproj(Sx[s0 + e], ux, uy, uz, sl.s, offv) > w_lo;
-                           })
-                                            : 0);
-      const int hi = s0 + warp_first_true(len, lane, [&](int e) {
-                       return sproj(Sx[s0 + e], ux, uy, uz, sl.s, offv) >= w_hi;
-                     });
       const int J0q = cs.J0[q], nbq = cs.nb_[q], cbq = cs.cb_[q];
+      auto proj = [&](int e) {  // projection of staged element e, as sorted
+        return moved ? proj_asc(g, sl.k, sl.s, cbq, nbq, J0q + e, offv)
+                     : sproj(Sx[s0 + e], ux, uy, uz, sl.s, offv);
+      };
+      const int lo = s0 + ((o == kSelfSlot)
+                               ? warp_first_true(len, lane, [&](int e) { return proj(e) > w_lo; })
+                               : 0);
+      const int hi = s0 + warp_first_true(len, lane, [&](int e) { return proj(e) >= w_hi; });
       const size_t kbq = (size_t)sl.k * g.n + cbq;
       auto jidx = [&](int j) {
         return cbq + (int)g.perm[kbq + order_pos(sl.s, J0q + j - s0, nbq)];
@@ -506,7 +511,7 @@ __global__ void __launch_bounds__(kBlkI, 4) k_backward_tasks(GridDev g) {
       const int si = ca + g.perm[kbase + ca + pos_i];
       laneb_set(L, g, B, sl, si, g.xm[si]);
       const float di = sl.s * g.dist[kbase + ca + pos_i];
-      const float reach = fmaxf(L.H, Hmax_b) + B.pad;
+      const float reach = fmaxf(L.H, Hmax_b) + window_pad(g, B, g.cell_box[a]);
       d_lo = di - reach;
       d_hi = di + reach;
     }

@@ -65,12 +65,6 @@ __device__ __forceinline__ Task decode(int4 t) {
   return r;
 }
 
-// Projection of the t-th particle of cell c (start cs, count cnt) in the
-// ascending-along-u order of slot (k, s), plus the cell shift `off`.
-__device__ __forceinline__ float proj_asc(const GridDev& g, int k, int s, int cs, int cnt, int t,
-                                          float off) {
-  return s * g.dist[(size_t)k * g.n + cs + order_pos(s, t, cnt)] + off;
-}
 
 // #{t : proj_asc(t) < lim} (ascending)
 __device__ __forceinline__ int count_below(const GridDev& g, int k, int s, int cs, int cnt,
@@ -104,7 +98,7 @@ __global__ void k_plan_slots(GridDev g, int wide) {
       const int ca = g.cell_start[a], cb = g.cell_start[b];
       float reach = g.cell_Hmax[a];
       if (wide) reach = fmaxf(reach, g.cell_Hmax[b]);
-      reach += B.pad;
+      reach += window_pad(g, B, g.cell_box[a]);
       if (o == kSelfSlot) {
         pl = make_int4(na, 0, nb, 0);
       } else {
@@ -179,7 +173,7 @@ __global__ void k_plan_tasks(GridDev g, int wide) {
     const Slot sl = slot_info(o);
     float reach = g.cell_Hmax[a];
     if (wide) reach = fmaxf(reach, g.cell_Hmax[b]);
-    reach += B.pad;
+    reach += window_pad(g, B, g.cell_box[a]);
     const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
     const int nblk = (nI + kBlkI - 1) / kBlkI;
     for (int bk = lane; bk < nblk; bk += 32) {
@@ -414,6 +408,10 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
     const int na = g.cell_count[a], ca = g.cell_start[a];
     const BoxDev B = g.boxes[g.cell_box[a]];
     const float mscale = munit * g.m_max[g.cell_box[a]];
+    const float padw = window_pad(g, B, g.cell_box[a]);
+    // after pv_update_positions the staged positions are no longer in sorted
+    // order: the window searches then read the sort's projections
+    const bool moved = g.box_disp[g.cell_box[a]] > 0.0f;
     const int4* pl = g.plan + (size_t)a * kNSlot;
     if (tid < kNSlot) {
       const int o = c_slot_order[tid];
@@ -497,20 +495,21 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
         const float h = Ah[il];
         lane_set(L, g, B, sl, ca + il, Ax[il], h);
         const float H = g.gamma * h;
-        d_lo = di - H - B.pad;
-        d_hi = di + H + B.pad;
+        d_lo = di - H - padw;
+        d_hi = di + H + padw;
       }
       const float w_lo = warp_min(d_lo), w_hi = warp_max(d_hi);
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
       const float offv = cs.offv[q];
-      const int lo = s0 + ((o == kSelfSlot) ? warp_first_true(len, lane, [&](int e) {
-                             return staged_proj(Sx[s0 + e], ux, uy, uz, sl.s, offv) > w_lo;
-                           })
-                                            : 0);
-      const int hi = s0 + warp_first_true(len, lane, [&](int e) {
-                       return staged_proj(Sx[s0 + e], ux, uy, uz, sl.s, offv) >= w_hi;
-                     });
       const int J0q = cs.J0[q], nbq = cs.nb_[q], cbq = cs.cb_[q];
+      auto proj = [&](int e) {  // projection of staged element e, as sorted
+        return moved ? proj_asc(g, sl.k, sl.s, cbq, nbq, J0q + e, offv)
+                     : staged_proj(Sx[s0 + e], ux, uy, uz, sl.s, offv);
+      };
+      const int lo = s0 + ((o == kSelfSlot)
+                               ? warp_first_true(len, lane, [&](int e) { return proj(e) > w_lo; })
+                               : 0);
+      const int hi = s0 + warp_first_true(len, lane, [&](int e) { return proj(e) >= w_hi; });
       const size_t kbq = (size_t)sl.k * g.n + cbq;
       auto jidx = [&](int j) {
         return cbq + (int)g.perm[kbq + order_pos(sl.s, J0q + j - s0, nbq)];
@@ -581,8 +580,8 @@ __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
       lane_set(L, g, B, sl, si, g.xm[si], h);
       const float di = sl.s * g.dist[kbase + ca + pos_i];
       const float H = g.gamma * h;
-      d_lo = di - H - B.pad;
-      d_hi = di + H + B.pad;
+      d_lo = di - H - window_pad(g, B, g.cell_box[a]);
+      d_hi = di + H + window_pad(g, B, g.cell_box[a]);
     }
     const float w_lo = warp_min(d_lo), w_hi = warp_max(d_hi);
     for (int j0 = tk.j0; j0 < tk.j1; j0 += kTileJ) {

@@ -154,8 +154,73 @@ __global__ void k_scatter(GridDev g, const double* __restrict__ pos, const float
   float mv = m ? m[p] : m_uniform;
   float mn = mmax > 0.0f ? mv / mmax : 0.0f;
   g.xm[s] = make_float4(off[0], off[1], off[2], mn);
+  g.xm_ref[s] = g.xm[s];
   g.hs[s] = h[p];
   g.orig[s] = p;
+}
+
+// New positions and smoothing lengths for the sorted grid (pv_update_positions):
+// particle p keeps its cell and slot; its offset is taken from that cell's
+// centre (nearest periodic image), and its displacement from the offset at the
+// sort raises the box's largest displacement.
+__global__ void k_update(GridDev g, const double* __restrict__ pos,
+                         const float* __restrict__ h) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  float disp = 0.0f;
+  int bx = -1;
+  if (p < g.n) {
+    const int cell = g.pcell[p];
+    bx = g.cell_box[cell];
+    const BoxDev B = g.boxes[bx];
+    const int s = g.cell_start[cell] + g.prank[p];
+    const int loc = cell - B.cell_base;
+    const int c3[3] = {loc / (B.nc * B.nc), (loc / B.nc) % B.nc, loc % B.nc};
+    uint32_t flags = 0;
+    float off[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      double x = pos[3 * (size_t)p + c];
+      if (!isfinite(x)) { flags |= PV_FLAG_BAD_POSITION; x = 0.0; }
+      if (!(x >= 0.0 && x < B.L)) x = wrap_coord(x, B.L);
+      double d = fma(-(c3[c] + 0.5), B.edge, x);  // as at the sort for an unmoved particle
+      d -= B.L * rint(d * B.inv_L);               // nearest image of the cell centre
+      off[c] = (float)d;
+      g.pos64[3 * (size_t)s + c] = x;
+    }
+    float hv = h[p];
+    if (!(hv > 0.0f) || !isfinite(hv)) {
+      flags |= PV_FLAG_BAD_SMOOTHING;
+      hv = 0.0f;
+    }
+    const float4 r = g.xm_ref[s];
+    const float dx = off[0] - r.x, dy = off[1] - r.y, dz = off[2] - r.z;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    // FP32 rounding of the norm and of the offsets: a relative and an
+    // absolute margin keep disp above the exact displacement
+    disp = d2 > 0.0f ? fmaf(sqrtf(d2), 1.0f + 1e-6f, ldexpf(B.edge_f, -20)) : 0.0f;
+    g.xm[s] = make_float4(off[0], off[1], off[2], r.w);
+    g.hs[s] = hv;
+    atomic_max_nonneg(&g.cell_Hmax[cell], g.gamma * hv);
+    if (flags) atomicOr(g.flags, flags);
+  }
+  const int b0 = __shfl_sync(0xffffffffu, bx, 0);
+  if (__all_sync(0xffffffffu, bx == b0 || bx < 0)) {
+    for (int o = 16; o > 0; o >>= 1) disp = fmaxf(disp, __shfl_xor_sync(0xffffffffu, disp, o));
+    if ((threadIdx.x & 31) == 0 && disp > 0.0f && b0 >= 0) atomic_max_nonneg(&g.box_disp[b0], disp);
+  } else if (bx >= 0 && disp > 0.0f) {
+    atomic_max_nonneg(&g.box_disp[bx], disp);
+  }
+}
+
+// Every cell must keep H_max + 2 delta within its edge (delta: the box's
+// largest displacement since the sort), else the 27-cell stencil of the last
+// sort no longer holds all pairs in range.
+__global__ void k_update_check(GridDev g) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell || g.cell_count[c] == 0) return;
+  const int bx = g.cell_box[c];
+  const BoxDev& B = g.boxes[bx];
+  if (g.cell_Hmax[c] + window_pad(g, B, bx) > B.edge_f) atomicOr(g.flags, PV_FLAG_SKIN_EXCEEDED);
 }
 
 __device__ __forceinline__ bool key_less(float ka, int oa, float kb, int ob) {
@@ -403,6 +468,15 @@ cudaError_t launch_scatter(const GridDev& g, const double* pos, const float* h, 
                            float m_uniform, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
   k_scatter<<<(g.n + 255) / 256, 256, 0, st>>>(g, pos, h, m, m_uniform);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const GridDev& g, const double* pos, const float* h, cudaStream_t st) {
+  if (g.n == 0) return cudaSuccess;
+  k_update<<<(g.n + 255) / 256, 256, 0, st>>>(g, pos, h);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_update_check<<<(g.ncell + 255) / 256, 256, 0, st>>>(g);
   return cudaGetLastError();
 }
 

@@ -65,6 +65,7 @@ struct GridDev {
   int32_t* prank;
   // per particle, cell order
   float4* xm;
+  float4* xm_ref;  // [N] xm at the last sort (reference of pv_update_positions)
   float* hs;
   int32_t* orig;
   double* pos64;
@@ -92,6 +93,7 @@ struct GridDev {
   // scalars
   uint32_t* flags;
   float* m_max;     // [n_boxes] largest mass of each box (mass unit of the accumulators)
+  float* box_disp;  // [n_boxes] largest displacement since the last sort (0 right after it)
   int32_t* max_count;
   unsigned long long* counters;  // [0] interactions, [1] guard pairs, [2] candidates,
                                  // [3] adjoint candidates, [4] adjoint pairs,
@@ -342,6 +344,19 @@ __device__ __forceinline__ void stage_flat(const int* off, int total, int tid, i
   }
 }
 
+// Projection of the t-th particle of cell c (start cs, count cnt) in the
+// ascending-along-u order of slot (k, s), plus the cell shift `off`.
+__device__ __forceinline__ float proj_asc(const GridDev& g, int k, int s, int cs, int cnt, int t,
+                                          float off) {
+  return s * g.dist[(size_t)k * g.n + cs + order_pos(s, t, cnt)] + off;
+}
+
+// Widening of every sorted window in box `bx`: projection rounding plus twice
+// the largest displacement since the last sort.
+__device__ __forceinline__ float window_pad(const GridDev& g, const BoxDev& B, int bx) {
+  return B.pad + 2.0f * g.box_disp[bx];
+}
+
 // ---- host-side launchers (defined in the .cu files) ------------------------
 cudaError_t launch_bin(const GridDev& g, const double* pos, const float* h, const float* m,
                        float m_uniform, cudaStream_t st);
@@ -349,6 +364,7 @@ cudaError_t launch_scan(const GridDev& g, cudaStream_t st);
 cudaError_t launch_scatter(const GridDev& g, const double* pos, const float* h, const float* m,
                            float m_uniform, cudaStream_t st);
 cudaError_t launch_sort(const GridDev& g, cudaStream_t st);
+cudaError_t launch_update(const GridDev& g, const double* pos, const float* h, cudaStream_t st);
 // Per-(cell, slot) plan, then per-cell routing: cells whose staged windows fit
 // `smem_budget` bytes (elem_j bytes per staged particle, elem_a per particle
 // of the cell) go to the cell-centric kernel, the others are split into tasks.

@@ -36,7 +36,7 @@ constexpr size_t scratch_bytes(int64_t n, int64_t c) {
          align_up(C * sizeof(float)) +
          align_up(pv::kNSlot * C * sizeof(int4)) + 2 * align_up(C * sizeof(int32_t)) +  // plan
          2 * align_up(N * sizeof(int32_t)) +          // pcell, prank
-         align_up(N * sizeof(float4)) + align_up(N * sizeof(float)) +
+         2 * align_up(N * sizeof(float4)) + align_up(N * sizeof(float)) +
          align_up(N * sizeof(int32_t)) + align_up(3 * N * sizeof(double)) +
          align_up(pv::kNDir * N * sizeof(uint16_t)) + align_up(pv::kNDir * N * sizeof(float)) +
          align_up(3 * N * sizeof(long long)) +
@@ -140,6 +140,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.pcell = carve<int32_t>(cur, N);
   d.prank = carve<int32_t>(cur, N);
   d.xm = carve<float4>(cur, N);
+  d.xm_ref = carve<float4>(cur, N);
   d.hs = carve<float>(cur, N);
   d.orig = carve<int32_t>(cur, N);
   d.pos64 = carve<double>(cur, 3 * N);
@@ -154,6 +155,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   if ((size_t)(cur - static_cast<unsigned char*>(base)) > kScratchBytes) return PV_ERR_TOO_LARGE;
   d.flags = reinterpret_cast<uint32_t*>(sc + 0);
   d.m_max = reinterpret_cast<float*>(sc + 1);  // one box
+  d.box_disp = reinterpret_cast<float*>(sc + 9);  // one box, zero (the scalars are cleared)
   d.max_count = sc + 2;
   d.n_big = sc + 3;
   d.ntask = sc + 4;

@@ -32,7 +32,7 @@ EXPORTS = ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
            "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
            "pv_status_str", "pv_last_cuda_error", "pv_density_static", "pv_grid_time_sweeps",
            "pv_grid_sweep_times", "pv_grid_set_tuning", "pv_grid_get_tuning",
-           "pv_grid_set_slot_mask", "pv_raw_interactions")
+           "pv_grid_set_slot_mask", "pv_raw_interactions", "pv_update_positions")
 STATIC_MAX_PARTICLES = 65536
 STATIC_MAX_CELLS = 4096
 
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pv_grid_stats.argtypes = [vp, ctypes.POINTER(pv_stats)]
     lib.pv_grid_time_sweeps.argtypes = [vp, i32]
     lib.pv_grid_set_slot_mask.argtypes = [vp, ctypes.c_uint32]
+    lib.pv_update_positions.argtypes = [vp, vp, vp, vp]
     lib.pv_raw_interactions.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_float,
                                         ctypes.c_int32, vp, vp]
     lib.pv_grid_set_tuning.argtypes = [vp, ctypes.POINTER(pv_tuning)]
@@ -102,7 +103,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
                  "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
                  "pv_grid_time_sweeps", "pv_grid_sweep_times", "pv_grid_set_tuning",
-                 "pv_grid_get_tuning", "pv_grid_set_slot_mask", "pv_raw_interactions"):
+                 "pv_grid_get_tuning", "pv_grid_set_slot_mask", "pv_raw_interactions",
+                 "pv_update_positions"):
         getattr(lib, name).restype = i32
     lib.pv_status_str.argtypes = [i32]
     lib.pv_status_str.restype = ctypes.c_char_p
@@ -191,6 +193,11 @@ def pv_grid_get_tuning(grid: int) -> tuple[int, int]:
 
 
 SLOT_MASK_ALL = (1 << 27) - 1
+FLAG_SKIN_EXCEEDED = 16
+
+
+def pv_update_positions(grid: int, pos: int, h: int, stream: int = 0) -> None:
+    _check(load_library().pv_update_positions(grid, pos, h, stream), "pv_update_positions")
 
 
 def pv_raw_interactions(xi: int, n_i: int, xj: int, n_j: int, H: float, reps: int, out: int,
@@ -331,6 +338,14 @@ class Grid:
         hp = self._dev(h, torch.float32, (self.n,), "h")
         mp = None if m is None else self._dev(m, torch.float32, (self.n,), "m")
         pv_sort_cells(self.handle, p, hp, mp, m_uniform, self._stream(stream))
+
+    def update(self, pos, h, stream=None) -> None:
+        """New positions and smoothing lengths, keeping the last sort (windows
+        widen by twice the largest displacement since it)."""
+        import torch
+        p = self._dev(pos, torch.float64, (self.n, 3), "pos")
+        hp = self._dev(h, torch.float32, (self.n,), "h")
+        pv_update_positions(self.handle, p, hp, self._stream(stream))
 
     def density(self, rho=None, drho_dh=None, n_ngb=None, stream=None):
         import torch

@@ -71,6 +71,7 @@ def test_argument_errors_return_before_device_work(lib):
     assert lib.pv_grid_stats(None, None) == 1
     assert lib.pv_grid_time_sweeps(None, 1) == 1
     assert lib.pv_grid_set_slot_mask(None, 1) == 1
+    assert lib.pv_update_positions(None, None, None, None) == 1
     assert lib.pv_raw_interactions(None, 4, None, 4, ctypes.c_float(1.0), 1, None, None) == 1
     assert lib.pv_raw_interactions(None, -1, None, 4, ctypes.c_float(1.0), 1, None, None) == 1
     assert lib.pv_raw_interactions(None, 0, None, 0, ctypes.c_float(0.0), 1, None, None) == 1
