@@ -179,6 +179,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   if (mt > 0x7fffffffLL) return PV_ERR_TOO_LARGE;
   d.max_tasks = (int32_t)mt;
   d.slot_mask = pv::kAllSlots;
+  d.moved = 0;
   PV_TRY(dev_alloc(g, &d.tasks, (size_t)d.max_tasks));
   // scalars in one allocation
   int32_t* sc;
@@ -275,7 +276,8 @@ pv_status pv_sort_cells(pv_grid* g, const double* pos, const float* h, const flo
   PV_CUDA(pv::launch_scan(d, st));
   PV_CUDA(pv::launch_scatter(d, pos, h, m, m_uniform, st));
   PV_CUDA(pv::launch_sort(d, st));
-  g->launches += g->n > 0 ? 5 : 1;
+  d.moved = 0;
+  g->launches += g->n > 0 ? 5 : 1;  // bin, scan, scatter, small-cell sort, big-cell sort
   g->sorted = true;
   return PV_OK;
 }
@@ -289,6 +291,7 @@ pv_status pv_update_positions(pv_grid* g, const double* pos, const float* h, voi
   PV_CUDA(cudaMemsetAsync(d.cell_Hmax, 0, (size_t)g->ncell * sizeof(float), st));
   PV_CUDA(cudaMemsetAsync(d.box_disp, 0, g->boxes.size() * sizeof(float), st));
   PV_CUDA(pv::launch_update(d, pos, h, st));
+  d.moved = 1;
   g->launches += g->n > 0 ? 2 : 0;  // update, update_check
   return PV_OK;
 }

@@ -356,9 +356,6 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
     const BoxDev B = g.boxes[g.cell_box[a]];
     const float mscale = munit * g.m_max[g.cell_box[a]];
     const float padw = window_pad(g, B, g.cell_box[a]);
-    // after pv_update_positions the staged positions are no longer in sorted
-    // order: the window searches then read the sort's projections
-    const bool moved = g.box_disp[g.cell_box[a]] > 0.0f;
     const int4* pl = g.plan + (size_t)a * kNSlot;
     if (tid < kNSlot) {
       const int o = c_border[tid];
@@ -441,9 +438,11 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
       const float offv = cs.offv[q];
       const int J0q = cs.J0[q], nbq = cs.nb_[q], cbq = cs.cb_[q];
+      // after pv_update_positions the staged positions are no longer in sorted
+      // order: the window searches then read the sort's projections
       auto proj = [&](int e) {  // projection of staged element e, as sorted
-        return moved ? proj_asc(g, sl.k, sl.s, cbq, nbq, J0q + e, offv)
-                     : sproj(Sx[s0 + e], ux, uy, uz, sl.s, offv);
+        return g.moved ? proj_asc(g, sl.k, sl.s, cbq, nbq, J0q + e, offv)
+                       : sproj(Sx[s0 + e], ux, uy, uz, sl.s, offv);
       };
       const int lo = s0 + ((o == kSelfSlot)
                                ? warp_first_true(len, lane, [&](int e) { return proj(e) > w_lo; })
@@ -587,7 +586,9 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   const int nb = (g.n + 255) / 256;
   k_bwd_prep<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_plan(g, 1, smem - kCellFixedSmem, kElemJ, kElemA, st)) != cudaSuccess) return e;
+  if ((e = launch_plan(g, 1, smem - kCellFixedSmem, kElemJ, kElemA, st)) !=
+      cudaSuccess)
+    return e;
   if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
   k_backward_cells<<<num_sms * ctas_per_sm, kCellThreads, smem, st>>>(g, g_rho, g_drho_dh, g_pos,
                                                                        g_h);

@@ -409,9 +409,6 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
     const BoxDev B = g.boxes[g.cell_box[a]];
     const float mscale = munit * g.m_max[g.cell_box[a]];
     const float padw = window_pad(g, B, g.cell_box[a]);
-    // after pv_update_positions the staged positions are no longer in sorted
-    // order: the window searches then read the sort's projections
-    const bool moved = g.box_disp[g.cell_box[a]] > 0.0f;
     const int4* pl = g.plan + (size_t)a * kNSlot;
     if (tid < kNSlot) {
       const int o = c_slot_order[tid];
@@ -502,9 +499,11 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
       const int s0 = cs.off[q], len = cs.off[q + 1] - s0;
       const float offv = cs.offv[q];
       const int J0q = cs.J0[q], nbq = cs.nb_[q], cbq = cs.cb_[q];
+      // after pv_update_positions the staged positions are no longer in sorted
+      // order: the window searches then read the sort's projections
       auto proj = [&](int e) {  // projection of staged element e, as sorted
-        return moved ? proj_asc(g, sl.k, sl.s, cbq, nbq, J0q + e, offv)
-                     : staged_proj(Sx[s0 + e], ux, uy, uz, sl.s, offv);
+        return g.moved ? proj_asc(g, sl.k, sl.s, cbq, nbq, J0q + e, offv)
+                       : staged_proj(Sx[s0 + e], ux, uy, uz, sl.s, offv);
       };
       const int lo = s0 + ((o == kSelfSlot)
                                ? warp_first_true(len, lane, [&](int e) { return proj(e) > w_lo; })
@@ -826,7 +825,8 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
                                        kCellSmemFor[1]);
   if (e != cudaSuccess) return e;
   const int smem = kCellSmemFor[ctas_per_sm];
-  if ((e = launch_plan(g, 0, smem - kCellFixedSmem, kCellElemJ, kCellElemA, st)) != cudaSuccess)
+  if ((e = launch_plan(g, 0, smem - kCellFixedSmem, kCellElemJ, kCellElemA,
+                       st)) != cudaSuccess)
     return e;
   if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
   k_density_cells<<<num_sms * ctas_per_sm, kCellThreads, smem, st>>>(g, rho, drho_dh, n_ngb);

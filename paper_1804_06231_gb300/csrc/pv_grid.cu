@@ -13,11 +13,12 @@
 //   k_scan     exclusive scan of the occupancies, list of big cells
 //   k_scatter  cell-order copies: FP32 offsets + normalised mass, h, caller
 //              index, wrapped FP64 position
-//   k_sort_small  one CTA per cell of <= 512 particles, one warp per axis:
+//   k_sort_small  one CTA per cell of <= 384 particles, one warp per axis:
 //              bucket (counting) sort in shared memory, exact order inside a
 //              bucket by (projection, caller index)
-//   k_sort_big    one CTA per larger cell, axes in turn, same algorithm with
-//              the buckets in global scratch
+//   k_sort_big    one CTA per (larger cell, axis), the same algorithm with up
+//              to 8192 buckets in shared memory
+//   k_update, k_update_check  new positions on a kept sort (pv_update_positions)
 #include <cuda_runtime.h>
 
 #include "pv_internal.cuh"
@@ -26,7 +27,9 @@ namespace pv {
 
 namespace {
 
-constexpr int kSortSmallMax = 512;
+// cells of up to kSortSmallMax particles sort in one CTA (74 KB of shared
+// memory, three CTAs per SM); larger ones with one CTA per (cell, axis)
+constexpr int kSortSmallMax = 384;
 constexpr int kSortThreads = kNDir * 32;
 
 __device__ __forceinline__ int box_of_particle(const GridDev& g, int p) {
@@ -315,17 +318,34 @@ __device__ void sort_axis(int cnt, const int* orig, const float* key, Idx* tmp, 
   group_sync<kBlock>();
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
+// Shared memory of k_sort_small<kMax>: staged particles, keys, buckets (a
+// power of two >= kMax), and the 16-bit index arrays of the 13 axes.
+template <int kMax>
+__host__ __device__ constexpr int sort_small_buckets() {
+  return kMax <= 32 ? 32 : 2 * sort_small_buckets<(kMax + 1) / 2>();
+}
+template <int kMax>
+constexpr size_t sort_small_smem() {
+  return (size_t)kMax * (sizeof(float4) + sizeof(int)) +
+         (size_t)kNDir * (kMax * (sizeof(float) + 2 * sizeof(uint16_t)) +
+                          sort_small_buckets<kMax>() * sizeof(int));
+}
+
+// One CTA per cell with lo < count <= kMax, one warp per axis.  The smaller
+// instances use less shared memory, so more CTAs share an SM.
+template <int kMax>
+__global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g, int lo) {
+  constexpr int kB = sort_small_buckets<kMax>();
   extern __shared__ float4 smem4[];
-  float4* s_x = smem4;                                                 // [512]
-  int* s_orig = reinterpret_cast<int*>(s_x + kSortSmallMax);            // [512]
-  float* s_key = reinterpret_cast<float*>(s_orig + kSortSmallMax);      // [13][512]
-  int* s_bkt = reinterpret_cast<int*>(s_key + kNDir * kSortSmallMax);   // [13][512]
-  uint16_t* s_out = reinterpret_cast<uint16_t*>(s_bkt + kNDir * kSortSmallMax);  // [13][512]
-  uint16_t* s_tmp = s_out + kNDir * kSortSmallMax;                     // [13][512]
+  float4* s_x = smem4;                                           // [kMax]
+  int* s_orig = reinterpret_cast<int*>(s_x + kMax);              // [kMax]
+  float* s_key = reinterpret_cast<float*>(s_orig + kMax);        // [13][kMax]
+  int* s_bkt = reinterpret_cast<int*>(s_key + kNDir * kMax);     // [13][kB]
+  uint16_t* s_out = reinterpret_cast<uint16_t*>(s_bkt + kNDir * kB);  // [13][kMax]
+  uint16_t* s_tmp = s_out + kNDir * kMax;                        // [13][kMax]
   const int c = blockIdx.x;
   const int cnt = g.cell_count[c];
-  if (cnt == 0 || cnt > kSortSmallMax) return;
+  if (cnt <= lo || cnt > kMax) return;
   const int cs = g.cell_start[c];
   for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
     s_x[t] = g.xm[cs + t];
@@ -335,10 +355,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g) {
   const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float ux, uy, uz;
   axis_u(k, ux, uy, uz);
-  float* key = s_key + k * kSortSmallMax;
-  uint16_t* out = s_out + k * kSortSmallMax;
-  uint16_t* tmp = s_tmp + k * kSortSmallMax;
-  int* bkt = s_bkt + k * kSortSmallMax;
+  float* key = s_key + k * kMax;
+  uint16_t* out = s_out + k * kMax;
+  uint16_t* tmp = s_tmp + k * kMax;
+  int* bkt = s_bkt + k * kB;
   float kmin = 3.0e38f, kmax = -3.0e38f;
   for (int t = lane; t < cnt; t += 32) {
     float d = project(s_x[t], ux, uy, uz);
@@ -480,19 +500,20 @@ cudaError_t launch_update(const GridDev& g, const double* pos, const float* h, c
   return cudaGetLastError();
 }
 
+template <int kMax>
+cudaError_t launch_sort_small(const GridDev& g, int lo, cudaStream_t st) {
+  static std::atomic<unsigned long long> smem_done{0};
+  constexpr int smem = (int)sort_small_smem<kMax>();
+  cudaError_t e = set_max_dynamic_smem(smem_done, reinterpret_cast<const void*>(&k_sort_small<kMax>),
+                                       smem);
+  if (e != cudaSuccess) return e;
+  k_sort_small<kMax><<<g.ncell, kSortThreads, smem, st>>>(g, lo);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sort(const GridDev& g, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
-  const size_t smem = kSortSmallMax * (sizeof(float4) + sizeof(int)) +
-                      kNDir * kSortSmallMax * (sizeof(float) + sizeof(int) + 2 * sizeof(uint16_t));
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  k_sort_small<<<g.ncell, kSortThreads, smem, st>>>(g);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_sort_small<kSortSmallMax>(g, 0, st);
   if (e != cudaSuccess) return e;
   k_sort_big<<<512, kSortBigThreads, 0, st>>>(g);
   return cudaGetLastError();

@@ -90,6 +90,7 @@ struct GridDev {
   int32_t* task_next;
   int32_t max_tasks;
   uint32_t slot_mask;  // neighbour slots the sweeps visit (bit o of slot o; all 27 normally)
+  int32_t moved;       // positions updated since the sort: windows use the stored projections
   // scalars
   uint32_t* flags;
   float* m_max;     // [n_boxes] largest mass of each box (mass unit of the accumulators)

@@ -149,6 +149,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.acc = carve<long long>(cur, 3 * N);
   d.max_tasks = (int32_t)pv::max_tasks_for(n, ncell);
   d.slot_mask = pv::kAllSlots;
+  d.moved = 0;
   d.tasks = carve<int4>(cur, (size_t)d.max_tasks);
   int32_t* sc = carve<int32_t>(cur, 16);
   d.counters = carve<unsigned long long>(cur, 16);
