@@ -289,13 +289,6 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
   }
 }
 
-// per-particle data a staged window element is built from
-struct StagedB {
-  float4 x;  // xm
-  float4 k;  // gk: G, K, H^2 + guard, H^2 - guard
-  float H;
-};
-
 __device__ __forceinline__ float4 staged_b(float4 x) {
   return make_float4(x.x, x.y, x.z, fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z)));
 }
@@ -398,12 +391,22 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
           const int pos = order_pos(sl.s, cs.J0[q] + f - cs.off[q], cs.nb_[q]);
           return cb + (int)g.perm[(size_t)sl.k * g.n + cb + pos];
         },
-        [&](int sj) { return StagedB{g.xm[sj], g.gk[sj], g.ghh[sj].y}; },
-        [&](int f, const StagedB& v) {
-          Sx[f] = staged_b(v.x);
-          Sa[f] = make_float4(v.x.w, v.k.x, v.k.y, v.H);
-          Se[f] = v.k.z;  // H_j^2 + guard_j
+        [](int sj) { return sj; },
+        [&](int f, int sj) {  // cp.async: xm, gk and H straight to shared memory
+          cp_async16(&Sx[f], &g.xm[sj]);
+          cp_async16(&Sa[f], &g.gk[sj]);
+          cp_async4(&Se[f], &g.ghh[sj].y);
         });
+    cp_async_wait_all();
+    // each thread rearranges its own elements: Sx {x, y, z, |x|^2},
+    // Sa {m, G, K, H}, Se {H^2 + guard}
+    for (int f = tid; f < total; f += kCellThreads) {
+      const float4 x = Sx[f], k = Sa[f];
+      const float H = Se[f];
+      Sx[f] = staged_b(x);
+      Sa[f] = make_float4(x.w, k.x, k.y, H);
+      Se[f] = k.z;
+    }
     for (int t = tid; t < 5 * na; t += kCellThreads) acc[t] = 0.0;
     __syncthreads();
     const int nitems = cs.runs[kNSlot];

@@ -446,6 +446,8 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
     float* Ah = Sm + total + kPad;                             // [na]
     int* acc_n = reinterpret_cast<int*>(Ah + na);              // [na]
     // stage the 27 windows in sorted order, and cell a in cell order
+    // (synchronous loads, three lookups in flight per thread: measured 2 %
+    // faster here than cp.async, which the adjoint kernel uses)
     stage_flat<3>(
         cs.off, total, tid, kCellThreads,
         [&](int f, int q) {

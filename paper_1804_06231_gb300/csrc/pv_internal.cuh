@@ -314,6 +314,22 @@ static __device__ __forceinline__ bool guard_inside(const double* __restrict__ p
   return r2 < Hd * Hd;
 }
 
+// Asynchronous global -> shared copies (cp.async): the data goes to shared
+// memory without passing through registers, so a thread can have many in
+// flight.  16-byte copies are cached in L2 only (.cg); 4-byte ones in L1 too.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// Waits for all of this thread's cp.async copies.
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // Stages the windows of a cell, one flat range [0, total) with window q at
 // [off[q], off[q+1]): thread t takes elements t, t + nthr, ... (so every warp
 // stays full across window boundaries), follows its window index forward
