@@ -30,8 +30,13 @@ if ROOT not in sys.path:
 METRIC = "density-loop pair interactions/s"
 UNIT = "interactions/s"
 WORKLOAD = "uniform N=1048576, 15^3 cells, h=1.2348 N^-1/3 U(0.9,1.1), sort+density+backward"
-# algorithmic FP32 work: flops per window candidate and per
-# in-range pair of the forward sweep, per candidate and per pair of the adjoint
+# Algorithmic FP32 work (an FMA counts 2).  Forward: a window candidate is a
+# distance test (3 sub, r^2 by 1 mul + 2 fma, compare = 9); a pair in range
+# adds q, the two cubic pieces, the select and two accumulations (23).
+# Adjoint: a candidate also takes the max of two squared supports (10); each
+# own pair adds r, q, the four kernel factors and three accumulations (24),
+# each transposed pair its two factors and its term (11), and each pair of
+# the union the three gradient FMAs (6).
 FWD_FLOP_CAND, FWD_FLOP_PAIR = 9, 23
 BWD_FLOP_CAND, BWD_FLOP_OWN, BWD_FLOP_TRANS, BWD_FLOP_PAIR = 10, 24, 11, 6
 FP32_LANES_PER_SM = 128
@@ -77,7 +82,7 @@ def profiled_traffic(kernel):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="pv", choices=["pv", "reference"])
     p.add_argument("--no-e2e", action="store_true")
@@ -109,21 +114,24 @@ def measured_peaks():
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling (every 20 ms, timestamped) of SM clock and throttle
+    reasons; stop() summarises the samples taken inside [t0, t1] (host wall
+    clock, set by mark_start / mark_stop)."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, uuid: str | None):
+        import tempfile
         self.proc = None
         self.uuid = uuid
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"pv_bench_clocks_{os.getpid()}.csv")
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                   "-lms", "200"]
+                   "-lms", "20"]
             if self.uuid:
                 cmd += ["-i", self.uuid]
             self.f = open(self.path, "w")
@@ -131,7 +139,16 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
+    def mark_start(self):
+        import datetime
+        self.t0 = datetime.datetime.now()
+
+    def mark_stop(self):
+        import datetime
+        self.t1 = datetime.datetime.now()
+
     def stop(self) -> dict:
+        import datetime
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -140,24 +157,37 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 8:
+                if len(parts) < 9:
                     continue
+                t = None
+                for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+                    try:
+                        t = datetime.datetime.strptime(parts[0], fmt)
+                        break
+                    except ValueError:
+                        pass
                 try:
-                    sm.append(float(parts[0]))
-                    smax.append(float(parts[1]))
+                    rows.append((t, float(parts[1]), float(parts[2]), parts[5:9]))
                 except ValueError:
                     continue
-                for nm, v in zip(names, parts[4:8]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        pad = datetime.timedelta(milliseconds=25)
+        inside = [r for r in rows if r[0] and self.t0 and self.t1 and
+                  self.t0 - pad <= r[0] <= self.t1 + pad]
+        use = inside or [r for r in rows if r[0] and self.t0 and r[0] >= self.t0] or rows
+        reasons = set()
+        for r in use:
+            for nm, v in zip(names, r[3]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median([r[1] for r in use]) if use else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "reasons": sorted(reasons), "samples": len(use),
+                "samples_in_timed_region": len(inside)}
 
 
 # ------------------------------------------------------------------ workloads
@@ -336,6 +366,22 @@ def sort_reuse(grid, box, pos, h, m_uniform, flush, density, backward, dev, K: i
             "step_ms_with_update": t_step, "displacement": "<= 0.05 H_max"}
 
 
+def graph_step(step, flush, K: int = 20) -> dict:
+    """The step captured once in a CUDA graph and replayed (L2 flushed before
+    each replay, outside the events); same kernels, no per-launch host work."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()  # eager warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    return {"ms_per_step": timed_steps(graph.replay, flush, K)}
+
+
 def orientation_breakdown(grid, st, flush, density, K: int = 5) -> dict:
     """Density pass restricted to each neighbour orientation class in turn
     (slot masks): time, window distance tests and interactions per class."""
@@ -493,9 +539,11 @@ def main():
     torch.cuda.synchronize()
     if clocks:
         clocks.start()
-        time.sleep(0.4)
+        time.sleep(0.3)  # nvidia-smi up and sampling
     launches0 = grid.stats().kernel_launches
     grid.time_sweeps(True)  # CUDA events around the two sweep kernels
+    if clocks:
+        clocks.mark_start()
     wall0 = time.perf_counter()
     for k in range(K):
         flush.zero_()  # evict the previous step's data from L2 (outside the events)
@@ -509,6 +557,9 @@ def main():
         e[3].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
+    if clocks:
+        clocks.mark_stop()
+        time.sleep(0.05)
     if ws > 1:
         dist.barrier()
     clk = clocks.stop() if clocks else None
@@ -591,6 +642,7 @@ def main():
         extras = {"orientation_breakdown": orientation_breakdown(
                       grid, st_c, flush, lambda: grid.density(rho, drho, nngb)),
                   "raw_interaction_ceiling": raw_ceiling(dev, props, peak_tflops),
+                  "cuda_graph_step": graph_step(step, flush),
                   "sort_reuse": sort_reuse(grid, box, pos, h, m_uniform, flush,
                                            lambda: grid.density(rho, drho, nngb),
                                            lambda: grid.backward(g_rho, g_d, gpos, gh), dev)}
