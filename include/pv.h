@@ -22,9 +22,11 @@
  * stream (a cudaStream_t passed as void*, NULL = the legacy default stream)
  * unless stated otherwise; argument errors are returned synchronously and
  * nothing is launched.  Errors found by the kernels (a support larger than
- * the cell edge, a non-finite position, a cell above PV_MAX_CELL_COUNT) are
- * latched in a device status word and returned by the next call that
- * synchronises (pv_grid_stats, pv_grid_sync) as PV_ERR_DEVICE.
+ * the cell edge, a non-finite position, a cell above PV_MAX_CELL_COUNT, a
+ * displacement beyond the skin of a kept sort) are latched in a device status
+ * word; later kernels of the grid then leave their outputs untouched, and the
+ * next call that synchronises (pv_grid_stats, pv_grid_sync) returns
+ * PV_ERR_DEVICE.
  *
  * Thread safety: a pv_grid may be used by one host thread at a time.
  */
@@ -48,7 +50,8 @@ typedef enum {
   PV_ERR_TOO_LARGE = 7         /* more than 2^31 - 1 particles or cells */
 } pv_status;
 
-/* Bits of pv_stats.device_flags (set by the kernels of pv_sort_cells). */
+/* Bits of pv_stats.device_flags (set by the kernels of pv_sort_cells and
+   pv_update_positions; cleared by pv_sort_cells). */
 #define PV_FLAG_SUPPORT_EXCEEDS_CELL 1u /* gamma h_i > L/nc for some particle */
 #define PV_FLAG_BAD_POSITION 2u         /* non-finite position coordinate */
 #define PV_FLAG_BAD_SMOOTHING 4u        /* h_i not finite or not > 0, or m_i not finite */

@@ -211,16 +211,6 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
-// last q in [0, n) with a[q] <= v for a non-decreasing int array with a[0] <= v
-__device__ __forceinline__ int seg_of(const int* a, int n, int v) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (a[mid] <= v) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 // last t in [0, n) with a[t] <= v, for a ascending, a[0] <= v and n <= 32; the
 // whole warp calls it with the same v (one ballot instead of a search)
 __device__ __forceinline__ int warp_seg_of(const int* a, int n, int v, int lane) {

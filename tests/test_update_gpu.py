@@ -116,3 +116,46 @@ def test_update_beyond_the_skin_is_flagged_then_resort_recovers():
         rho, D, n = g.density()
         g.sync()
         assert g.stats().device_flags == 0
+
+
+def test_update_on_a_batched_grid_tracks_each_box(oracle_lib):
+    """Several boxes in one grid, moved by different amounts: each box's
+    windows widen by its own displacement, and every box still matches the
+    oracle on its moved particles."""
+    import torch
+    from paper_1804_06231_gb300.pv import Grid
+    boxes = [I.uniform(20000, 50 + k, nc=None) for k in range(3)]
+    for b in boxes:
+        b.h = (b.h * 0.85).astype(np.float32)
+    moved = [_moved(b, f, 60 + k) for k, (b, f) in enumerate(zip(boxes, (0.0, 0.3, 0.8)))]
+    cat = lambda arrs: np.ascontiguousarray(np.concatenate(arrs))
+    pos, h, m = _tensors(cat([b.pos for b in boxes]), cat([b.h for b in boxes]),
+                         cat([b.m for b in boxes]))
+    npos, = _tensors(cat([p for p, _ in moved]))
+    with Grid([(b.n, b.L, b.nc) for b in boxes]) as g:
+        g.sort(pos, h, m)
+        g.update(npos, h)
+        rho, D, n = (t.cpu().numpy() for t in g.density())
+        assert g.stats().device_flags == 0
+    first = 0
+    for b, (p, _) in zip(boxes, moved):
+        sl = slice(first, first + b.n)
+        ref = oracle_lib.density_cells(p, b.h, b.m, b.L, b.nc)
+        check_density(rho[sl].astype(np.float64), D[sl].astype(np.float64), n[sl], ref)
+        first += b.n
+
+
+def test_update_of_empty_and_single_particle_grids():
+    import torch
+    from paper_1804_06231_gb300.pv import Grid
+    dev = torch.device("cuda", 0)
+    with Grid([(0, 1.0, 3), (1, 1.0, 3)]) as g:
+        pos = torch.tensor([[0.5, 0.5, 0.5]], dtype=torch.float64, device=dev)
+        h = torch.tensor([0.1], dtype=torch.float32, device=dev)
+        g.sort(pos, h, None, 1.0)
+        g.update(pos + 0.01, h)
+        rho, D, n = g.density()
+        g.sync()
+        H = 1.825742 * 0.1
+        assert rho.item() == pytest.approx(8.0 / np.pi / H ** 3, rel=1e-6)
+        assert n.item() == 0
