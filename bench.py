@@ -88,6 +88,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
+    p.add_argument("--workload", default="uniform1m", choices=["uniform1m", "clustered4m"],
+                   help="the timed workload (clustered4m: for profiling the dense-cell paths)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the 4M clustered and 64-box workloads (extra keys)")
     # smaller uniform workloads with the same h rule, for profiler captures
@@ -192,10 +194,12 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ workloads
 
-def workload(seed: int, particles: int = 0, cells: int = 0):
+def workload(seed: int, particles: int = 0, cells: int = 0, name: str = "uniform1m"):
     from paper_1804_06231_gb300 import inputs as I
     if particles:
         return I.uniform(particles, seed, nc=cells or None)
+    if name == "clustered4m":
+        return I.cfg2(I.SEEDS["cfg2"] + seed - 1)
     return I.cfg1(seed)
 
 
@@ -489,7 +493,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     stream = torch.cuda.current_stream()
 
-    box = workload(1 + rank, args.particles, args.cells)  # one box per rank (weak scaling)
+    box = workload(1 + rank, args.particles, args.cells, args.workload)  # one box per rank
     n = box.n
     pos = torch.from_numpy(box.pos).to(dev)
     h = torch.from_numpy(box.h).to(dev)
@@ -635,7 +639,7 @@ def main():
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     peak_src = f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
-    default_size = not (args.particles or args.cells)
+    default_size = not (args.particles or args.cells) and args.workload == "uniform1m"
     pairs = interactions + n  # in-range pairs evaluated, including j = i
     fwd_flops = FWD_FLOP_CAND * candidates + FWD_FLOP_PAIR * pairs
     bwd_flops = (BWD_FLOP_CAND * cand_adj + (BWD_FLOP_OWN + BWD_FLOP_TRANS) * interactions
@@ -652,7 +656,7 @@ def main():
     roofline_fwd = roof("k_density_cells", fwd_flops, k_dens)
 
     extras = None
-    if rank == 0 and ws == 1 and not args.no_extras and not args.particles:
+    if rank == 0 and ws == 1 and not args.no_extras and default_size:
         extras = {"orientation_breakdown": orientation_breakdown(
                       grid, st_c, flush, lambda: grid.density(rho, drho, nngb)),
                   "raw_interaction_ceiling": raw_ceiling(dev, props, peak_tflops),
@@ -680,8 +684,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if not args.particles else
-                       f"uniform N={n}, {box.nc}^3 cells (profiling size)", "n_particles_per_gpu": n, "cells": box.nc ** 3,
+            "config": {"workload": (f"uniform N={n}, {box.nc}^3 cells (profiling size)"
+                                    if args.particles else
+                                    f"clustered N={n}, {box.nc}^3 cells, 64 Gaussians + 20% "
+                                    "uniform, sort+density+backward"
+                                    if args.workload == "clustered4m" else WORKLOAD),
+                       "n_particles_per_gpu": n, "cells": box.nc ** 3,
                        "l2": "flushed between steps (512 MiB write)",
                        "launch_shape": tuning or {"density_ctas_per_sm": 3,
                                                   "backward_ctas_per_sm": 2, "source": "default"},

@@ -109,3 +109,20 @@ def test_autograd_function(oracle_lib):
     assert rel_l2(h.grad.cpu().numpy().astype(np.float64), gh0) <= ADJ_RTOL
     assert np.abs(rho.detach().cpu().numpy() / ref.rho - 1).max() < 1e-5
     grid.close()
+
+
+@pytest.mark.slow
+def test_adjoint_1m_every_particle(oracle_lib):
+    """The benchmark workload (N = 1,048,576 uniform, 15^3 cells): the whole
+    adjoint against the oracle's cell-list adjoint (relative L2 <= 1e-4 for
+    dL/dx and dL/dh) and per particle within 1e-3 of the largest component."""
+    box = I.cfg1()
+    w, v = I.loss_weights(box.n, 3)
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
+    g, k = oracle_lib.loss_upstream(ref.rho, w, v)
+    gp, gh = gpu_adjoint(box, g, k, uniform_mass=True)
+    gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g, k, 1.0, box.nc)
+    assert rel_l2(gp, gp0) <= ADJ_RTOL
+    assert rel_l2(gh, gh0) <= ADJ_RTOL
+    assert np.abs(gp - gp0).max() <= 1e-3 * np.abs(gp0).max()
+    assert np.abs(gh - gh0).max() <= 1e-3 * np.abs(gh0).max()

@@ -260,3 +260,16 @@ def test_raw_interactions_match_oracle_kernel(oracle_lib):
         m = xj[:, 3].astype(np.float64)
         assert out[i, 0] == pytest.approx(c * (m * W).sum(), rel=2e-5)
         assert abs(out[i, 1] + c * h * (m * Wh).sum()) <= 1e-4 * c * h * (m * np.abs(Wh)).sum()
+
+
+@pytest.mark.slow
+def test_clustered_4m_every_particle(oracle_lib):
+    """N = 4,194,304 clustered particles on the finest grid (41^3 cells, up to
+    21,392 particles in a cell: both the cell-centric and the task kernels and
+    the per-axis sort of dense cells): every particle against the oracle's
+    pseudo-Verlet sweep."""
+    box = I.cfg2()
+    rho, D, n, st, _ = run_density(box, uniform_mass=True)
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
+    check_density(rho, D, n, ref)
+    assert abs(st.interactions - int(ref.n_ngb.sum())) <= int(ref.band.sum())
