@@ -126,3 +126,17 @@ def test_adjoint_1m_every_particle(oracle_lib):
     assert rel_l2(gh, gh0) <= ADJ_RTOL
     assert np.abs(gp - gp0).max() <= 1e-3 * np.abs(gp0).max()
     assert np.abs(gh - gh0).max() <= 1e-3 * np.abs(gh0).max()
+
+
+def test_adjoint_box_of_other_size_with_unwrapped_positions(oracle_lib):
+    """Edge L = 3.7, positions anywhere in [-L, 2L), varied masses: the adjoint
+    against the oracle on the same (wrapped by both) positions."""
+    from test_density_gpu import _scaled_wrapped_box
+    box = _scaled_wrapped_box(93)
+    w, v = I.loss_weights(box.n, 4)
+    ref = oracle_lib.density_cells(box.pos, box.h, box.m, box.L, box.nc)
+    g, k = oracle_lib.loss_upstream(ref.rho, w, v)
+    gp, gh = gpu_adjoint(box, g, k)
+    gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g, k, box.L, box.nc)
+    assert rel_l2(gp, gp0) <= ADJ_RTOL
+    assert rel_l2(gh, gh0) <= ADJ_RTOL

@@ -273,3 +273,23 @@ def test_clustered_4m_every_particle(oracle_lib):
     ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
     check_density(rho, D, n, ref)
     assert abs(st.interactions - int(ref.n_ngb.sum())) <= int(ref.band.sum())
+
+
+def _scaled_wrapped_box(seed):
+    """A box of edge L = 3.7 (not 1) whose positions are given anywhere in
+    [-L, 2L) (each coordinate shifted by -L, 0 or +L) with masses in
+    [0.5, 1.5] of the mean."""
+    base = I.uniform(20000, seed, nc=None)
+    L = 3.7
+    rng = np.random.default_rng(seed + 1)
+    pos = base.pos * L + L * rng.integers(-1, 2, (base.n, 3))
+    h = (base.h.astype(np.float64) * L).astype(np.float32)
+    m = (base.m * rng.uniform(0.5, 1.5, base.n)).astype(np.float32)
+    return I.Box(np.ascontiguousarray(pos), h, m, L, base.nc)
+
+
+def test_box_of_other_size_with_unwrapped_positions(oracle_lib):
+    box = _scaled_wrapped_box(91)
+    rho, D, n, _, _ = run_density(box)
+    ref = oracle_lib.density_cells(box.pos, box.h, box.m, box.L, box.nc)
+    check_density(rho, D, n, ref)
