@@ -672,7 +672,8 @@ def main():
         oracle.build()
         cores = host_cores()
         cbox = cpu_sample(0)
-        c_inter, c_times = time_oracle(cbox, 2, 0, cores)
+        # about 10 s of oracle work on 16 cores: 1 warm-up and 10 timed steps
+        c_inter, c_times = time_oracle(cbox, 10, 1, cores)
         cpu = {"value": c_inter / statistics.mean(c_times), "unit": UNIT, "cores": cores,
                "kind": "oracle",
                "sample": cbox.name + "; FP64 pseudo-Verlet density + cell-list adjoint, "

@@ -43,7 +43,6 @@ constexpr int kCellThreads = 256;
 // dynamic shared memory of k_density_cells for 1..4 resident CTAs per SM (the
 // SM's 228 KB less 1 KB reserved and the static part per CTA); 3 by default
 constexpr int kCellSmemFor[5] = {0, 200 * 1024, 110 * 1024, 72 * 1024, 54 * 1024};
-constexpr int kCellSmem = kCellSmemFor[3];
 constexpr int kPad = 32;         // slack after staged arrays for the 32-wide sweep
 
 // slots ordered by expected cost: self, faces, edges, corners
