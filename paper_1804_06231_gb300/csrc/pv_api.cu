@@ -266,18 +266,13 @@ pv_status pv_sort_cells(pv_grid* g, const double* pos, const float* h, const flo
   if (!m && !(m_uniform >= 0.0f && std::isfinite(m_uniform))) return PV_ERR_INVALID_ARGUMENT;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GridDev& d = g->d;
-  const size_t C = (size_t)g->ncell;
-  PV_CUDA(cudaMemsetAsync(d.cell_count, 0, C * sizeof(int32_t), st));
-  PV_CUDA(cudaMemsetAsync(d.cell_Hmax, 0, C * sizeof(float), st));
-  PV_CUDA(cudaMemsetAsync(d.flags, 0, 4 * sizeof(int32_t), st));  // flags, -, max_count, n_big
-  PV_CUDA(cudaMemsetAsync(d.m_max, 0, g->boxes.size() * sizeof(float), st));
-  PV_CUDA(cudaMemsetAsync(d.box_disp, 0, g->boxes.size() * sizeof(float), st));
+  PV_CUDA(pv::launch_clear(d, st));
   PV_CUDA(pv::launch_bin(d, pos, h, m, m_uniform, st));
   PV_CUDA(pv::launch_scan(d, st));
-  PV_CUDA(pv::launch_scatter(d, pos, h, m, m_uniform, st));
-  PV_CUDA(pv::launch_sort(d, st));
+  PV_CUDA(pv::launch_scatter(d, st));
+  PV_CUDA(pv::launch_sort(d, pos, h, m, m_uniform, st));
   d.moved = 0;
-  g->launches += g->n > 0 ? 5 : 1;  // bin, scan, scatter, small-cell sort, big-cell sort
+  g->launches += g->n > 0 ? 6 : 3;  // clear, bin, scan, scatter, cell sort, big-cell sort
   g->sorted = true;
   return PV_OK;
 }

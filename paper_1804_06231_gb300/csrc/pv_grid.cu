@@ -8,12 +8,15 @@
 // frame in double precision and only then converted to single precision.
 //
 // Kernels (all HBM-bound except the sort, which is shared-memory bound):
-//   k_bin      particle -> cell id, occupancy histogram, cell H_max, box m_max,
-//              input checks (latched flags)
+//   k_clear    zeroes the occupancies and the per-sort scalars
+//   k_bin      particle -> cell id, occupancy histogram, box m_max, input
+//              checks (latched flags)
 //   k_scan     exclusive scan of the occupancies, list of big cells
-//   k_scatter  cell-order copies: FP32 offsets + normalised mass, h, caller
-//              index, wrapped FP64 position
-//   k_sort_small  one CTA per cell of <= 384 particles, one warp per axis:
+//   k_scatter  caller index of every cell-order slot
+//   k_cell_sort   one CTA per cell: gathers the cell's particles into cell
+//              order (FP32 offsets + normalised mass, h, wrapped FP64
+//              position) with coalesced writes, the cell's H_max, and, for a
+//              cell of <= 384 particles, the 13 sorts, one warp per axis:
 //              bucket (counting) sort in shared memory, exact order inside a
 //              bucket by (projection, caller index)
 //   k_sort_big    one CTA per (larger cell, axis), the same algorithm with up
@@ -42,11 +45,29 @@ __device__ __forceinline__ int box_of_particle(const GridDev& g, int p) {
   return lo;
 }
 
+__device__ __forceinline__ bool valid_h_m(float hv, float mv) {
+  return hv > 0.0f && isfinite(hv) && mv >= 0.0f && isfinite(mv);
+}
+
 __device__ __forceinline__ double wrap_coord(double x, double L) {
   double y = x - L * floor(x / L);
   if (y >= L) y = 0.0;
   if (y < 0.0) y = 0.0;
   return y;
+}
+
+__global__ void k_clear(GridDev g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < g.ncell) g.cell_count[i] = 0;
+  if (i < g.n_boxes) {
+    g.m_max[i] = 0.0f;
+    g.box_disp[i] = 0.0f;
+  }
+  if (i == 0) {
+    *g.flags = 0u;
+    *g.max_count = 0;
+    *g.n_big = 0;
+  }
 }
 
 __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
@@ -68,17 +89,13 @@ __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __
       c3[c] = ci < 0 ? 0 : (ci >= B.nc ? B.nc - 1 : ci);
     }
     const int cell = B.cell_base + (c3[0] * B.nc + c3[1]) * B.nc + c3[2];
-    float hv = h[p];
+    const float hv = h[p];
     const float mv = m ? m[p] : m_uniform;
-    if (!(hv > 0.0f) || !isfinite(hv) || !(mv >= 0.0f) || !isfinite(mv)) {
-      flags |= PV_FLAG_BAD_SMOOTHING;
-      hv = 0.0f;
-    }
-    if (g.gamma_d * (double)hv > B.edge) flags |= PV_FLAG_SUPPORT_EXCEEDS_CELL;
+    if (!valid_h_m(hv, mv)) flags |= PV_FLAG_BAD_SMOOTHING;
+    else if (g.gamma_d * (double)hv > B.edge) flags |= PV_FLAG_SUPPORT_EXCEEDS_CELL;
     if (flags) atomicOr(g.flags, flags);
     g.pcell[p] = cell;
     g.prank[p] = atomicAdd(&g.cell_count[cell], 1);
-    atomic_max_nonneg(&g.cell_Hmax[cell], g.gamma * hv);
     mw = (mv > 0.0f && isfinite(mv)) ? mv : 0.0f;
   }
   // m_max of a box is one address for all its particles: reduce over the
@@ -133,33 +150,9 @@ __global__ void __launch_bounds__(1024) k_scan(GridDev g) {
   }
 }
 
-__global__ void k_scatter(GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
-                          const float* __restrict__ m, float m_uniform) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= g.n) return;
-  const int cell = g.pcell[p];
-  const BoxDev B = g.boxes[g.cell_box[cell]];
-  const int s = g.cell_start[cell] + g.prank[p];
-  const int loc = cell - B.cell_base;
-  const int c3[3] = {loc / (B.nc * B.nc), (loc / B.nc) % B.nc, loc % B.nc};
-  double xw[3];
-  float off[3];
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    double x = pos[3 * (size_t)p + c];
-    if (!isfinite(x)) x = 0.0;
-    if (!(x >= 0.0 && x < B.L)) x = wrap_coord(x, B.L);
-    xw[c] = x;
-    off[c] = (float)fma(-(c3[c] + 0.5), B.edge, x);  // shift first, then round
-    g.pos64[3 * (size_t)s + c] = xw[c];
-  }
-  const float mmax = g.m_max[g.cell_box[cell]];
-  float mv = m ? m[p] : m_uniform;
-  float mn = mmax > 0.0f ? mv / mmax : 0.0f;
-  g.xm[s] = make_float4(off[0], off[1], off[2], mn);
-  g.xm_ref[s] = g.xm[s];
-  g.hs[s] = h[p];
-  g.orig[s] = p;
+__global__ void k_scatter(GridDev g) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < g.n) g.orig[g.cell_start[g.pcell[p]] + g.prank[p]] = p;
 }
 
 // New positions and smoothing lengths for the sorted grid (pv_update_positions):
@@ -318,7 +311,7 @@ __device__ void sort_axis(int cnt, const int* orig, const float* key, Idx* tmp, 
   group_sync<kBlock>();
 }
 
-// Shared memory of k_sort_small<kMax>: staged particles, keys, buckets (a
+// Shared memory of k_cell_sort<kMax>: staged particles, keys, buckets (a
 // power of two >= kMax), and the 16-bit index arrays of the 13 axes.
 template <int kMax>
 __host__ __device__ constexpr int sort_small_buckets() {
@@ -331,12 +324,22 @@ constexpr size_t sort_small_smem() {
                           sort_small_buckets<kMax>() * sizeof(int));
 }
 
-// One CTA per cell with lo < count <= kMax, one warp per axis.  The smaller
-// instances use less shared memory, so more CTAs share an SM.
+// One CTA per cell.  All threads gather the cell's particles (caller indices
+// in orig) into cell order with coalesced writes: FP32 offsets from the cell
+// centre (Section 3.2: shifted in FP64, then rounded) with the normalised
+// mass, h, the copy kept for pv_update_positions and the wrapped FP64
+// position; the cell's H_max is reduced on the way.  A cell of at most kMax
+// particles is then sorted along the 13 axes from the staged copy, one warp
+// per axis; larger cells are left to k_sort_big.
 template <int kMax>
-__global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g, int lo) {
+__global__ void __launch_bounds__(kSortThreads) k_cell_sort(GridDev g,
+                                                            const double* __restrict__ pos,
+                                                            const float* __restrict__ h,
+                                                            const float* __restrict__ m,
+                                                            float m_uniform) {
   constexpr int kB = sort_small_buckets<kMax>();
   extern __shared__ float4 smem4[];
+  __shared__ unsigned int s_hmax;
   float4* s_x = smem4;                                           // [kMax]
   int* s_orig = reinterpret_cast<int*>(s_x + kMax);              // [kMax]
   float* s_key = reinterpret_cast<float*>(s_orig + kMax);        // [13][kMax]
@@ -345,13 +348,45 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g, int lo) 
   uint16_t* s_tmp = s_out + kNDir * kMax;                        // [13][kMax]
   const int c = blockIdx.x;
   const int cnt = g.cell_count[c];
-  if (cnt <= lo || cnt > kMax) return;
   const int cs = g.cell_start[c];
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    s_x[t] = g.xm[cs + t];
-    s_orig[t] = g.orig[cs + t];
-  }
+  const int bx = g.cell_box[c];
+  const BoxDev B = g.boxes[bx];
+  const int loc = c - B.cell_base;
+  const double ctr[3] = {-((loc / (B.nc * B.nc)) + 0.5), -(((loc / B.nc) % B.nc) + 0.5),
+                         -((loc % B.nc) + 0.5)};
+  const float mmax = g.m_max[bx];
+  if (threadIdx.x == 0) s_hmax = 0u;
   __syncthreads();
+  float hmax = 0.0f;
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const int p = g.orig[cs + t];
+    const size_t s = (size_t)cs + t;
+    float off[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      double x = pos[3 * (size_t)p + k];
+      if (!isfinite(x)) x = 0.0;
+      if (!(x >= 0.0 && x < B.L)) x = wrap_coord(x, B.L);
+      off[k] = (float)fma(ctr[k], B.edge, x);
+      g.pos64[3 * s + k] = x;
+    }
+    const float mv = m ? m[p] : m_uniform;
+    const float hv = h[p];
+    const float4 xm = make_float4(off[0], off[1], off[2], mmax > 0.0f ? mv / mmax : 0.0f);
+    g.xm[s] = xm;
+    g.xm_ref[s] = xm;
+    g.hs[s] = hv;
+    if (valid_h_m(hv, mv)) hmax = fmaxf(hmax, g.gamma * hv);
+    if (cnt <= kMax) {
+      s_x[t] = xm;
+      s_orig[t] = p;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+  if ((threadIdx.x & 31) == 0 && hmax > 0.0f) atomicMax(&s_hmax, __float_as_uint(hmax));
+  __syncthreads();
+  if (threadIdx.x == 0) g.cell_Hmax[c] = __uint_as_float(s_hmax);
+  if (cnt > kMax) return;
   const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float ux, uy, uz;
   axis_u(k, ux, uy, uz);
@@ -370,9 +405,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(GridDev g, int lo) 
     kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
     kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
   }
-  int B = 32;
-  while (B < cnt) B <<= 1;
-  sort_axis<false>(cnt, s_orig, key, tmp, out, bkt, nullptr, B, lane, 32, kmin, kmax);
+  int nb = 32;
+  while (nb < cnt) nb <<= 1;
+  sort_axis<false>(cnt, s_orig, key, tmp, out, bkt, nullptr, nb, lane, 32, kmin, kmax);
   const size_t base = (size_t)k * g.n + cs;
   for (int t = lane; t < cnt; t += 32) {
     int v = out[t];
@@ -484,10 +519,9 @@ cudaError_t launch_scan(const GridDev& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const GridDev& g, const double* pos, const float* h, const float* m,
-                           float m_uniform, cudaStream_t st) {
+cudaError_t launch_scatter(const GridDev& g, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
-  k_scatter<<<(g.n + 255) / 256, 256, 0, st>>>(g, pos, h, m, m_uniform);
+  k_scatter<<<(g.n + 255) / 256, 256, 0, st>>>(g);
   return cudaGetLastError();
 }
 
@@ -500,21 +534,21 @@ cudaError_t launch_update(const GridDev& g, const double* pos, const float* h, c
   return cudaGetLastError();
 }
 
-template <int kMax>
-cudaError_t launch_sort_small(const GridDev& g, int lo, cudaStream_t st) {
-  static std::atomic<unsigned long long> smem_done{0};
-  constexpr int smem = (int)sort_small_smem<kMax>();
-  cudaError_t e = set_max_dynamic_smem(smem_done, reinterpret_cast<const void*>(&k_sort_small<kMax>),
-                                       smem);
-  if (e != cudaSuccess) return e;
-  k_sort_small<kMax><<<g.ncell, kSortThreads, smem, st>>>(g, lo);
+cudaError_t launch_clear(const GridDev& g, cudaStream_t st) {
+  const int n = g.ncell > g.n_boxes ? g.ncell : g.n_boxes;
+  k_clear<<<(n + 255) / 256, 256, 0, st>>>(g);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const GridDev& g, cudaStream_t st) {
-  if (g.n == 0) return cudaSuccess;
-  cudaError_t e = launch_sort_small<kSortSmallMax>(g, 0, st);
+cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, const float* m,
+                        float m_uniform, cudaStream_t st) {
+  static std::atomic<unsigned long long> smem_done{0};
+  constexpr int smem = (int)sort_small_smem<kSortSmallMax>();
+  cudaError_t e = set_max_dynamic_smem(
+      smem_done, reinterpret_cast<const void*>(&k_cell_sort<kSortSmallMax>), smem);
   if (e != cudaSuccess) return e;
+  k_cell_sort<kSortSmallMax><<<g.ncell, kSortThreads, smem, st>>>(g, pos, h, m, m_uniform);
+  if ((e = cudaGetLastError()) != cudaSuccess || g.n == 0) return e;
   k_sort_big<<<512, kSortBigThreads, 0, st>>>(g);
   return cudaGetLastError();
 }

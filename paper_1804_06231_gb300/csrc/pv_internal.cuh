@@ -369,12 +369,17 @@ __device__ __forceinline__ float window_pad(const GridDev& g, const BoxDev& B, i
 }
 
 // ---- host-side launchers (defined in the .cu files) ------------------------
+// The sort of pv_sort_cells in launch order: clear, bin, scan, scatter, sort.
+// launch_clear zeroes the occupancies, flags, max_count, n_big, m_max and
+// box_disp; launch_sort gathers every cell into cell order (xm, xm_ref, hs,
+// pos64, cell_Hmax) and writes perm and dist.
+cudaError_t launch_clear(const GridDev& g, cudaStream_t st);
 cudaError_t launch_bin(const GridDev& g, const double* pos, const float* h, const float* m,
                        float m_uniform, cudaStream_t st);
 cudaError_t launch_scan(const GridDev& g, cudaStream_t st);
-cudaError_t launch_scatter(const GridDev& g, const double* pos, const float* h, const float* m,
-                           float m_uniform, cudaStream_t st);
-cudaError_t launch_sort(const GridDev& g, cudaStream_t st);
+cudaError_t launch_scatter(const GridDev& g, cudaStream_t st);
+cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, const float* m,
+                        float m_uniform, cudaStream_t st);
 cudaError_t launch_update(const GridDev& g, const double* pos, const float* h, cudaStream_t st);
 // Per-(cell, slot) plan, then per-cell routing: cells whose staged windows fit
 // `smem_budget` bytes (elem_j bytes per staged particle, elem_a per particle

@@ -193,16 +193,14 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   k_static_setup<<<(int)((C + 255) / 256), 256, 0, st>>>(box, B, first, d.cell_box, (int)C);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_static_setup");
   if ((e = cudaMemsetAsync(d.cell_count, 0, C * sizeof(int32_t), st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(d.cell_Hmax, 0, C * sizeof(float), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(sc, 0, 16 * sizeof(int32_t), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(d.counters, 0, 16 * sizeof(unsigned long long), st)) != cudaSuccess ||
       (N && (e = cudaMemsetAsync(d.acc, 0, 3 * N * sizeof(long long), st)) != cudaSuccess))
     return fail(e, "cudaMemsetAsync");
   if ((e = pv::launch_bin(d, pos, h, m, m_uniform, st)) != cudaSuccess) return fail(e, "bin");
   if ((e = pv::launch_scan(d, st)) != cudaSuccess) return fail(e, "scan");
-  if ((e = pv::launch_scatter(d, pos, h, m, m_uniform, st)) != cudaSuccess)
-    return fail(e, "scatter");
-  if ((e = pv::launch_sort(d, st)) != cudaSuccess) return fail(e, "sort");
+  if ((e = pv::launch_scatter(d, st)) != cudaSuccess) return fail(e, "scatter");
+  if ((e = pv::launch_sort(d, pos, h, m, m_uniform, st)) != cudaSuccess) return fail(e, "sort");
   if ((e = pv::launch_density(d, rho, drho_dh, n_ngb, num_sms, pv::kDensityCtasDefault, st)) != cudaSuccess)
     return fail(e, "density");
   if (flags_out &&
