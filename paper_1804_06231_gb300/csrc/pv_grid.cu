@@ -33,6 +33,7 @@ namespace {
 // cells of up to kSortSmallMax particles sort in one CTA (74 KB of shared
 // memory, three CTAs per SM); larger ones with one CTA per (cell, axis)
 constexpr int kSortSmallMax = 384;
+static_assert(kSortSmallMax % 32 == 0, "whole particles per lane in the cell sort");
 constexpr int kSortThreads = kNDir * 32;
 
 __device__ __forceinline__ int box_of_particle(const GridDev& g, int p) {
@@ -223,11 +224,6 @@ __device__ __forceinline__ bool key_less(float ka, int oa, float kb, int ob) {
   return ka < kb || (ka == kb && oa < ob);
 }
 
-template <bool kBlock>
-__device__ __forceinline__ void group_sync() {
-  if (kBlock) __syncthreads(); else __syncwarp();
-}
-
 // Exclusive prefix of v over the group (a warp, or the whole block when
 // kBlock; `scratch` holds one int per warp of the block).
 template <bool kBlock>
@@ -259,56 +255,68 @@ __device__ __forceinline__ int group_exclusive_scan(int v, int rank, int* scratc
   return r;
 }
 
-// Sorts the cnt particles of one cell by key.  `grp` threads (a warp, or the
-// whole block when kBlock) with ranks 0..grp-1 cooperate.  Arrays:
-//   orig[cnt] (tie break), key[cnt], tmp[cnt] and out[cnt] (cell-local
-//   indices), bucket[B] (B a power of two >= grp), scratch[32] (block scan).
+// Sorts the cnt <= 32 kPer particles of one cell along one axis with one
+// warp.  Lane l holds in kr[j] the key of the particle t = l + 32 j (for
+// t < cnt); the shared arrays are key[cnt] (the same keys, read by the other
+// lanes), orig[cnt] (caller indices, the tie break), tmp[cnt], out[cnt]
+// (cell-local indices) and bucket[nb] (nb a power of two, 32 <= nb).
 // Buckets are monotone in the key: a counting sort by bucket leaves only the
-// order inside each bucket, which every element then settles by counting the
-// members of its bucket that precede it in (key, caller index) order.
-template <bool kBlock, typename Idx>
-__device__ void sort_axis(int cnt, const int* orig, const float* key, Idx* tmp, Idx* out,
-                          int* bucket, int* scratch, int B, int rank, int grp, float kmin,
-                          float kmax) {
-  const float scale = kmax > kmin ? (float)B / (kmax - kmin) : 0.0f;
-  for (int b = rank; b < B; b += grp) bucket[b] = 0;
-  group_sync<kBlock>();
-  for (int t = rank; t < cnt; t += grp) {
-    const int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
-    atomicAdd(&bucket[b], 1);
-  }
-  group_sync<kBlock>();
-  // exclusive scan: each rank owns B/grp consecutive buckets
-  const int per = B / grp;
-  const int b0 = rank * per;
+// order inside each bucket, which every particle then settles by counting the
+// members of its bucket that precede it in (key, caller index) order.  The
+// per-lane particles are unrolled, so that their shared-memory accesses and
+// atomics are in flight together.
+template <int kPer>
+__device__ __forceinline__ void warp_sort_axis(int cnt, const float (&kr)[kPer],
+                                               const float* key, const int* orig,
+                                               uint16_t* tmp, uint16_t* out, int* bucket,
+                                               int nb, int lane, float kmin, float kmax) {
+  const float scale = kmax > kmin ? (float)nb / (kmax - kmin) : 0.0f;
+  int bk[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; j++)
+    bk[j] = lane + 32 * j < cnt ? min(nb - 1, max(0, (int)((kr[j] - kmin) * scale))) : -1;
+  for (int b = lane; b < nb; b += 32) bucket[b] = 0;
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < kPer; j++)
+    if (bk[j] >= 0) atomicAdd(&bucket[bk[j]], 1);
+  __syncwarp();
+  // exclusive scan: each lane owns nb / 32 consecutive buckets
+  const int per = nb >> 5, b0 = lane * per;
   int sum = 0;
   for (int b = b0; b < b0 + per; b++) sum += bucket[b];
-  int run = group_exclusive_scan<kBlock>(sum, rank, scratch);
+  int run = group_exclusive_scan<false>(sum, lane, nullptr);
   for (int b = b0; b < b0 + per; b++) {
     const int v = bucket[b];
     bucket[b] = run;
     run += v;
   }
-  group_sync<kBlock>();
-  for (int t = rank; t < cnt; t += grp) {
-    const int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
-    tmp[atomicAdd(&bucket[b], 1)] = (Idx)t;
-  }
-  group_sync<kBlock>();
-  // bucket[b] is now the end of bucket b (= the start of bucket b+1)
-  for (int t = rank; t < cnt; t += grp) {
-    const int b = min(B - 1, max(0, (int)((key[t] - kmin) * scale)));
-    const int s0 = b ? bucket[b - 1] : 0, s1 = bucket[b];
-    const float kt = key[t];
-    const int ot = orig[t];
+  __syncwarp();
+  int at[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; j++) at[j] = bk[j] >= 0 ? atomicAdd(&bucket[bk[j]], 1) : 0;
+#pragma unroll
+  for (int j = 0; j < kPer; j++)
+    if (bk[j] >= 0) tmp[at[j]] = (uint16_t)(lane + 32 * j);
+  __syncwarp();
+  // bucket[b] is now the end of bucket b (= the start of bucket b+1); a
+  // particle alone in its bucket is already in place
+#pragma unroll
+  for (int j = 0; j < kPer; j++) {
+    if (bk[j] < 0) continue;
+    const int t = lane + 32 * j;
+    const int s0 = bk[j] ? bucket[bk[j] - 1] : 0, s1 = bucket[bk[j]];
     int r = 0;
-    for (int u = s0; u < s1; u++) {
-      const int v = tmp[u];
-      r += key_less(key[v], orig[v], kt, ot) ? 1 : 0;
+    if (s1 - s0 > 1) {
+      const int ot = orig[t];
+      for (int u = s0; u < s1; u++) {
+        const int v = tmp[u];
+        r += key_less(key[v], orig[v], kr[j], ot) ? 1 : 0;
+      }
     }
-    out[s0 + r] = (Idx)t;
+    out[s0 + r] = (uint16_t)t;
   }
-  group_sync<kBlock>();
+  __syncwarp();
 }
 
 // Shared memory of k_cell_sort<kMax>: staged particles, keys, buckets (a
@@ -332,7 +340,7 @@ constexpr size_t sort_small_smem() {
 // particles is then sorted along the 13 axes from the staged copy, one warp
 // per axis; larger cells are left to k_sort_big.
 template <int kMax>
-__global__ void __launch_bounds__(kSortThreads) k_cell_sort(GridDev g,
+__global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g,
                                                             const double* __restrict__ pos,
                                                             const float* __restrict__ h,
                                                             const float* __restrict__ m,
@@ -394,12 +402,20 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort(GridDev g,
   uint16_t* out = s_out + k * kMax;
   uint16_t* tmp = s_tmp + k * kMax;
   int* bkt = s_bkt + k * kB;
+  constexpr int kPer = kMax / 32;
+  float kr[kPer];
   float kmin = 3.0e38f, kmax = -3.0e38f;
-  for (int t = lane; t < cnt; t += 32) {
-    float d = project(s_x[t], ux, uy, uz);
-    key[t] = d;
-    kmin = fminf(kmin, d);
-    kmax = fmaxf(kmax, d);
+#pragma unroll
+  for (int j = 0; j < kPer; j++) {
+    const int t = lane + 32 * j;
+    kr[j] = 0.0f;
+    if (t < cnt) {
+      const float d = project(s_x[t], ux, uy, uz);
+      key[t] = d;
+      kr[j] = d;
+      kmin = fminf(kmin, d);
+      kmax = fmaxf(kmax, d);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
@@ -407,12 +423,16 @@ __global__ void __launch_bounds__(kSortThreads) k_cell_sort(GridDev g,
   }
   int nb = 32;
   while (nb < cnt) nb <<= 1;
-  sort_axis<false>(cnt, s_orig, key, tmp, out, bkt, nullptr, nb, lane, 32, kmin, kmax);
+  warp_sort_axis<kPer>(cnt, kr, key, s_orig, tmp, out, bkt, nb, lane, kmin, kmax);
   const size_t base = (size_t)k * g.n + cs;
-  for (int t = lane; t < cnt; t += 32) {
-    int v = out[t];
-    g.perm[base + t] = (uint16_t)v;
-    g.dist[base + t] = key[v];
+#pragma unroll
+  for (int j = 0; j < kPer; j++) {
+    const int t = lane + 32 * j;
+    if (t < cnt) {
+      const int v = out[t];
+      g.perm[base + t] = (uint16_t)v;
+      g.dist[base + t] = key[v];
+    }
   }
 }
 
