@@ -121,6 +121,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
     // window pad covers two of them plus the FP32 cell shift
     B.pad = (float)(std::ldexp(B.edge, -18));
     B.guard = 0.0f;
+    B.h_limit = pv::support_h_limit(gamma, B.edge);
     B.nc = bd.nc;
     B.cell_base = (int32_t)ncell;
     B.first = bd.first;

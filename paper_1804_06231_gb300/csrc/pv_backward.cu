@@ -131,7 +131,6 @@ struct LaneB {
   float nx, ny, nz;      // -2 x_i
   float ci, di;          // pre-filter bounds: own H_i^2+guard-|x_i|^2+margin, margin-|x_i|^2
   float Hsq_hi, Hsq_lo, Hinv, H, G, K, m;
-  double Hd;
   int si;
   float Sth, Suh, gx, gy, gz;
 };
@@ -142,7 +141,6 @@ __device__ __forceinline__ void laneb_init(LaneB& L) {
   L.di = -3.0e38f;
   L.Hsq_hi = L.Hsq_lo = -1.0f;
   L.Hinv = L.H = L.G = L.K = L.m = 0.0f;
-  L.Hd = 0.0;
   L.si = 0;
   L.Sth = L.Suh = L.gx = L.gy = L.gz = 0.0f;
 }
@@ -158,7 +156,6 @@ __device__ __forceinline__ void laneb_set(LaneB& L, const GridDev& g, const BoxD
   L.m = xi.w;
   L.G = ak.x; L.K = ak.y; L.Hsq_hi = ak.z; L.Hsq_lo = ak.w;
   L.Hinv = hh.x; L.H = hh.y;
-  L.Hd = g.gamma_d * (double)g.hs[si];
   L.nx = -2.0f * L.x;
   L.ny = -2.0f * L.y;
   L.nz = -2.0f * L.z;
@@ -279,7 +276,8 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
             const bool gtr = r2 < ej.x && r2 >= fmaf(2.0f * aj.w, aj.w, -ej.x);
             if (gown || gtr) {
               const int sj = jidx(j);
-              const bool out_o = gown && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L, L.Hd);
+              const bool out_o = gown && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L,
+                                                     g.gamma_d * (double)g.hs[L.si]);
               const bool out_t = gtr && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L,
                                                      g.gamma_d * (double)g.hs[sj]);
               if (out_o || out_t)

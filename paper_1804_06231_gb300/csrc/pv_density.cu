@@ -200,7 +200,6 @@ struct LaneI {
   float nx, ny, nz, ci;    // -2 x_i and H_i^2 + guard - |x_i|^2 + margin (prefilter)
   float Hsq_hi, Hsq_lo;    // guard band around H_i^2 (-1: inactive lane)
   float Hinv2;             // 1 / H_i^2
-  double Hd;               // FP64 support, for the guard re-decision
   int si;                  // cell-order index of i
   float rho, D;            // sum_j m_j wh, sum_j m_j th
   int n;                   // pairs with r < H_i (j = i included)
@@ -210,7 +209,7 @@ __device__ __forceinline__ void lane_init(LaneI& L) {
   L.x = L.y = L.z = 0.0f;
   L.nx = L.ny = L.nz = 0.0f;
   L.ci = -3.0e38f;
-  L.Hsq_hi = -1.0f; L.Hsq_lo = -1.0f; L.Hinv2 = 0.0f; L.Hd = 0.0; L.si = 0;
+  L.Hsq_hi = -1.0f; L.Hsq_lo = -1.0f; L.Hinv2 = 0.0f; L.si = 0;
   L.rho = 0.0f; L.D = 0.0f; L.n = 0;
 }
 
@@ -225,7 +224,6 @@ __device__ __forceinline__ void lane_set(LaneI& L, const GridDev& g, const BoxDe
   L.Hsq_hi = Hsq + gb;
   L.Hsq_lo = Hsq - gb;
   L.Hinv2 = __fdividef(1.0f, Hsq);
-  L.Hd = g.gamma_d * (double)h;
   L.nx = -2.0f * L.x;
   L.ny = -2.0f * L.y;
   L.nz = -2.0f * L.z;
@@ -324,7 +322,8 @@ __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ S
             const float r2 = pair_r2(L, Sx[j]);
             if (r2 < L.Hsq_hi && r2 >= L.Hsq_lo) {
               guards++;
-              if (!guard_inside(g.pos64, L.si, jidx(j), B.L, B.inv_L, L.Hd)) {
+              if (!guard_inside(g.pos64, L.si, jidx(j), B.L, B.inv_L,
+                                g.gamma_d * (double)g.hs[L.si])) {
                 fwd_pair(L, r2, -Sm[j]);
                 L.n -= 1;
               }

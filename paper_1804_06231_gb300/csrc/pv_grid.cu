@@ -50,6 +50,17 @@ __device__ __forceinline__ bool valid_h_m(float hv, float mv) {
   return hv > 0.0f && isfinite(hv) && mv >= 0.0f && isfinite(mv);
 }
 
+// isfinite(x) and 0 <= x < L (L > 0) on the FP64 bit patterns, in integer
+// arithmetic: sm_103 has few FP64 units.  Non-negative doubles order as their
+// bit patterns; -0.0 passes, as in the FP64 comparison.
+__device__ __forceinline__ bool finite_bits(double x) {
+  return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+__device__ __forceinline__ bool in_box_bits(double x, double L) {
+  const long long b = __double_as_longlong(x);
+  return (b >= 0 && b < __double_as_longlong(L)) || b == (long long)0x8000000000000000ULL;
+}
+
 __device__ __forceinline__ double wrap_coord(double x, double L) {
   double y = x - L * floor(x / L);
   if (y >= L) y = 0.0;
@@ -84,8 +95,8 @@ __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       double x = pos[3 * (size_t)p + c];
-      if (!isfinite(x)) { flags |= PV_FLAG_BAD_POSITION; x = 0.0; }
-      if (!(x >= 0.0 && x < B.L)) x = wrap_coord(x, B.L);  // FP64 division only when needed
+      if (!finite_bits(x)) { flags |= PV_FLAG_BAD_POSITION; x = 0.0; }
+      if (!in_box_bits(x, B.L)) x = wrap_coord(x, B.L);  // FP64 division only when needed
       const int ci = (int)(x * B.inv_edge);
       c3[c] = ci < 0 ? 0 : (ci >= B.nc ? B.nc - 1 : ci);
     }
@@ -93,7 +104,7 @@ __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __
     const float hv = h[p];
     const float mv = m ? m[p] : m_uniform;
     if (!valid_h_m(hv, mv)) flags |= PV_FLAG_BAD_SMOOTHING;
-    else if (g.gamma_d * (double)hv > B.edge) flags |= PV_FLAG_SUPPORT_EXCEEDS_CELL;
+    else if (hv > B.h_limit) flags |= PV_FLAG_SUPPORT_EXCEEDS_CELL;  // gamma h > edge
     if (flags) atomicOr(g.flags, flags);
     g.pcell[p] = cell;
     g.prank[p] = atomicAdd(&g.cell_count[cell], 1);
@@ -177,8 +188,8 @@ __global__ void k_update(GridDev g, const double* __restrict__ pos,
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       double x = pos[3 * (size_t)p + c];
-      if (!isfinite(x)) { flags |= PV_FLAG_BAD_POSITION; x = 0.0; }
-      if (!(x >= 0.0 && x < B.L)) x = wrap_coord(x, B.L);
+      if (!finite_bits(x)) { flags |= PV_FLAG_BAD_POSITION; x = 0.0; }
+      if (!in_box_bits(x, B.L)) x = wrap_coord(x, B.L);
       double d = fma(-(c3[c] + 0.5), B.edge, x);  // as at the sort for an unmoved particle
       d -= B.L * rint(d * B.inv_L);               // nearest image of the cell centre
       off[c] = (float)d;
@@ -255,11 +266,17 @@ __device__ __forceinline__ int group_exclusive_scan(int v, int rank, int* scratc
   return r;
 }
 
+// Bucket b of a scan in which each of nthr threads owns per = nb / nthr
+// consecutive buckets sits at b + b / per (sh = log2 per): one pad word per
+// chunk puts the chunks' i-th buckets in distinct shared-memory banks.
+__device__ __forceinline__ int bucket_slot(int b, int sh) { return b + (b >> sh); }
+
 // Sorts the cnt <= 32 kPer particles of one cell along one axis with one
 // warp.  Lane l holds in kr[j] the key of the particle t = l + 32 j (for
 // t < cnt); the shared arrays are key[cnt] (the same keys, read by the other
 // lanes), orig[cnt] (caller indices, the tie break), tmp[cnt], out[cnt]
-// (cell-local indices) and bucket[nb] (nb a power of two, 32 <= nb).
+// (cell-local indices) and bucket[nb + 32] (nb a power of two, 32 <= nb;
+// bucket b at bucket_slot(b, log2(nb / 32))).
 // Buckets are monotone in the key: a counting sort by bucket leaves only the
 // order inside each bucket, which every particle then settles by counting the
 // members of its bucket that precede it in (key, caller index) order.  The
@@ -275,18 +292,19 @@ __device__ __forceinline__ void warp_sort_axis(int cnt, const float (&kr)[kPer],
 #pragma unroll
   for (int j = 0; j < kPer; j++)
     bk[j] = lane + 32 * j < cnt ? min(nb - 1, max(0, (int)((kr[j] - kmin) * scale))) : -1;
-  for (int b = lane; b < nb; b += 32) bucket[b] = 0;
+  const int per = nb >> 5, sh = __ffs(per) - 1;
+  for (int b = lane; b < nb + 32; b += 32) bucket[b] = 0;
   __syncwarp();
 #pragma unroll
   for (int j = 0; j < kPer; j++)
-    if (bk[j] >= 0) atomicAdd(&bucket[bk[j]], 1);
+    if (bk[j] >= 0) atomicAdd(&bucket[bucket_slot(bk[j], sh)], 1);
   __syncwarp();
   // exclusive scan: each lane owns nb / 32 consecutive buckets
-  const int per = nb >> 5, b0 = lane * per;
+  const int p0 = bucket_slot(lane * per, sh);
   int sum = 0;
-  for (int b = b0; b < b0 + per; b++) sum += bucket[b];
+  for (int b = p0; b < p0 + per; b++) sum += bucket[b];
   int run = group_exclusive_scan<false>(sum, lane, nullptr);
-  for (int b = b0; b < b0 + per; b++) {
+  for (int b = p0; b < p0 + per; b++) {
     const int v = bucket[b];
     bucket[b] = run;
     run += v;
@@ -294,7 +312,8 @@ __device__ __forceinline__ void warp_sort_axis(int cnt, const float (&kr)[kPer],
   __syncwarp();
   int at[kPer];
 #pragma unroll
-  for (int j = 0; j < kPer; j++) at[j] = bk[j] >= 0 ? atomicAdd(&bucket[bk[j]], 1) : 0;
+  for (int j = 0; j < kPer; j++)
+    at[j] = bk[j] >= 0 ? atomicAdd(&bucket[bucket_slot(bk[j], sh)], 1) : 0;
 #pragma unroll
   for (int j = 0; j < kPer; j++)
     if (bk[j] >= 0) tmp[at[j]] = (uint16_t)(lane + 32 * j);
@@ -305,7 +324,8 @@ __device__ __forceinline__ void warp_sort_axis(int cnt, const float (&kr)[kPer],
   for (int j = 0; j < kPer; j++) {
     if (bk[j] < 0) continue;
     const int t = lane + 32 * j;
-    const int s0 = bk[j] ? bucket[bk[j] - 1] : 0, s1 = bucket[bk[j]];
+    const int s0 = bk[j] ? bucket[bucket_slot(bk[j] - 1, sh)] : 0;
+    const int s1 = bucket[bucket_slot(bk[j], sh)];
     int r = 0;
     if (s1 - s0 > 1) {
       const int ot = orig[t];
@@ -329,7 +349,7 @@ template <int kMax>
 constexpr size_t sort_small_smem() {
   return (size_t)kMax * (sizeof(float4) + sizeof(int)) +
          (size_t)kNDir * (kMax * (sizeof(float) + 2 * sizeof(uint16_t)) +
-                          sort_small_buckets<kMax>() * sizeof(int));
+                          (sort_small_buckets<kMax>() + 32) * sizeof(int));
 }
 
 // One CTA per cell.  All threads gather the cell's particles (caller indices
@@ -351,8 +371,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g,
   float4* s_x = smem4;                                           // [kMax]
   int* s_orig = reinterpret_cast<int*>(s_x + kMax);              // [kMax]
   float* s_key = reinterpret_cast<float*>(s_orig + kMax);        // [13][kMax]
-  int* s_bkt = reinterpret_cast<int*>(s_key + kNDir * kMax);     // [13][kB]
-  uint16_t* s_out = reinterpret_cast<uint16_t*>(s_bkt + kNDir * kB);  // [13][kMax]
+  int* s_bkt = reinterpret_cast<int*>(s_key + kNDir * kMax);     // [13][kB + 32]
+  uint16_t* s_out = reinterpret_cast<uint16_t*>(s_bkt + kNDir * (kB + 32));  // [13][kMax]
   uint16_t* s_tmp = s_out + kNDir * kMax;                        // [13][kMax]
   const int c = blockIdx.x;
   const int cnt = g.cell_count[c];
@@ -373,8 +393,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g,
 #pragma unroll
     for (int k = 0; k < 3; k++) {
       double x = pos[3 * (size_t)p + k];
-      if (!isfinite(x)) x = 0.0;
-      if (!(x >= 0.0 && x < B.L)) x = wrap_coord(x, B.L);
+      if (!finite_bits(x)) x = 0.0;
+      if (!in_box_bits(x, B.L)) x = wrap_coord(x, B.L);
       off[k] = (float)fma(ctr[k], B.edge, x);
       g.pos64[3 * s + k] = x;
     }
@@ -401,7 +421,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g,
   float* key = s_key + k * kMax;
   uint16_t* out = s_out + k * kMax;
   uint16_t* tmp = s_tmp + k * kMax;
-  int* bkt = s_bkt + k * kB;
+  int* bkt = s_bkt + k * (kB + 32);
   constexpr int kPer = kMax / 32;
   float kr[kPer];
   float kmin = 3.0e38f, kmax = -3.0e38f;
@@ -446,7 +466,7 @@ constexpr int kSortBigThreads = 1024;
 constexpr int kSortBigBuckets = 8192;
 
 __global__ void __launch_bounds__(kSortBigThreads) k_sort_big(GridDev g) {
-  __shared__ int s_bkt[kSortBigBuckets];
+  __shared__ int s_bkt[kSortBigBuckets + kSortBigThreads];  // bucket b at bucket_slot(b, sh)
   __shared__ float s_red[2][32];
   __shared__ int s_scan[32];
   if (*g.flags) return;
@@ -479,7 +499,8 @@ __global__ void __launch_bounds__(kSortBigThreads) k_sort_big(GridDev g) {
       s_red[0][tid >> 5] = kmin;
       s_red[1][tid >> 5] = kmax;
     }
-    for (int b = tid; b < B; b += nthr) s_bkt[b] = 0;
+    const int per = B / nthr, sh = __ffs(per) - 1;
+    for (int b = tid; b < B + nthr; b += nthr) s_bkt[b] = 0;
     __syncthreads();
     kmin = s_red[0][0];
     kmax = s_red[1][0];
@@ -490,27 +511,27 @@ __global__ void __launch_bounds__(kSortBigThreads) k_sort_big(GridDev g) {
     const float scale = kmax > kmin ? (float)B / (kmax - kmin) : 0.0f;
     auto bucket_of = [&](float d) { return min(B - 1, max(0, (int)((d - kmin) * scale))); };
     for (int t = tid; t < cnt; t += nthr)
-      atomicAdd(&s_bkt[bucket_of(project(X[t], ux, uy, uz))], 1);
+      atomicAdd(&s_bkt[bucket_slot(bucket_of(project(X[t], ux, uy, uz)), sh)], 1);
     __syncthreads();
     // exclusive scan: each thread owns B / nthr consecutive buckets
-    const int per = B / nthr, b0 = tid * per;
+    const int p0 = bucket_slot(tid * per, sh);
     int sum = 0;
-    for (int b = b0; b < b0 + per; b++) sum += s_bkt[b];
+    for (int b = p0; b < p0 + per; b++) sum += s_bkt[b];
     int run = group_exclusive_scan<true>(sum, tid, s_scan);
-    for (int b = b0; b < b0 + per; b++) {
+    for (int b = p0; b < p0 + per; b++) {
       const int v = s_bkt[b];
       s_bkt[b] = run;
       run += v;
     }
     __syncthreads();
     for (int t = tid; t < cnt; t += nthr)
-      tmp[atomicAdd(&s_bkt[bucket_of(project(X[t], ux, uy, uz))], 1)] = t;
+      tmp[atomicAdd(&s_bkt[bucket_slot(bucket_of(project(X[t], ux, uy, uz)), sh)], 1)] = t;
     __syncthreads();
     // s_bkt[b] is now the end of bucket b; rank each particle inside its bucket
     for (int t = tid; t < cnt; t += nthr) {
       const float kt = project(X[t], ux, uy, uz);
       const int b = bucket_of(kt);
-      const int s0 = b ? s_bkt[b - 1] : 0, s1 = s_bkt[b];
+      const int s0 = b ? s_bkt[bucket_slot(b - 1, sh)] : 0, s1 = s_bkt[bucket_slot(b, sh)];
       const int ot = O[t];
       int r = 0;
       for (int u = s0; u < s1; u++) {

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cmath>
 #include <stdint.h>
 
 #include "pv.h"
@@ -31,8 +32,7 @@ constexpr int kNDir = 13;   // distinct axes joining neighbouring cell centres
 constexpr int kNSlot = 27;  // neighbour offsets (ox,oy,oz) in {-1,0,1}^3
 constexpr int kSelfSlot = 13;
 constexpr uint32_t kAllSlots = (1u << 27) - 1u;
-constexpr int kFixShift = 36;                       // fixed-point scale 2^36
-constexpr double kFixScale = 68719476736.0;         // 2^36
+constexpr double kFixScale = 68719476736.0;         // fixed-point scale 2^36
 constexpr double kFixInv = 1.0 / 68719476736.0;
 constexpr float kPiF = 3.14159265358979f;
 
@@ -41,10 +41,21 @@ struct BoxDev {
   float edge_f;    // FP32 cell edge
   float pad;       // window pad covering FP32 rounding of projections
   float guard;     // guard half-width factor for r^2 (see guard_band())
+  float h_limit;   // largest FP32 h whose support gamma h (FP64) is within the edge
   int32_t nc;
   int32_t cell_base;  // first global cell id of the box
   int64_t first, n;
 };
+
+// The largest FP32 h with gamma * (double)h <= edge: for FP32 h the test
+// h > h_limit is then the same as the FP64 test gamma h > edge (the product
+// is monotone in h), with no FP64 arithmetic per particle.
+inline float support_h_limit(double gamma, double edge) {
+  float h = (float)(edge / gamma);
+  while (h > 0.0f && gamma * (double)h > edge) h = std::nextafter(h, 0.0f);
+  while (gamma * (double)std::nextafter(h, INFINITY) <= edge) h = std::nextafter(h, INFINITY);
+  return h;
+}
 
 // Everything a kernel needs, passed by value.
 struct GridDev {

@@ -183,6 +183,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   B.edge_f = (float)B.edge;
   B.pad = (float)std::ldexp(B.edge, -18);
   B.guard = 0.0f;
+  B.h_limit = pv::support_h_limit(gamma, B.edge);
   B.nc = nc;
   B.cell_base = 0;
   B.first = 0;
