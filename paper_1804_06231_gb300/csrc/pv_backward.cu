@@ -73,7 +73,7 @@ __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.n || *g.flags) return;
   const int i = g.orig[s];
-  const BoxDev& B = g.boxes[g.cell_box[g.pcell[i]]];
+  const BoxDev& B = g.boxes[box_of_particle(g, i)];
   const float h = g.hs[s];
   const float H = g.gamma * h;
   const float H2 = H * H;

@@ -80,11 +80,13 @@ __device__ __forceinline__ int count_below(const GridDev& g, int k, int s, int c
 // One thread per (cell a, slot o): the number of particles of a that can reach
 // b (first_a trimming with the cell's largest support) and the window [J0, J1)
 // of b that the nearest of them can touch.  `wide` widens every reach to the
-// larger of the two cells' largest supports (adjoint pass).
+// larger of the two cells' largest supports (adjoint pass).  The two binary
+// searches are independent and run in lockstep, so that their global loads
+// are in flight together; a grid with latched input errors gets empty plans.
 __global__ void k_plan_slots(GridDev g, int wide) {
-  if (*g.flags) return;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.ncell * kNSlot) return;
+  const uint32_t flagged = *g.flags;
   const int a = idx / kNSlot, o = idx % kNSlot;
   const int na = g.cell_count[a];
   int4 pl = make_int4(0, 0, 0, 0);
@@ -103,21 +105,28 @@ __global__ void k_plan_slots(GridDev g, int wide) {
       } else {
         const float off = vnorm(sl.v2) * B.edge_f;
         const float db_min = proj_asc(g, sl.k, sl.s, cb, nb, 0, off);
-        // descending order along u: position p <-> ascending index na-1-p
-        int lo = 0, hi = na;
-        while (lo < hi) {
-          int mid = (lo + hi) >> 1;
-          float d = proj_asc(g, sl.k, sl.s, ca, na, na - 1 - mid, 0.0f);
-          if (d + reach > db_min) lo = mid + 1; else hi = mid;
+        const float lim = proj_asc(g, sl.k, sl.s, ca, na, na - 1, 0.0f) + reach;
+        // lo1: particles of a, in descending order along u (position p is
+        // ascending index na-1-p), whose reach passes b's nearest particle;
+        // lo2: particles of b below the reach of a's farthest one
+        int lo1 = 0, hi1 = na, lo2 = 0, hi2 = nb;
+        while (lo1 < hi1 || lo2 < hi2) {
+          const int m1 = (lo1 + hi1) >> 1, m2 = (lo2 + hi2) >> 1;
+          const bool s1 = lo1 < hi1, s2 = lo2 < hi2;
+          const float d1 = s1 ? proj_asc(g, sl.k, sl.s, ca, na, na - 1 - m1, 0.0f) : 0.0f;
+          const float d2 = s2 ? proj_asc(g, sl.k, sl.s, cb, nb, m2, off) : 0.0f;
+          if (s1) {
+            if (d1 + reach > db_min) lo1 = m1 + 1; else hi1 = m1;
+          }
+          if (s2) {
+            if (d2 < lim) lo2 = m2 + 1; else hi2 = m2;
+          }
         }
-        if (lo > 0) {
-          const float dmax = proj_asc(g, sl.k, sl.s, ca, na, na - 1, 0.0f);
-          pl = make_int4(lo, 0, count_below(g, sl.k, sl.s, cb, nb, off, dmax + reach), 0);
-        }
+        if (lo1 > 0) pl = make_int4(lo1, 0, lo2, 0);
       }
     }
   }
-  g.plan[idx] = pl;
+  g.plan[idx] = flagged ? make_int4(0, 0, 0, 0) : pl;
 }
 
 // One thread per cell: route the cell to the cell-centric kernel when its

@@ -36,16 +36,6 @@ constexpr int kSortSmallMax = 384;
 static_assert(kSortSmallMax % 32 == 0, "whole particles per lane in the cell sort");
 constexpr int kSortThreads = kNDir * 32;
 
-__device__ __forceinline__ int box_of_particle(const GridDev& g, int p) {
-  // last box whose first index is <= p (boxes are contiguous and ordered)
-  int lo = 0, hi = g.n_boxes - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (g.box_first[mid] <= (int64_t)p) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 __device__ __forceinline__ bool valid_h_m(float hv, float mv) {
   return hv > 0.0f && isfinite(hv) && mv >= 0.0f && isfinite(mv);
 }

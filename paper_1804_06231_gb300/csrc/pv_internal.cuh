@@ -157,6 +157,17 @@ __device__ __forceinline__ float project(float4 x, float ux, float uy, float uz)
 }
 
 // neighbour cell of global cell a at slot o (periodic wrap inside the box)
+// Box of the particle with caller index p: the last box whose first index is
+// <= p (boxes are contiguous and ordered).
+__device__ __forceinline__ int box_of_particle(const GridDev& g, int p) {
+  int lo = 0, hi = g.n_boxes - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.box_first[mid] <= (int64_t)p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ int neighbour_cell(const GridDev& g, int a, int o) {
   const BoxDev& B = g.boxes[g.cell_box[a]];
   int nc = B.nc, loc = a - B.cell_base;
@@ -170,8 +181,13 @@ __device__ __forceinline__ int neighbour_cell(const GridDev& g, int a, int o) {
 }
 
 // ---- float <-> orderable int for atomicMax on non-negative floats ---------
+// Raises *p to v (both non-negative floats, ordered as their bit patterns).
+// The current value is read first and the atomic issued only when it can
+// raise it: the value only grows, so a stale read costs at most one needless
+// atomic, and threads holding the same value (a uniform mass, say) do not
+// queue on one address.
 __device__ __forceinline__ void atomic_max_nonneg(float* p, float v) {
-  atomicMax(reinterpret_cast<int*>(p), __float_as_int(v));
+  if (v > __ldcg(p)) atomicMax(reinterpret_cast<int*>(p), __float_as_int(v));
 }
 
 // Pre-filter of 8 consecutive staged particles (float4 {x, y, z, |x|^2} at
