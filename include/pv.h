@@ -186,7 +186,7 @@ pv_status pv_grid_stats(pv_grid* g, pv_stats* out);
    more warps to hide latency.  0 selects the default. */
 typedef struct {
   int32_t density_ctas_per_sm;   /* 1..4 (default 3) */
-  int32_t backward_ctas_per_sm;  /* 1..2 (default 2) */
+  int32_t backward_ctas_per_sm;  /* 1..3 (default 3) */
   int32_t reserved[6];           /* must be 0 */
 } pv_tuning;
 

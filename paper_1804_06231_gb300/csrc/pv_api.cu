@@ -171,8 +171,8 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_TRY(dev_alloc(g, &d.dist, pv::kNDir * N));
   PV_TRY(dev_alloc(g, &d.acc, 3 * N));
   PV_TRY(dev_alloc(g, &d.gacc, 5 * N));
-  PV_TRY(dev_alloc(g, &d.gk, N));
-  PV_TRY(dev_alloc(g, &d.ghh, N));
+  PV_TRY(dev_alloc(g, &d.bx, N));
+  PV_TRY(dev_alloc(g, &d.ba, N));
   PV_TRY(dev_alloc(g, &d.plan, (size_t)pv::kNSlot * C));
   PV_TRY(dev_alloc(g, &d.ccells, C));
   PV_TRY(dev_alloc(g, &d.tcells, C));
@@ -374,7 +374,7 @@ pv_status pv_grid_set_tuning(pv_grid* g, const pv_tuning* t) {
     if (r != 0) return PV_ERR_INVALID_ARGUMENT;
   const int d = t->density_ctas_per_sm ? t->density_ctas_per_sm : pv::kDensityCtasDefault;
   const int b = t->backward_ctas_per_sm ? t->backward_ctas_per_sm : pv::kBackwardCtasDefault;
-  if (d < 1 || d > 4 || b < 1 || b > 2) return PV_ERR_INVALID_ARGUMENT;
+  if (d < 1 || d > 4 || b < 1 || b > 3) return PV_ERR_INVALID_ARGUMENT;
   g->ctas[0] = d;
   g->ctas[1] = b;
   return PV_OK;

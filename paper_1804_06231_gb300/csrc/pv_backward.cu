@@ -23,11 +23,13 @@
 //   dL/dh_i = (16/pi)/(h_i H_i^3) [ -g_i sum_j m_j th_i + (k_i/h_i) sum_j m_j uh_i ]
 //
 // Mapping: the cell-centric kernel of the forward pass (one CTA per cell, 27
-// staged windows, warps pulling (slot, run) items, candidates pre-filtered 64
-// at a time into a bit mask), with both the own and the transposed cut-off in
-// the pre-filter; per-particle sums in FP64 shared-memory accumulators.
-// Cells whose windows exceed the shared-memory budget run as tasks
-// (cell, slot, block of 128 particles) with FP64 global accumulators.
+// staged windows, warps pulling (slot, run) items, candidates pre-filtered 8
+// at a time into bit masks), with both the own and the transposed cut-off in
+// the pre-filter; per-particle sums in FP32 shared-memory accumulators (one
+// addition per particle and work item).  A staged particle takes 32 bytes
+// ({x, y, z, H^2 + guard} and {m, G, K, H}), so three CTAs fit an SM.  Cells
+// whose windows exceed the shared-memory budget run as tasks (cell, slot,
+// block of 128 particles) with FP64 global accumulators.
 #include <cuda_runtime.h>
 
 #include "pv_internal.cuh"
@@ -39,13 +41,12 @@ namespace {
 constexpr int kBlkI = 128;   // must match the plan kernel
 constexpr int kTileJ = 512;
 constexpr int kCellThreads = 256;
-// dynamic shared memory of k_backward_cells for 1 or 2 resident CTAs per SM
-// (2 by default; its registers allow no more)
-constexpr int kCellSmemFor[3] = {0, 200 * 1024, 110 * 1024};
+// dynamic shared memory of k_backward_cells for 1 to 3 resident CTAs per SM
+// (its registers allow no more than three)
+constexpr int kCellSmemFor[4] = {0, 200 * 1024, 110 * 1024, 72 * 1024};
 constexpr int kPad = 32;
-constexpr int kElemJ = 40;   // staged bytes per particle of a window: {x,y,z,|x|^2}, {m,G,K,H},
-                             // {H^2 + guard, 1/H}
-constexpr int kElemA = 40;   // bytes per particle of the cell: five FP64 sums
+constexpr int kElemJ = 32;   // staged bytes per particle of a window: {x,y,z,E}, {m,G,K,H}
+constexpr int kElemA = 20;   // bytes per particle of the cell: five FP32 sums
 
 __constant__ int8_t c_border[kNSlot] = {13, 4,  10, 12, 14, 16, 22, 1,  3,  5,  7,  9, 11, 15,
                                         17, 19, 21, 23, 25, 0,  2,  6,  8,  18, 20, 24, 26};
@@ -66,8 +67,8 @@ __device__ __forceinline__ TaskB decode_b(int4 t) {
 }
 
 // Upstream gradients to cell order, with the per-particle constants of the
-// sweep: gk = {G = g/H^5, K = k/(h H^5), H^2 + guard, H^2 - guard},
-// ghh = {1/H, H}.
+// sweep, in the form the sweeps stage them: bx = {x', y', z', E = H^2 +
+// guard} and ba = {m / m_max, G = g/H^5, K = k/(h H^5), H}.
 __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
                            const float* __restrict__ g_D) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -81,8 +82,9 @@ __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
   const float gi = g_rho[i];
   const float ki = g_D ? g_D[i] : 0.0f;
   const float gb = guard_band(H, B.edge_f);
-  g.gk[s] = make_float4(gi * iH5, ki * iH5 / h, H2 + gb, H2 - gb);
-  g.ghh[s] = make_float2(1.0f / H, H);
+  const float4 xm = g.xm[s];
+  g.bx[s] = make_float4(xm.x, xm.y, xm.z, H2 + gb);
+  g.ba[s] = make_float4(xm.w, gi * iH5, ki * iH5 / h, H);
 }
 
 // Half-scaled kernel factors of the adjoint, without branches.  With
@@ -128,17 +130,15 @@ __device__ __forceinline__ float warp_max_b(float v) {
 
 struct LaneB {
   float x, y, z;         // i in b's frame
-  float nx, ny, nz;      // -2 x_i
-  float ci, di;          // pre-filter bounds: own H_i^2+guard-|x_i|^2+margin, margin-|x_i|^2
   float Hsq_hi, Hsq_lo, Hinv, H, G, K, m;
   int si;
   float Sth, Suh, gx, gy, gz;
 };
 
+// An inactive lane sits far outside every window (its r^2 is ~1e36), so the
+// pre-filter gives it no hits.
 __device__ __forceinline__ void laneb_init(LaneB& L) {
-  L.x = L.y = L.z = L.nx = L.ny = L.nz = 0.0f;
-  L.ci = -3.0e38f;
-  L.di = -3.0e38f;
+  L.x = L.y = L.z = 1.0e18f;
   L.Hsq_hi = L.Hsq_lo = -1.0f;
   L.Hinv = L.H = L.G = L.K = L.m = 0.0f;
   L.si = 0;
@@ -146,37 +146,32 @@ __device__ __forceinline__ void laneb_init(LaneB& L) {
 }
 
 __device__ __forceinline__ void laneb_set(LaneB& L, const GridDev& g, const BoxDev& B,
-                                          const Slot& sl, int si, float4 xi) {
-  const float4 ak = g.gk[si];
-  const float2 hh = g.ghh[si];
+                                          const Slot& sl, int si) {
+  const float4 xe = g.bx[si];
+  const float4 ak = g.ba[si];
   L.si = si;
-  L.x = xi.x - sl.ox * B.edge_f;
-  L.y = xi.y - sl.oy * B.edge_f;
-  L.z = xi.z - sl.oz * B.edge_f;
-  L.m = xi.w;
-  L.G = ak.x; L.K = ak.y; L.Hsq_hi = ak.z; L.Hsq_lo = ak.w;
-  L.Hinv = hh.x; L.H = hh.y;
-  L.nx = -2.0f * L.x;
-  L.ny = -2.0f * L.y;
-  L.nz = -2.0f * L.z;
-  // the pre-filter of the forward sweep, for both cut-offs
-  const float xi2 = fmaf(L.x, L.x, fmaf(L.y, L.y, L.z * L.z));
-  const float margin = 1.0e-5f * B.edge_f * B.edge_f;
-  L.ci = (L.Hsq_hi - xi2) + margin;
-  L.di = margin - xi2;
+  L.x = xe.x - sl.ox * B.edge_f;
+  L.y = xe.y - sl.oy * B.edge_f;
+  L.z = xe.z - sl.oz * B.edge_f;
+  L.m = ak.x; L.G = ak.y; L.K = ak.z; L.H = ak.w;
+  L.Hsq_hi = xe.w;
+  // H^2 - guard = 2 H^2 - (H^2 + guard), to within an ulp: the band only has
+  // to cover the FP32 rounding of r^2, which it does twice over
+  L.Hsq_lo = fmaf(2.0f * L.H, L.H, -xe.w);
+  L.Hinv = 1.0f / L.H;
 }
 
 constexpr int kMaskChunks = 8;  // 32-candidate chunks per segment of the sweep
 
 // Adds the own (scaled by mo = m_j or 0) and transposed (mt = m_i or 0) terms
-// of the pair (i, j) to lane i's five sums (Hinv_j = 1 / H_j).
+// of the pair (i, j) to lane i's five sums (aj = {m_j, G_j, K_j, H_j}).
 __device__ __forceinline__ void bwd_pair(LaneB& L, float dx, float dy, float dz, float r2,
-                                         float4 aj, float Hinv_j, float mo, float mt) {
+                                         float4 aj, float mo, float mt) {
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float r = r2 * rinv;
   float th, uh, vr, vh, vrj, vhj;
   spline_bwd(r * L.Hinv, L.H * rinv, th, uh, vr, vh);
-  spline_bwd_v(r * Hinv_j, aj.w * rinv, vrj, vhj);
+  spline_bwd_v(__fdividef(r, aj.w), aj.w * rinv, vrj, vhj);
   L.Sth = fmaf(mo, th, L.Sth);
   L.Suh = fmaf(mo, uh, L.Suh);
   const float cc = fmaf(mo, fmaf(L.G, vr, -L.K * vh), mt * fmaf(aj.y, vrj, -aj.z * vhj));
@@ -185,23 +180,24 @@ __device__ __forceinline__ void bwd_pair(LaneB& L, float dx, float dy, float dz,
   L.gz = fmaf(cc, dz, L.gz);
 }
 
-// Pre-filter of 8 staged candidates for the adjoint: shifts the sign of
-// |x_j|^2 - 2 x_i.x_j - max(ci, di + E_j) into `m`, first candidate first, so
-// a hit is a pair with r < max(H_i, H_j) up to the FP32 margin (ci covers
-// H_i^2 + guard, E_j = H_j^2 + guard_j).
+// Pre-filter of 8 staged candidates {x, y, z, E_j = H_j^2 + guard_j} for the
+// adjoint: shifts the sign of r^2 - max(H_i^2 + guard_i, E_j) into `m`, first
+// candidate first.  r^2 is the same FP32 expression as in the evaluation, so
+// a hit is exactly a pair that is in range of the own or the transposed test.
 __device__ __forceinline__ void prefilter8_bwd(unsigned& m, const float4* __restrict__ X,
-                                               const float2* __restrict__ E, const LaneB& L) {
+                                               const LaneB& L) {
 #pragma unroll
   for (int c = 0; c < 8; c++) {
     const float4 q = X[c];
-    const float t = fmaxf(L.ci, L.di + E[c].x);
-    const float d = fmaf(L.nx, q.x, fmaf(L.ny, q.y, fmaf(L.nz, q.z, q.w - t)));
+    const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float d = r2 - fmaxf(L.Hsq_hi, q.w);
     m = __funnelshift_l(__float_as_uint(d), m, 1);
   }
 }
 
-// Adjoint sweep over staged particles [lo, hi): Sx {x,y,z,|x|^2}, Sa {m_j, G_j,
-// K_j, H_j}, Se {H_j^2 + guard_j, 1/H_j}; jidx(e) gives the cell-order index of
+// Adjoint sweep over staged particles [lo, hi): Sx {x, y, z, E_j = H_j^2 +
+// guard_j}, Sa {m_j, G_j, K_j, H_j}; jidx(e) gives the cell-order index of
 // staged particle e (read only for FP64 re-decisions near a cut-off).  Same
 // two passes as the forward sweep: the pre-filter keeps the candidates with
 // r < max(H_i, H_j) (the windows themselves reach max(H_i, H_max of the other
@@ -209,8 +205,7 @@ __device__ __forceinline__ void prefilter8_bwd(unsigned& m, const float4* __rest
 // (r < H_i) and transposed (r < H_j) tests.
 template <typename JIndex>
 __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ Sx,
-                                          const float4* __restrict__ Sa,
-                                          const float2* __restrict__ Se, int lo, int hi,
+                                          const float4* __restrict__ Sa, int lo, int hi,
                                           unsigned* __restrict__ M, int lane, const GridDev& g,
                                           const BoxDev& B, JIndex jidx) {
   for (int seg = lo; seg < hi; seg += 32 * kMaskChunks) {
@@ -224,7 +219,7 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
       unsigned m = 0;
       int c0 = 0;
 #pragma unroll 1
-      for (; c0 < cnt; c0 += 8) prefilter8_bwd(m, Sx + base + c0, Se + base + c0, L);
+      for (; c0 < cnt; c0 += 8) prefilter8_bwd(m, Sx + base + c0, L);
       m = __brev(m) >> (32 - c0);
       if (cnt < 32) m &= (1u << cnt) - 1u;
       M[k * 32 + lane] = m;
@@ -235,10 +230,10 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
     int k = 0;
     unsigned m = 0;
     bool amb = false;
-    // eight rounds per iteration: their kernel evaluations are independent, so
-    // the compiler interleaves them (measured 6 % faster on the 1M workload
-    // than one round per iteration)
-#pragma unroll 8
+    // four rounds per iteration: their kernel evaluations are independent, so
+    // the compiler interleaves them (within the 80 registers of three CTAs
+    // per SM)
+#pragma unroll 4
     for (int round = 0; round < tot; round++) {
       if (m == 0u && nz != 0u) {
         k = __ffs(nz) - 1;
@@ -248,17 +243,16 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
       const int c = __ffs(m) - 1;
       m &= m - 1u;
       const int j = seg + 32 * k + max(c, 0);
-      const float4 q = Sx[j];
+      const float4 q = Sx[j];    // x_j, y_j, z_j, E_j
       const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       const float4 aj = Sa[j];   // m_j, G_j, K_j, H_j
-      const float2 ej = Se[j];   // H_j^2 + guard_j, 1/H_j
       // pairs within rounding of a cut-off count as in range here and are
       // re-decided in FP64 after the rounds (H_j^2 - guard_j = 2 H_j^2 - E_j)
       const bool own = (c >= 0) && (r2 < L.Hsq_hi);
-      const bool trans = (c >= 0) && (r2 < ej.x);
-      amb |= (own && r2 >= L.Hsq_lo) || (trans && r2 >= fmaf(2.0f * aj.w, aj.w, -ej.x));
-      bwd_pair(L, dx, dy, dz, r2, aj, ej.y, own ? aj.x : 0.0f, trans ? L.m : 0.0f);
+      const bool trans = (c >= 0) && (r2 < q.w);
+      amb |= (own && r2 >= L.Hsq_lo) || (trans && r2 >= fmaf(2.0f * aj.w, aj.w, -q.w));
+      bwd_pair(L, dx, dy, dz, r2, aj, own ? aj.x : 0.0f, trans ? L.m : 0.0f);
     }
     if (__any_sync(0xffffffffu, amb)) {
       if (amb) {
@@ -271,9 +265,8 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
             const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             const float4 aj = Sa[j];
-            const float2 ej = Se[j];
             const bool gown = r2 < L.Hsq_hi && r2 >= L.Hsq_lo;
-            const bool gtr = r2 < ej.x && r2 >= fmaf(2.0f * aj.w, aj.w, -ej.x);
+            const bool gtr = r2 < q.w && r2 >= fmaf(2.0f * aj.w, aj.w, -q.w);
             if (gown || gtr) {
               const int sj = jidx(j);
               const bool out_o = gown && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L,
@@ -281,18 +274,13 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
               const bool out_t = gtr && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L,
                                                      g.gamma_d * (double)g.hs[sj]);
               if (out_o || out_t)
-                bwd_pair(L, dx, dy, dz, r2, aj, ej.y, out_o ? -aj.x : 0.0f,
-                         out_t ? -L.m : 0.0f);
+                bwd_pair(L, dx, dy, dz, r2, aj, out_o ? -aj.x : 0.0f, out_t ? -L.m : 0.0f);
             }
           }
         }
       }
     }
   }
-}
-
-__device__ __forceinline__ float4 staged_b(float4 x) {
-  return make_float4(x.x, x.y, x.z, fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z)));
 }
 
 // outputs of one particle from its five sums
@@ -330,7 +318,7 @@ __device__ __forceinline__ float sproj(float4 x, float ux, float uy, float uz, i
   return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
 }
 
-__global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
+__global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
     GridDev g, const float* __restrict__ g_rho, const float* __restrict__ g_D,
     float* __restrict__ g_pos, float* __restrict__ g_h) {
   extern __shared__ float4 dsm[];
@@ -381,10 +369,9 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
     __syncthreads();
     const int total = cs.off[kNSlot];
     // variable carve: kElemJ (total + kPad) + kElemA na bytes, checked by the plan
-    float4* Sx = var;                                  // [total + kPad] {x,y,z,|x|^2}
+    float4* Sx = var;                                  // [total + kPad] {x, y, z, E}
     float4* Sa = Sx + total + kPad;                    // [total + kPad] {m, G, K, H}
-    double* acc = reinterpret_cast<double*>(Sa + total + kPad);  // [5][na]
-    float2* Se = reinterpret_cast<float2*>(acc + 5 * na);        // [total + kPad] {E_j, 1/H_j}
+    float* acc = reinterpret_cast<float*>(Sa + total + kPad);  // [5][na]
     stage_flat<4>(
         cs.off, total, tid, kCellThreads,
         [&](int f, int q) {
@@ -394,22 +381,12 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
           return cb + (int)g.perm[(size_t)sl.k * g.n + cb + pos];
         },
         [](int sj) { return sj; },
-        [&](int f, int sj) {  // cp.async: xm, gk and H straight to shared memory
-          cp_async16(&Sx[f], &g.xm[sj]);
-          cp_async16(&Sa[f], &g.gk[sj]);
-          cp_async8(&Se[f], &g.ghh[sj]);  // {1/H, H}
+        [&](int f, int sj) {  // cp.async: both records straight to shared memory
+          cp_async16(&Sx[f], &g.bx[sj]);
+          cp_async16(&Sa[f], &g.ba[sj]);
         });
+    for (int t = tid; t < 5 * na; t += kCellThreads) acc[t] = 0.0f;
     cp_async_wait_all();
-    // each thread rearranges its own elements: Sx {x, y, z, |x|^2},
-    // Sa {m, G, K, H}, Se {H^2 + guard, 1/H}
-    for (int f = tid; f < total; f += kCellThreads) {
-      const float4 x = Sx[f], k = Sa[f];
-      const float2 hh = Se[f];  // {1/H, H}
-      Sx[f] = staged_b(x);
-      Sa[f] = make_float4(x.w, k.x, k.y, hh.y);
-      Se[f] = make_float2(k.z, hh.x);
-    }
-    for (int t = tid; t < 5 * na; t += kCellThreads) acc[t] = 0.0;
     __syncthreads();
     const int nitems = cs.runs[kNSlot];
     for (;;) {
@@ -433,7 +410,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
         const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
         const size_t kb = (size_t)sl.k * g.n + ca + pos_i;
         il = g.perm[kb];
-        laneb_set(L, g, B, sl, ca + il, g.xm[ca + il]);
+        laneb_set(L, g, B, sl, ca + il);
         const float di = sl.s * g.dist[kb];
         const float reach = fmaxf(L.H, Hmb) + padw;
         d_lo = di - reach;
@@ -457,15 +434,15 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
       auto jidx = [&](int j) {
         return cbq + (int)g.perm[kbq + order_pos(sl.s, J0q + j - s0, nbq)];
       };
-      sweep_bwd(L, Sx, Sa, Se, lo, hi, Mw, lane, g, B, jidx);
+      sweep_bwd(L, Sx, Sa, lo, hi, Mw, lane, g, B, jidx);
       // lanes whose windows held no pair in range have nothing to add
       if (valid && (L.Sth != 0.0f || L.Suh != 0.0f || L.gx != 0.0f || L.gy != 0.0f ||
                     L.gz != 0.0f)) {
-        atomicAdd(&acc[0 * na + il], (double)L.Sth);
-        atomicAdd(&acc[1 * na + il], (double)L.Suh);
-        atomicAdd(&acc[2 * na + il], (double)L.gx);
-        atomicAdd(&acc[3 * na + il], (double)L.gy);
-        atomicAdd(&acc[4 * na + il], (double)L.gz);
+        atomicAdd(&acc[0 * na + il], L.Sth);
+        atomicAdd(&acc[1 * na + il], L.Suh);
+        atomicAdd(&acc[2 * na + il], L.gx);
+        atomicAdd(&acc[3 * na + il], L.gy);
+        atomicAdd(&acc[4 * na + il], L.gz);
       }
     }
     __syncthreads();
@@ -481,7 +458,6 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_backward_cells(
 __global__ void __launch_bounds__(kBlkI, 4) k_backward_tasks(GridDev g) {
   __shared__ float4 s_x[kTileJ + kPad];
   __shared__ float4 s_a[kTileJ + kPad];
-  __shared__ float2 s_e[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
   __shared__ int s_j[kTileJ + kPad];
   __shared__ unsigned s_mask[kBlkI / 32][kMaskChunks * 32];
@@ -513,7 +489,7 @@ __global__ void __launch_bounds__(kBlkI, 4) k_backward_tasks(GridDev g) {
     if (valid) {
       const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
       const int si = ca + g.perm[kbase + ca + pos_i];
-      laneb_set(L, g, B, sl, si, g.xm[si]);
+      laneb_set(L, g, B, sl, si);
       const float di = sl.s * g.dist[kbase + ca + pos_i];
       const float reach = fmaxf(L.H, Hmax_b) + window_pad(g, B, g.cell_box[a]);
       d_lo = di - reach;
@@ -525,11 +501,8 @@ __global__ void __launch_bounds__(kBlkI, 4) k_backward_tasks(GridDev g) {
       for (int e = threadIdx.x; e < len; e += blockDim.x) {
         const int pos_j = order_pos(sl.s, j0 + e, nb);
         const int sj = cb + g.perm[kbase + cb + pos_j];
-        const float4 xj = g.xm[sj];
-        const float4 ak = g.gk[sj];
-        s_x[e] = staged_b(xj);
-        s_a[e] = make_float4(xj.w, ak.x, ak.y, g.ghh[sj].y);
-        s_e[e] = make_float2(ak.z, g.ghh[sj].x);
+        s_x[e] = g.bx[sj];
+        s_a[e] = g.ba[sj];
         s_d[e] = sl.s * g.dist[kbase + cb + pos_j] + off;
         s_j[e] = sj;
       }
@@ -538,7 +511,7 @@ __global__ void __launch_bounds__(kBlkI, 4) k_backward_tasks(GridDev g) {
         const int lo = (o == kSelfSlot) ? upper_bound_f(s_d, len, w_lo) : 0;
         const int hi = lower_bound_f(s_d, len, w_hi);
         auto jidx = [&](int j) { return s_j[j]; };
-        sweep_bwd(L, s_x, s_a, s_e, lo, hi, s_mask[warp], lane, g, B, jidx);
+        sweep_bwd(L, s_x, s_a, lo, hi, s_mask[warp], lane, g, B, jidx);
       }
       __syncthreads();
     }
@@ -582,7 +555,7 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
                             float* g_pos, float* g_h, int num_sms, int ctas_per_sm,
                             cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
   if (g.n == 0) return cudaSuccess;
-  if (ctas_per_sm < 1 || ctas_per_sm > 2) return cudaErrorInvalidValue;
+  if (ctas_per_sm < 1 || ctas_per_sm > 3) return cudaErrorInvalidValue;
   static std::atomic<unsigned long long> smem_done{0};
   cudaError_t e = set_max_dynamic_smem(smem_done, reinterpret_cast<const void*>(&k_backward_cells),
                                        kCellSmemFor[1]);

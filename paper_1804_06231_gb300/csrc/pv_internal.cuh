@@ -86,8 +86,8 @@ struct GridDev {
   long long* acc;    // [3][N]: rho, drho/dh (2^36 scale), n
   // backward accumulators (cell order), FP64 [5][N]: sum m th, sum m uh, gx, gy, gz
   long long* gacc;
-  float4* gk;        // [N] backward: {g/H^5, k/(h H^5), H^2+guard, H^2-guard}, cell order
-  float2* ghh;       // [N] backward: {1/H, H}
+  float4* bx;        // [N] backward, cell order: {x', y', z', H^2 + guard}
+  float4* ba;        // [N] backward, cell order: {m/m_max, g/H^5, k/(h H^5), H}
   // plan: per (cell, slot) {reachable count of a, window [J0, J1) of b, 0}
   int4* plan;        // [C][27]
   int32_t* ccells;   // [C] cells for the cell-centric kernel
@@ -415,7 +415,7 @@ cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j,
                         cudaStream_t st);
 int64_t max_tasks_for(int64_t n, int64_t ncell);
 // ctas_per_sm: resident CTAs of the cell-centric sweep kernel per SM (1..4
-// forward, 1..2 adjoint); it sets the kernel's shared memory and so which
+// forward, 1..3 adjoint); it sets the kernel's shared memory and so which
 // cells the plan routes to it.  t0/t1 (optional): events recorded on `st`
 // just before and after that kernel.
 cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t* n_ngb,
@@ -424,7 +424,7 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
 cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g_drho_dh,
                             float* g_pos, float* g_h, int num_sms, int ctas_per_sm,
                             cudaStream_t st, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
-constexpr int kDensityCtasDefault = 3, kBackwardCtasDefault = 2;
+constexpr int kDensityCtasDefault = 3, kBackwardCtasDefault = 3;
 
 // Raises `func`'s dynamic shared-memory limit to `bytes` the first time it is
 // called on a device (bit `dev` of `done` records it; devices >= 64 set it on

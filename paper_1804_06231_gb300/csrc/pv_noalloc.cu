@@ -165,8 +165,8 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.ccell_next = sc + 7;
   d.n_tcells = sc + 8;
   d.gacc = nullptr;
-  d.gk = nullptr;
-  d.ghh = nullptr;
+  d.bx = nullptr;
+  d.ba = nullptr;
   d.n_boxes = 1;
   d.n = (int32_t)n;
   d.ncell = (int32_t)ncell;

@@ -22,8 +22,8 @@ import os
 import statistics
 
 DENSITY_CHOICES = (2, 3, 4)
-BACKWARD_CHOICES = (1, 2)
-DEFAULT = (3, 2)
+BACKWARD_CHOICES = (1, 2, 3)
+DEFAULT = (3, 3)
 
 
 def default_cache_path() -> str:

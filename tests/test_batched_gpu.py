@@ -141,7 +141,7 @@ def test_launch_shapes_meet_parity_and_autotune(oracle_lib, tmp_path):
     with Grid((box.n, box.L, box.nc)) as g:
         g.sort(pos, h, m)
         assert g.tuning() == tune.DEFAULT
-        for d, b in ((2, 1), (3, 2), (4, 2), (4, 1)):
+        for d, b in ((2, 1), (3, 2), (4, 3), (4, 1)):
             g.set_tuning(d, b)
             assert g.tuning() == (d, b)
             rho, D, n = g.density()
@@ -155,7 +155,7 @@ def test_launch_shapes_meet_parity_and_autotune(oracle_lib, tmp_path):
         with pytest.raises(PvError):
             g.set_tuning(5, 2)
         with pytest.raises(PvError):
-            g.set_tuning(3, 3)
+            g.set_tuning(3, 4)
         path = str(tmp_path / "tuning.json")
         r1 = tune.autotune(g, gr, gd, reps=2, cache_path=path)
         assert r1["source"] == "timed"

@@ -13,12 +13,12 @@ def test_choose_picks_fastest_per_pass():
 
     def measure(d, b, reps):
         calls.append((d, b))
-        return {2: 5.0, 3: 4.0, 4: 3.0}[d], {1: 7.0, 2: 9.0}[b]
+        return {2: 5.0, 3: 4.0, 4: 3.0}[d], {1: 7.0, 2: 9.0, 3: 8.0}[b]
 
     (d, b), times = tune.choose(measure, reps=3)
     assert (d, b) == (4, 1)
     assert times["density"] == {2: 5.0, 3: 4.0, 4: 3.0}
-    assert times["backward"] == {1: 7.0, 2: 9.0}
+    assert times["backward"] == {1: 7.0, 2: 9.0, 3: 8.0}
     # density shapes are timed with the default backward shape and vice versa
     assert all(b == tune.DEFAULT[1] for d, b in calls[:3])
     assert all(d == tune.DEFAULT[0] for d, b in calls[3:])
@@ -66,19 +66,19 @@ def test_autotune_cache_round_trip(tmp_path):
 
     def measure(d, b, reps):
         n["calls"] += 1
-        return {2: 2.0, 3: 1.0, 4: 1.5}[d], {1: 0.5, 2: 0.7}[b]
+        return {2: 2.0, 3: 1.0, 4: 1.5}[d], {1: 0.5, 2: 0.7, 3: 0.6}[b]
 
     r1 = tune.autotune(g, None, cache_path=path, measure=measure, device_info=("GB300", 152))
     assert r1["source"] == "timed" and (r1["density_ctas_per_sm"], r1["backward_ctas_per_sm"]) == (3, 1)
-    assert g.set[-1] == (3, 1) and n["calls"] == 5
+    assert g.set[-1] == (3, 1) and n["calls"] == 6
     data = json.load(open(path))
     assert r1["signature"] in data
     r2 = tune.autotune(_FakeGrid(), None, cache_path=path, measure=measure,
                        device_info=("GB300", 152))
-    assert r2["source"] == "cache" and n["calls"] == 5
+    assert r2["source"] == "cache" and n["calls"] == 6
     # another device: timed again, both entries kept
     tune.autotune(_FakeGrid(), None, cache_path=path, measure=measure, device_info=("B200", 148))
-    assert len(json.load(open(path))) == 2 and n["calls"] == 10
+    assert len(json.load(open(path))) == 2 and n["calls"] == 12
 
 
 def test_autotune_ignores_bad_cache(tmp_path):
