@@ -88,6 +88,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
+    p.add_argument("--launch-shape", default="",
+                   help="D,B: CTAs per SM of the density and adjoint sweep kernels (no tuning)")
     p.add_argument("--workload", default="uniform1m", choices=["uniform1m", "clustered4m"],
                    help="the timed workload (clustered4m: for profiling the dense-cell paths)")
     p.add_argument("--no-extras", action="store_true",
@@ -515,8 +517,14 @@ def main():
         grid.backward(g_rho, g_d, gpos, gh)
 
     tuning = None
+    shape0 = grid.tuning()
     step()  # first sort, so that the autotuner sees the sorted grid
-    if not args.no_tune:
+    if args.launch_shape:
+        d_ctas, b_ctas = (int(x) for x in args.launch_shape.split(","))
+        grid.set_tuning(d_ctas, b_ctas)
+        tuning = {"density_ctas_per_sm": d_ctas, "backward_ctas_per_sm": b_ctas,
+                  "source": "given"}
+    elif not args.no_tune:
         from paper_1804_06231_gb300 import tune
         tr = tune.autotune(grid, g_rho, g_d, reps=5)
         tuning = {"density_ctas_per_sm": tr["density_ctas_per_sm"],
@@ -692,8 +700,9 @@ def main():
                                     if args.workload == "clustered4m" else WORKLOAD),
                        "n_particles_per_gpu": n, "cells": box.nc ** 3,
                        "l2": "flushed between steps (512 MiB write)",
-                       "launch_shape": tuning or {"density_ctas_per_sm": 3,
-                                                  "backward_ctas_per_sm": 2, "source": "default"},
+                       "launch_shape": tuning or {"density_ctas_per_sm": shape0[0],
+                                                  "backward_ctas_per_sm": shape0[1],
+                                                  "source": "default"},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "e2e": e2e,
             "gpu_launches": launches,
