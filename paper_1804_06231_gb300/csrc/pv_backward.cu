@@ -27,7 +27,7 @@
 // at a time into bit masks), with both the own and the transposed cut-off in
 // the pre-filter; per-particle sums in FP32 shared-memory accumulators (one
 // addition per particle and work item).  A staged particle takes 32 bytes
-// ({x, y, z, H^2 + guard} and {m, G, K, H}), so three CTAs fit an SM.  Cells
+// ({x, y, z, H^2 + guard} and {m, G', K, H}), so three CTAs fit an SM.  Cells
 // whose windows exceed the shared-memory budget run as tasks (cell, slot,
 // block of 128 particles) with FP64 global accumulators.
 #include <cuda_runtime.h>
@@ -68,7 +68,8 @@ __device__ __forceinline__ TaskB decode_b(int4 t) {
 
 // Upstream gradients to cell order, with the per-particle constants of the
 // sweep, in the form the sweeps stage them: bx = {x', y', z', E = H^2 +
-// guard} and ba = {m / m_max, G = g/H^5, K = k/(h H^5), H}.
+// guard} and ba = {m / m_max, G' = G - 4K, K, H} with G = g/H^5 and
+// K = k/(h H^5).
 __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
                            const float* __restrict__ g_D) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -83,40 +84,36 @@ __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
   const float ki = g_D ? g_D[i] : 0.0f;
   const float gb = guard_band(H, B.edge_f);
   const float4 xm = g.xm[s];
+  const float K = ki * iH5 / h;
   g.bx[s] = make_float4(xm.x, xm.y, xm.z, H2 + gb);
-  g.ba[s] = make_float4(xm.w, gi * iH5, ki * iH5 / h, H);
+  g.ba[s] = make_float4(xm.w, fmaf(-4.0f, K, gi * iH5), K, H);
 }
 
 // Half-scaled kernel factors of the adjoint, without branches.  With
-// s = max(1 - q, 0) and t = max(1/2 - q, 0) the cubic spline is
-// w = s^3 - 4 t^3 (half-scaled), so every factor is a piece in s minus four
-// times the same piece in t:
-//   th = 3w + q w'                = s^2 (3 - 6q) - t^2 (6 - 24q)
-//   uh = 12w + 8q w' + q^2 w''    = A(s) - 4 A(t),  A(x) = x (12x^2 - 24qx + 6q^2)
-//   vr = w'/q                     = (12 t^2 - 3 s^2) / q
-//   vh = (4w' + q w'')/q          = 4 vr + 6s - 24t
-// For q < 1/2 the numerator of vr is formed as q (9q - 6) (the same
-// polynomial), which keeps vr accurate as q -> 0.
-__device__ __forceinline__ float vr_half(float q, float qinv, float s) {
-  const float core = q < 0.5f ? q * fmaf(9.0f, q, -6.0f) : -3.0f * s * s;
-  return core * qinv;
-}
-
+// s = 1 - q, each factor is one polynomial on q < 1/2 and one on 1/2 <= q < 1
+// (the two cubic pieces of the spline), chosen by one predicate:
+//   th = 3w + q w'                 q<1/2: 3/2 + q^2 (18q - 15)   else s^2 (3 - 6q)
+//   uh = 12w + 8q w' + q^2 w''     q<1/2: 6 + q^2 (126q - 90)    else 6 s (7s^2 - 6s + 1)
+//   vr = w'/q                      q<1/2: 9q - 6                 else -3 s^2 / q
+//   w6 = (4w' + q w'')/q - 4 vr    q<1/2: 18q - 6                else 6 s
+// (vh = 4 vr + w6 is the factor of W_hr; s is clamped at 0, so every factor
+// vanishes for q >= 1).  The gradient coefficient G vr - K vh is formed as
+// (G - 4K) vr - K w6, with G' = G - 4K stored per particle.
 __device__ __forceinline__ void spline_bwd(float q, float qinv, float& th, float& uh, float& vr,
-                                           float& vh) {
-  const float s = fmaxf(1.0f - q, 0.0f), t = fmaxf(0.5f - q, 0.0f);
-  const float s2 = s * s, t2 = t * t;
-  th = fmaf(s2, fmaf(-6.0f, q, 3.0f), -t2 * fmaf(-24.0f, q, 6.0f));
-  const float q6 = 6.0f * q * q;
-  uh = fmaf(s, fmaf(12.0f * s, s - 2.0f * q, q6), -4.0f * t * fmaf(12.0f * t, t - 2.0f * q, q6));
-  vr = vr_half(q, qinv, s);
-  vh = fmaf(4.0f, vr, fmaf(6.0f, s, -24.0f * t));
+                                           float& w6) {
+  const bool lo = q < 0.5f;
+  const float s = fmaxf(1.0f - q, 0.0f), s2 = s * s, q2 = q * q;
+  th = lo ? fmaf(q2, fmaf(18.0f, q, -15.0f), 1.5f) : s2 * fmaf(-6.0f, q, 3.0f);
+  uh = lo ? fmaf(q2, fmaf(126.0f, q, -90.0f), 6.0f) : 6.0f * s * fmaf(7.0f, s2, fmaf(-6.0f, s, 1.0f));
+  vr = lo ? fmaf(9.0f, q, -6.0f) : (-3.0f * s2) * qinv;
+  w6 = lo ? fmaf(18.0f, q, -6.0f) : 6.0f * s;
 }
 
-__device__ __forceinline__ void spline_bwd_v(float q, float qinv, float& vr, float& vh) {
-  const float s = fmaxf(1.0f - q, 0.0f), t = fmaxf(0.5f - q, 0.0f);
-  vr = vr_half(q, qinv, s);
-  vh = fmaf(4.0f, vr, fmaf(6.0f, s, -24.0f * t));
+__device__ __forceinline__ void spline_bwd_v(float q, float qinv, float& vr, float& w6) {
+  const bool lo = q < 0.5f;
+  const float s = fmaxf(1.0f - q, 0.0f);
+  vr = lo ? fmaf(9.0f, q, -6.0f) : (-3.0f * s * s) * qinv;
+  w6 = lo ? fmaf(18.0f, q, -6.0f) : 6.0f * s;
 }
 
 __device__ __forceinline__ float warp_min_b(float v) {
@@ -130,7 +127,7 @@ __device__ __forceinline__ float warp_max_b(float v) {
 
 struct LaneB {
   float x, y, z;         // i in b's frame
-  float Hsq_hi, Hsq_lo, Hinv, H, G, K, m;
+  float Hsq_hi, Hsq_lo, Hinv, H, G, K, m;  // G holds G' = G - 4K
   int si;
   float Sth, Suh, gx, gy, gz;
 };
@@ -164,17 +161,17 @@ __device__ __forceinline__ void laneb_set(LaneB& L, const GridDev& g, const BoxD
 constexpr int kMaskChunks = 8;  // 32-candidate chunks per segment of the sweep
 
 // Adds the own (scaled by mo = m_j or 0) and transposed (mt = m_i or 0) terms
-// of the pair (i, j) to lane i's five sums (aj = {m_j, G_j, K_j, H_j}).
+// of the pair (i, j) to lane i's five sums (aj = {m_j, G'_j, K_j, H_j}).
 __device__ __forceinline__ void bwd_pair(LaneB& L, float dx, float dy, float dz, float r2,
                                          float4 aj, float mo, float mt) {
   const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
   const float r = r2 * rinv;
-  float th, uh, vr, vh, vrj, vhj;
-  spline_bwd(r * L.Hinv, L.H * rinv, th, uh, vr, vh);
-  spline_bwd_v(__fdividef(r, aj.w), aj.w * rinv, vrj, vhj);
+  float th, uh, vr, w6, vrj, w6j;
+  spline_bwd(r * L.Hinv, L.H * rinv, th, uh, vr, w6);
+  spline_bwd_v(__fdividef(r, aj.w), aj.w * rinv, vrj, w6j);
   L.Sth = fmaf(mo, th, L.Sth);
   L.Suh = fmaf(mo, uh, L.Suh);
-  const float cc = fmaf(mo, fmaf(L.G, vr, -L.K * vh), mt * fmaf(aj.y, vrj, -aj.z * vhj));
+  const float cc = fmaf(mo, fmaf(L.G, vr, -L.K * w6), mt * fmaf(aj.y, vrj, -aj.z * w6j));
   L.gx = fmaf(cc, dx, L.gx);
   L.gy = fmaf(cc, dy, L.gy);
   L.gz = fmaf(cc, dz, L.gz);
@@ -197,7 +194,7 @@ __device__ __forceinline__ void prefilter8_bwd(unsigned& m, const float4* __rest
 }
 
 // Adjoint sweep over staged particles [lo, hi): Sx {x, y, z, E_j = H_j^2 +
-// guard_j}, Sa {m_j, G_j, K_j, H_j}; jidx(e) gives the cell-order index of
+// guard_j}, Sa {m_j, G'_j, K_j, H_j}; jidx(e) gives the cell-order index of
 // staged particle e (read only for FP64 re-decisions near a cut-off).  Same
 // two passes as the forward sweep: the pre-filter keeps the candidates with
 // r < max(H_i, H_j) (the windows themselves reach max(H_i, H_max of the other
@@ -246,7 +243,7 @@ __device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ S
       const float4 q = Sx[j];    // x_j, y_j, z_j, E_j
       const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float4 aj = Sa[j];   // m_j, G_j, K_j, H_j
+      const float4 aj = Sa[j];   // m_j, G'_j, K_j, H_j
       // pairs within rounding of a cut-off count as in range here and are
       // re-decided in FP64 after the rounds (H_j^2 - guard_j = 2 H_j^2 - E_j)
       const bool own = (c >= 0) && (r2 < L.Hsq_hi);
@@ -370,7 +367,7 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
     const int total = cs.off[kNSlot];
     // variable carve: kElemJ (total + kPad) + kElemA na bytes, checked by the plan
     float4* Sx = var;                                  // [total + kPad] {x, y, z, E}
-    float4* Sa = Sx + total + kPad;                    // [total + kPad] {m, G, K, H}
+    float4* Sa = Sx + total + kPad;                    // [total + kPad] {m, G', K, H}
     float* acc = reinterpret_cast<float*>(Sa + total + kPad);  // [5][na]
     stage_flat<4>(
         cs.off, total, tid, kCellThreads,
@@ -532,19 +529,35 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
                                  const float* __restrict__ g_D, float* __restrict__ g_pos,
                                  float* __restrict__ g_h) {
   if (*g.flags) return;
-  const int nt = *g.n_tcells;
   const float munit = (float)(16.0 / 3.14159265358979323846);
   double* acc = reinterpret_cast<double*>(g.gacc);
   const size_t N = (size_t)g.n;
-  for (int c = blockIdx.x; c < nt; c += gridDim.x) {
-    const int a = g.tcells[c];
-    const int ca = g.cell_start[a], na = g.cell_count[a];
-    const float mscale = munit * g.m_max[g.cell_box[a]];
-    for (int t = threadIdx.x; t < na; t += blockDim.x) {
-      const int s = ca + t;
-      write_bwd(g, s, acc[s], acc[N + s], acc[2 * N + s], acc[3 * N + s], acc[4 * N + s],
-                g_rho, g_D, g_pos, g_h, mscale);
-      for (int q = 0; q < 5; q++) acc[q * N + s] = 0.0;
+  const int lane = threadIdx.x & 31;
+  auto fin = [&](int s, float mscale) {
+    write_bwd(g, s, acc[s], acc[N + s], acc[2 * N + s], acc[3 * N + s], acc[4 * N + s], g_rho,
+              g_D, g_pos, g_h, mscale);
+    for (int q = 0; q < 5; q++) acc[q * N + s] = 0.0;
+  };
+  // as the forward finalize: one warp per self-slot task (blocks of kBlkI
+  // cell-local indices), or one block per task cell when the self slot is
+  // masked out
+  if ((g.slot_mask >> kSelfSlot) & 1u) {
+    const int ntask = *g.ntask;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ntask;
+         w += (gridDim.x * blockDim.x) >> 5) {
+      const TaskB tk = decode_b(g.tasks[w]);
+      if (tk.o != kSelfSlot) continue;
+      const int ca = g.cell_start[tk.a];
+      const float mscale = munit * g.m_max[g.cell_box[tk.a]];
+      for (int t = tk.p0 + lane; t < tk.p1; t += 32) fin(ca + t, mscale);
+    }
+  } else {
+    const int nt = *g.n_tcells;
+    for (int c = blockIdx.x; c < nt; c += gridDim.x) {
+      const int a = g.tcells[c];
+      const int ca = g.cell_start[a], na = g.cell_count[a];
+      const float mscale = munit * g.m_max[g.cell_box[a]];
+      for (int t = threadIdx.x; t < na; t += blockDim.x) fin(ca + t, mscale);
     }
   }
 }

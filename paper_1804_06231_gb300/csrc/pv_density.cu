@@ -132,31 +132,59 @@ __global__ void k_plan_slots(GridDev g, int wide) {
 // One thread per cell: route the cell to the cell-centric kernel when its
 // staged windows fit `smem_budget`, else to the task kernel, reserving one
 // task of kBlkI particles per block of each slot (the first task's index goes
-// to plan.w; k_plan_tasks fills the tasks in).
+// to plan.w; k_plan_tasks fills the tasks in).  The list appends and the task
+// reservations are aggregated per warp (one atomic per warp and list instead
+// of one per cell: a clustered box has tens of thousands of cells).
 __global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a) {
   if (*g.flags) return;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= g.ncell) return;
-  const int na = g.cell_count[a];
-  if (na == 0) return;
-  int4* pl = g.plan + (size_t)a * kNSlot;
-  int total = 0;
-  for (int o = 0; o < kNSlot; o++) total += pl[o].z - pl[o].y;
-  if (elem_j * (total + kPad) + elem_a * na <= smem_budget) {
-    g.ccells[atomicAdd(g.n_ccells, 1)] = a;
+  const int lane = threadIdx.x & 31;
+  int na = 0;
+  int4* pl = nullptr;
+  bool fits = false;
+  int nblk_tot = 0;  // task blocks of this cell (task-path cells only)
+  if (a < g.ncell) {
+    na = g.cell_count[a];
+    if (na > 0) {
+      pl = g.plan + (size_t)a * kNSlot;
+      int total = 0;
+      for (int o = 0; o < kNSlot; o++) total += pl[o].z - pl[o].y;
+      fits = elem_j * (total + kPad) + elem_a * na <= smem_budget;
+      if (!fits)
+        for (int o = 0; o < kNSlot; o++) nblk_tot += (pl[o].x + kBlkI - 1) / kBlkI;
+    }
+  }
+  const bool task = na > 0 && !fits;
+  const unsigned below = (1u << lane) - 1u;
+  const unsigned mc = __ballot_sync(0xffffffffu, fits), mt = __ballot_sync(0xffffffffu, task);
+  int incl = nblk_tot;  // inclusive scan of the task blocks over the warp
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, s);
+    if (lane >= s) incl += v;
+  }
+  int bc = 0, bt = 0, bk = 0;
+  if (lane == 31) {
+    if (mc) bc = atomicAdd(g.n_ccells, __popc(mc));
+    if (mt) bt = atomicAdd(g.n_tcells, __popc(mt));
+    if (incl) bk = atomicAdd(g.ntask, incl);
+  }
+  bc = __shfl_sync(0xffffffffu, bc, 31);
+  bt = __shfl_sync(0xffffffffu, bt, 31);
+  bk = __shfl_sync(0xffffffffu, bk, 31);
+  if (fits) g.ccells[bc + __popc(mc & below)] = a;
+  if (!task) return;
+  g.tcells[bt + __popc(mt & below)] = a;
+  int base = bk + incl - nblk_tot;
+  if (base + nblk_tot > g.max_tasks) {  // cannot happen with the allocated bound
+    atomicOr(g.flags, PV_FLAG_CELL_OVERFLOW);
     return;
   }
-  g.tcells[atomicAdd(g.n_tcells, 1)] = a;
   for (int o = 0; o < kNSlot; o++) {
     const int nI = pl[o].x;
     if (nI == 0) continue;
-    const int nblk = (nI + kBlkI - 1) / kBlkI;
-    const int base = atomicAdd(g.ntask, nblk);
-    if (base + nblk > g.max_tasks) {  // cannot happen with the allocated bound
-      atomicOr(g.flags, PV_FLAG_CELL_OVERFLOW);
-      return;
-    }
     pl[o].w = base;
+    base += (nI + kBlkI - 1) / kBlkI;
   }
 }
 
@@ -627,26 +655,43 @@ __global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
   if (lane == 0 && guards) atomicAdd(&g.counters[1], (unsigned long long)guards);
 }
 
-// Fixed point -> caller order for the particles of the task-path cells.
+// Fixed point -> caller order for the particles of the task-path cells.  The
+// self-slot tasks of a cell cover its positions [0, na) in blocks of kBlkI,
+// so one warp per self-slot task finalises cell-local indices [p0, p1): big
+// cells are spread over many warps.  (A pass whose slot mask leaves out the
+// self slot has no such tasks: one block per task cell then.)
 __global__ void k_finalize_t(GridDev g, float* __restrict__ rho, float* __restrict__ drho_dh,
                              int32_t* __restrict__ n_ngb) {
   if (*g.flags) return;
-  const int nt = *g.n_tcells;
+  const int lane = threadIdx.x & 31;
   const float munit = (float)(16.0 / 3.14159265358979323846 * kFixInv);
   unsigned long long inter = 0;
   const size_t N = (size_t)g.n;
-  for (int c = blockIdx.x; c < nt; c += gridDim.x) {
-    const int a = g.tcells[c];
-    const int ca = g.cell_start[a], na = g.cell_count[a];
-    const float mscale = munit * g.m_max[g.cell_box[a]];
-    for (int t = threadIdx.x; t < na; t += blockDim.x) {
-      const int s = ca + t;
-      const long long an = g.acc[2 * N + s];
-      write_out(g, s, g.acc[s], g.acc[N + s], (int)an, rho, drho_dh, n_ngb, mscale);
-      inter += (unsigned long long)(an - 1);
-      g.acc[s] = 0;
-      g.acc[N + s] = 0;
-      g.acc[2 * N + s] = 0;
+  auto fin = [&](int s, float mscale) {
+    const long long an = g.acc[2 * N + s];
+    write_out(g, s, g.acc[s], g.acc[N + s], (int)an, rho, drho_dh, n_ngb, mscale);
+    inter += (unsigned long long)(an - 1);
+    g.acc[s] = 0;
+    g.acc[N + s] = 0;
+    g.acc[2 * N + s] = 0;
+  };
+  if ((g.slot_mask >> kSelfSlot) & 1u) {
+    const int ntask = *g.ntask;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ntask;
+         w += (gridDim.x * blockDim.x) >> 5) {
+      const Task tk = decode(g.tasks[w]);
+      if (tk.o != kSelfSlot) continue;
+      const int ca = g.cell_start[tk.a];
+      const float mscale = munit * g.m_max[g.cell_box[tk.a]];
+      for (int t = tk.p0 + lane; t < tk.p1; t += 32) fin(ca + t, mscale);
+    }
+  } else {
+    const int nt = *g.n_tcells;
+    for (int c = blockIdx.x; c < nt; c += gridDim.x) {
+      const int a = g.tcells[c];
+      const int ca = g.cell_start[a], na = g.cell_count[a];
+      const float mscale = munit * g.m_max[g.cell_box[a]];
+      for (int t = threadIdx.x; t < na; t += blockDim.x) fin(ca + t, mscale);
     }
   }
   for (int s = 16; s > 0; s >>= 1) inter += __shfl_xor_sync(0xffffffffu, inter, s);
