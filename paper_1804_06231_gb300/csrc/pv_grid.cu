@@ -13,12 +13,15 @@
 //              checks (latched flags)
 //   k_scan     exclusive scan of the occupancies, list of big cells
 //   k_scatter  caller index of every cell-order slot
-//   k_cell_sort   one CTA per cell: gathers the cell's particles into cell
-//              order (FP32 offsets + normalised mass, h, wrapped FP64
-//              position) with coalesced writes, the cell's H_max, and, for a
-//              cell of <= 384 particles, the 13 sorts, one warp per axis:
-//              bucket (counting) sort in shared memory, exact order inside a
-//              bucket by (projection, caller index)
+//   k_cell_sort   one CTA per cell of more than 64 particles: gathers the
+//              cell's particles into cell order (FP32 offsets + normalised
+//              mass, h, wrapped FP64 position) with coalesced writes, the
+//              cell's H_max, and, for a cell of <= 384 particles, the 13
+//              sorts, one warp per axis: bucket (counting) sort in shared
+//              memory, exact order inside a bucket by (projection, caller
+//              index)
+//   k_cell_sort_tiny  the same for cells of <= 64 particles, one warp per
+//              cell (the 13 axes in turn)
 //   k_sort_big    one CTA per (larger cell, axis), the same algorithm with up
 //              to 8192 buckets in shared memory
 //   k_update, k_update_check  new positions on a kept sort (pv_update_positions)
@@ -30,8 +33,12 @@ namespace pv {
 
 namespace {
 
-// cells of up to kSortSmallMax particles sort in one CTA (74 KB of shared
-// memory, three CTAs per SM); larger ones with one CTA per (cell, axis)
+// cells of up to kSortTinyMax particles are gathered and sorted by one warp
+// (all 13 axes in turn), cells of up to kSortSmallMax particles by one CTA
+// (74 KB of shared memory, three CTAs per SM, one warp per axis); larger
+// ones are gathered by that CTA and sorted with one CTA per (cell, axis)
+constexpr int kSortTinyMax = 64;
+constexpr int kSortTinyWarps = 8;
 constexpr int kSortSmallMax = 384;
 static_assert(kSortSmallMax % 32 == 0, "whole particles per lane in the cell sort");
 constexpr int kSortThreads = kNDir * 32;
@@ -366,6 +373,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g,
   uint16_t* s_tmp = s_out + kNDir * kMax;                        // [13][kMax]
   const int c = blockIdx.x;
   const int cnt = g.cell_count[c];
+  if (cnt <= kSortTinyMax) return;  // k_cell_sort_tiny's
   const int cs = g.cell_start[c];
   const int bx = g.cell_box[c];
   const BoxDev B = g.boxes[bx];
@@ -442,6 +450,103 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g,
       const int v = out[t];
       g.perm[base + t] = (uint16_t)v;
       g.dist[base + t] = key[v];
+    }
+  }
+}
+
+// One warp per cell of at most kSortTinyMax particles (a clustered box has
+// tens of thousands of them, which k_cell_sort's one CTA per cell handles
+// poorly): the same gather into cell order and H_max, then the 13 axes in
+// turn with the same warp bucket sort, from a per-warp copy of the keys.
+__global__ void __launch_bounds__(kSortTinyWarps * 32) k_cell_sort_tiny(
+    GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
+    const float* __restrict__ m, float m_uniform) {
+  constexpr int kPer = kSortTinyMax / 32;
+  __shared__ float4 s_x[kSortTinyWarps][kSortTinyMax];
+  __shared__ float s_key[kSortTinyWarps][kSortTinyMax];
+  __shared__ int s_orig[kSortTinyWarps][kSortTinyMax];
+  __shared__ uint16_t s_tmp[kSortTinyWarps][kSortTinyMax];
+  __shared__ uint16_t s_out[kSortTinyWarps][kSortTinyMax];
+  __shared__ int s_bkt[kSortTinyWarps][kSortTinyMax + 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* wx = s_x[warp];
+  float* key = s_key[warp];
+  int* orig = s_orig[warp];
+  for (int c = blockIdx.x * kSortTinyWarps + warp; c < g.ncell;
+       c += gridDim.x * kSortTinyWarps) {
+    const int cnt = g.cell_count[c];
+    if (cnt > kSortTinyMax) continue;
+    const int cs = g.cell_start[c];
+    const int bx = g.cell_box[c];
+    const BoxDev& B = g.boxes[bx];
+    const int loc = c - B.cell_base;
+    const double ctr[3] = {-((loc / (B.nc * B.nc)) + 0.5), -(((loc / B.nc) % B.nc) + 0.5),
+                           -((loc % B.nc) + 0.5)};
+    const float mmax = g.m_max[bx];
+    float hmax = 0.0f;
+    for (int t = lane; t < cnt; t += 32) {
+      const int p = g.orig[cs + t];
+      const size_t s = (size_t)cs + t;
+      float off[3];
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        double x = pos[3 * (size_t)p + k];
+        if (!finite_bits(x)) x = 0.0;
+        if (!in_box_bits(x, B.L)) x = wrap_coord(x, B.L);
+        off[k] = (float)fma(ctr[k], B.edge, x);
+        g.pos64[3 * s + k] = x;
+      }
+      const float mv = m ? m[p] : m_uniform;
+      const float hv = h[p];
+      const float4 xm = make_float4(off[0], off[1], off[2], mmax > 0.0f ? mv / mmax : 0.0f);
+      g.xm[s] = xm;
+      g.xm_ref[s] = xm;
+      g.hs[s] = hv;
+      if (valid_h_m(hv, mv)) hmax = fmaxf(hmax, g.gamma * hv);
+      wx[t] = xm;
+      orig[t] = p;
+    }
+    for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    if (lane == 0) g.cell_Hmax[c] = hmax;
+    if (cnt == 0) continue;
+    __syncwarp();
+    int nb = 32;
+    while (nb < cnt) nb <<= 1;
+    for (int k = 0; k < kNDir; k++) {
+      float ux, uy, uz;
+      axis_u(k, ux, uy, uz);
+      float kr[kPer];
+      float kmin = 3.0e38f, kmax = -3.0e38f;
+#pragma unroll
+      for (int j = 0; j < kPer; j++) {
+        const int t = lane + 32 * j;
+        kr[j] = 0.0f;
+        if (t < cnt) {
+          const float d = project(wx[t], ux, uy, uz);
+          key[t] = d;
+          kr[j] = d;
+          kmin = fminf(kmin, d);
+          kmax = fmaxf(kmax, d);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+      }
+      __syncwarp();
+      warp_sort_axis<kPer>(cnt, kr, key, orig, s_tmp[warp], s_out[warp], s_bkt[warp], nb, lane,
+                           kmin, kmax);
+      const size_t base = (size_t)k * g.n + cs;
+#pragma unroll
+      for (int j = 0; j < kPer; j++) {
+        const int t = lane + 32 * j;
+        if (t < cnt) {
+          const int v = s_out[warp][t];
+          g.perm[base + t] = (uint16_t)v;
+          g.dist[base + t] = key[v];
+        }
+      }
+      __syncwarp();  // key is rewritten by the next axis
     }
   }
 }
@@ -579,6 +684,9 @@ cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, con
       smem_done, reinterpret_cast<const void*>(&k_cell_sort<kSortSmallMax>), smem);
   if (e != cudaSuccess) return e;
   k_cell_sort<kSortSmallMax><<<g.ncell, kSortThreads, smem, st>>>(g, pos, h, m, m_uniform);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_cell_sort_tiny<<<(g.ncell + kSortTinyWarps - 1) / kSortTinyWarps, kSortTinyWarps * 32, 0,
+                     st>>>(g, pos, h, m, m_uniform);
   if ((e = cudaGetLastError()) != cudaSuccess || g.n == 0) return e;
   k_sort_big<<<512, kSortBigThreads, 0, st>>>(g);
   return cudaGetLastError();
