@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
 
 // ---- task kernel (cells too dense for the cell-centric kernel) ----------------------
 
-__global__ void __launch_bounds__(kBlkI, 4) k_backward_tasks(GridDev g) {
+__global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
   __shared__ float4 s_x[kTileJ + kPad];
   __shared__ float4 s_a[kTileJ + kPad];
   __shared__ float s_d[kTileJ];

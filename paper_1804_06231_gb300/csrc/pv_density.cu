@@ -38,7 +38,7 @@ namespace pv {
 namespace {
 
 constexpr int kBlkI = 128;       // particles of a per task (task path)
-constexpr int kTileJ = 1024;     // particles of b per tile (task path)
+constexpr int kTileJ = 512;      // particles of b per tile (task path)
 constexpr int kCellThreads = 256;
 // dynamic shared memory of k_density_cells for 1..4 resident CTAs per SM (the
 // SM's 228 KB less 1 KB reserved and the static part per CTA); 3 by default
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
 
 // ---- task kernel (cells too dense for the cell-centric kernel) ---------------------
 
-__global__ void __launch_bounds__(kBlkI) k_density_tasks(GridDev g) {
+__global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
   __shared__ float4 s_x[kTileJ + kPad];
   __shared__ float s_m[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
