@@ -273,7 +273,7 @@ pv_status pv_sort_cells(pv_grid* g, const double* pos, const float* h, const flo
   PV_CUDA(pv::launch_scatter(d, st));
   PV_CUDA(pv::launch_sort(d, pos, h, m, m_uniform, st));
   d.moved = 0;
-  g->launches += g->n > 0 ? 7 : 4;  // clear, bin, scan, scatter, cell sorts (x2), big-cell sort
+  g->launches += g->n > 0 ? 8 : 4;  // clear, bin, scan, scatter, cell sorts (x2), big-cell sorts (x2)
   g->sorted = true;
   return PV_OK;
 }

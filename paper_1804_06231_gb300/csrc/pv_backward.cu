@@ -587,7 +587,7 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
   k_backward_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_bwd_finalize_t<<<num_sms * 2, 256, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
+  k_bwd_finalize_t<<<num_sms * 8, 256, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
   return cudaGetLastError();
 }
 

@@ -216,9 +216,25 @@ __global__ void k_plan_tasks(GridDev g, int wide) {
       const int p0 = bk * kBlkI, p1 = min(nI, p0 + kBlkI);
       int j0, j1;
       if (o == kSelfSlot) {
+        // upper bound of d[p0] - reach and lower bound of d[p1 - 1] + reach,
+        // in lockstep so that the two searches' loads are in flight together
         const float* d = g.dist + cb;  // axis 0, ascending
-        j0 = upper_bound_f(d, nb, d[p0] - reach);
-        j1 = lower_bound_f(d, nb, d[p1 - 1] + reach);
+        const float x0 = d[p0] - reach, x1 = d[p1 - 1] + reach;
+        int lo0 = 0, hi0 = nb, lo1 = 0, hi1 = nb;
+        while (lo0 < hi0 || lo1 < hi1) {
+          const int m0 = (lo0 + hi0) >> 1, m1 = (lo1 + hi1) >> 1;
+          const bool s0 = lo0 < hi0, s1 = lo1 < hi1;
+          const float v0 = s0 ? d[m0] : 0.0f;
+          const float v1 = s1 ? d[m1] : 0.0f;
+          if (s0) {
+            if (v0 <= x0) lo0 = m0 + 1; else hi0 = m0;
+          }
+          if (s1) {
+            if (v1 < x1) lo1 = m1 + 1; else hi1 = m1;
+          }
+        }
+        j0 = lo0;
+        j1 = lo1;
       } else {
         const float dmax = proj_asc(g, sl.k, sl.s, ca, na, na - 1 - p0, 0.0f);
         j0 = 0;
@@ -863,7 +879,9 @@ cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j,
   if (e != cudaSuccess) return e;
   k_plan_cells<<<(g.ncell + 127) / 128, 128, 0, st>>>(g, smem_budget, elem_j, elem_a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_plan_tasks<<<512, 256, 0, st>>>(g, wide);
+  // one warp per (task cell, slot): enough warps that the big cells' many
+  // (cell, slot) pairs do not queue behind each other
+  k_plan_tasks<<<2048, 256, 0, st>>>(g, wide);
   return cudaGetLastError();
 }
 
@@ -890,7 +908,7 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
   k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_finalize_t<<<num_sms * 2, 256, 0, st>>>(g, rho, drho_dh, n_ngb);
+  k_finalize_t<<<num_sms * 8, 256, 0, st>>>(g, rho, drho_dh, n_ngb);
   return cudaGetLastError();
 }
 

@@ -552,25 +552,37 @@ __global__ void __launch_bounds__(kSortTinyWarps * 32) k_cell_sort_tiny(
 }
 
 // One CTA per (cell of more than kSortSmallMax particles, axis), the same
-// bucket sort with the buckets in shared memory.  It needs no scratch beyond
-// the axis's own outputs: the bucket-grouped indices go into dist[k] (as int
-// bits) until the exact ranks have been written to perm[k], then dist[k]
-// receives the keys, which are recomputed from xm wherever they are needed
-// (the same FP32 expression each time, so the same values).
+// bucket sort with the buckets in shared memory.  For a cell of at most
+// kSortBigSmem particles the keys, caller indices and bucket-grouped indices
+// are staged in shared memory too (keys computed once); larger cells need no
+// scratch beyond the axis's own outputs: the bucket-grouped indices go into
+// dist[k] (as int bits) until the exact ranks have been written to perm[k],
+// then dist[k] receives the keys, which are recomputed from xm wherever they
+// are needed (the same FP32 expression each time, so the same values).
 constexpr int kSortBigThreads = 1024;
 constexpr int kSortBigBuckets = 8192;
+constexpr int kSortBigSmem = 6144;
+constexpr size_t kSortBigDynSmem =
+    (size_t)kSortBigSmem * (sizeof(float) + sizeof(int) + sizeof(uint16_t));
 
-__global__ void __launch_bounds__(kSortBigThreads) k_sort_big(GridDev g) {
+template <bool kStaged>
+__global__ void __launch_bounds__(kSortBigThreads, kStaged ? 2 : 1) k_sort_big(GridDev g) {
   __shared__ int s_bkt[kSortBigBuckets + kSortBigThreads];  // bucket b at bucket_slot(b, sh)
   __shared__ float s_red[2][32];
   __shared__ int s_scan[32];
+  extern __shared__ float s_key[];                                  // [kSortBigSmem]
+  int* s_org = reinterpret_cast<int*>(s_key + kSortBigSmem);        // [kSortBigSmem]
+  uint16_t* s_grp = reinterpret_cast<uint16_t*>(s_org + kSortBigSmem);  // [kSortBigSmem]
   if (*g.flags) return;
   const int nbig = *g.n_big;
   const int tid = threadIdx.x, nthr = blockDim.x;
   for (int idx = blockIdx.x; idx < nbig * kNDir; idx += gridDim.x) {
     const int c = g.big_cells[idx / kNDir], k = idx % kNDir;
     const int cnt = min(g.cell_count[c], PV_MAX_CELL_COUNT);
+    // cells of at most kSortBigSmem particles go to the staged instance
+    if ((cnt <= kSortBigSmem) != kStaged) continue;
     const int cs = g.cell_start[c];
+    constexpr bool staged = kStaged;
     int B = kSortBigThreads;
     while (B < cnt && B < kSortBigBuckets) B <<= 1;
     float ux, uy, uz;
@@ -580,9 +592,15 @@ __global__ void __launch_bounds__(kSortBigThreads) k_sort_big(GridDev g) {
     const size_t base = (size_t)k * g.n + cs;
     int* tmp = reinterpret_cast<int*>(g.dist + base);
     uint16_t* out = g.perm + base;
+    auto key_of = [&](int t) { return staged ? s_key[t] : project(X[t], ux, uy, uz); };
+    auto org_of = [&](int t) { return staged ? s_org[t] : O[t]; };
     float kmin = 3.0e38f, kmax = -3.0e38f;
     for (int t = tid; t < cnt; t += nthr) {
       const float d = project(X[t], ux, uy, uz);
+      if (staged) {
+        s_key[t] = d;
+        s_org[t] = O[t];
+      }
       kmin = fminf(kmin, d);
       kmax = fmaxf(kmax, d);
     }
@@ -606,7 +624,7 @@ __global__ void __launch_bounds__(kSortBigThreads) k_sort_big(GridDev g) {
     const float scale = kmax > kmin ? (float)B / (kmax - kmin) : 0.0f;
     auto bucket_of = [&](float d) { return min(B - 1, max(0, (int)((d - kmin) * scale))); };
     for (int t = tid; t < cnt; t += nthr)
-      atomicAdd(&s_bkt[bucket_slot(bucket_of(project(X[t], ux, uy, uz)), sh)], 1);
+      atomicAdd(&s_bkt[bucket_slot(bucket_of(key_of(t)), sh)], 1);
     __syncthreads();
     // exclusive scan: each thread owns B / nthr consecutive buckets
     const int p0 = bucket_slot(tid * per, sh);
@@ -619,24 +637,26 @@ __global__ void __launch_bounds__(kSortBigThreads) k_sort_big(GridDev g) {
       run += v;
     }
     __syncthreads();
-    for (int t = tid; t < cnt; t += nthr)
-      tmp[atomicAdd(&s_bkt[bucket_slot(bucket_of(project(X[t], ux, uy, uz)), sh)], 1)] = t;
+    for (int t = tid; t < cnt; t += nthr) {
+      const int at = atomicAdd(&s_bkt[bucket_slot(bucket_of(key_of(t)), sh)], 1);
+      if (staged) s_grp[at] = (uint16_t)t; else tmp[at] = t;
+    }
     __syncthreads();
     // s_bkt[b] is now the end of bucket b; rank each particle inside its bucket
     for (int t = tid; t < cnt; t += nthr) {
-      const float kt = project(X[t], ux, uy, uz);
+      const float kt = key_of(t);
       const int b = bucket_of(kt);
       const int s0 = b ? s_bkt[bucket_slot(b - 1, sh)] : 0, s1 = s_bkt[bucket_slot(b, sh)];
-      const int ot = O[t];
+      const int ot = org_of(t);
       int r = 0;
       for (int u = s0; u < s1; u++) {
-        const int v = tmp[u];
-        r += key_less(project(X[v], ux, uy, uz), O[v], kt, ot) ? 1 : 0;
+        const int v = staged ? (int)s_grp[u] : tmp[u];
+        r += key_less(key_of(v), org_of(v), kt, ot) ? 1 : 0;
       }
       out[s0 + r] = (uint16_t)t;
     }
     __syncthreads();
-    for (int t = tid; t < cnt; t += nthr) g.dist[base + t] = project(X[out[t]], ux, uy, uz);
+    for (int t = tid; t < cnt; t += nthr) g.dist[base + t] = key_of(out[t]);
     __syncthreads();
   }
 }
@@ -688,7 +708,13 @@ cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, con
   k_cell_sort_tiny<<<(g.ncell + kSortTinyWarps - 1) / kSortTinyWarps, kSortTinyWarps * 32, 0,
                      st>>>(g, pos, h, m, m_uniform);
   if ((e = cudaGetLastError()) != cudaSuccess || g.n == 0) return e;
-  k_sort_big<<<512, kSortBigThreads, 0, st>>>(g);
+  static std::atomic<unsigned long long> big_done{0};
+  if ((e = set_max_dynamic_smem(big_done, reinterpret_cast<const void*>(&k_sort_big<true>),
+                                (int)kSortBigDynSmem)) != cudaSuccess)
+    return e;
+  k_sort_big<true><<<512, kSortBigThreads, kSortBigDynSmem, st>>>(g);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_sort_big<false><<<512, kSortBigThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 
