@@ -462,6 +462,7 @@ __global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
   if (*g.flags) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ntask = *g.ntask;
+  if (ntask == 0) return;  // no task cells: leave without touching the task counter
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(g.task_next, 1);
     __syncthreads();
