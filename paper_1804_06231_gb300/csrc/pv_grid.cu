@@ -712,9 +712,15 @@ cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, con
   if ((e = set_max_dynamic_smem(big_done, reinterpret_cast<const void*>(&k_sort_big<true>),
                                 (int)kSortBigDynSmem)) != cudaSuccess)
     return e;
-  k_sort_big<true><<<512, kSortBigThreads, kSortBigDynSmem, st>>>(g);
+  // persistent grids over (big cell, axis): two CTAs per SM for the staged
+  // instance, one for the rare cells above kSortBigSmem
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  k_sort_big<true><<<2 * sms, kSortBigThreads, kSortBigDynSmem, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_sort_big<false><<<512, kSortBigThreads, 0, st>>>(g);
+  k_sort_big<false><<<sms, kSortBigThreads, 0, st>>>(g);
   return cudaGetLastError();
 }
 
