@@ -57,6 +57,8 @@ def _load():
         lib.or_backward_brute.argtypes = [i64, p, p, p, d, d, p, p, p, p, i32]
         lib.or_backward_cells.restype = i32
         lib.or_backward_cells.argtypes = [i64, p, p, p, d, i32, d, p, p, p, p, i32]
+        lib.or_backward_pv.restype = i32
+        lib.or_backward_pv.argtypes = [i64, p, p, p, d, i32, d, p, p, p, p, i32]
         lib.or_adjoint_counts.restype = i32
         lib.or_adjoint_counts.argtypes = [i64, p, p, d, i32, d, p, i32]
         lib.or_fd_loss.restype = d
@@ -200,6 +202,21 @@ def backward_cells(pos, h, m, g_rho, g_D, L=1.0, nc=3, gamma=GAMMA_DEFAULT, thre
                                    int(threads))
     if rc:
         raise ValueError(f"oracle backward_cells: {_ERR.get(rc, rc)}")
+    return gp, gh
+
+
+def backward_pv(pos, h, m, g_rho, g_D, L=1.0, nc=3, gamma=GAMMA_DEFAULT, threads=0):
+    """Adjoint by the pseudo-Verlet sweep (windows widened to max(H_i, Hmax_b)):
+    returns (dL/dx [n,3], dL/dh [n]); equal to backward_cells up to summation
+    order, and fast on dense clustered cells."""
+    pos = _f64(pos, (-1, 3)); n = pos.shape[0]
+    h = _f64(h); m = _f64(m); g_rho = _f64(g_rho); g_D = _f64(g_D)
+    gp = np.zeros((n, 3)); gh = np.zeros(n)
+    rc = _load().or_backward_pv(n, _ptr(pos), _ptr(h), _ptr(m), float(L), int(nc),
+                                float(gamma), _ptr(g_rho), _ptr(g_D), _ptr(gp), _ptr(gh),
+                                int(threads))
+    if rc:
+        raise ValueError(f"oracle backward_pv: {_ERR.get(rc, rc)}")
     return gp, gh
 
 

@@ -38,7 +38,10 @@
  *                        visited (the "first_a" trimming of Section 3.3).
  *
  * The adjoint of the density loop (not in the paper; it maps dL/drho and
- * dL/d(drho/dh) to dL/dx and dL/dh) is or_backward_cells.
+ * dL/d(drho/dh) to dL/dx and dL/dh) comes by three routes as well:
+ * or_backward_brute (definition), or_backward_cells (cell list) and
+ * or_backward_pv (the pseudo-Verlet sweep with every reach widened to
+ * max(H_i, Hmax_b), which the transposed term r < H_j needs).
  *
  * Readings of the paper that this file takes (the paper is silent on them):
  *   - the paper's cut-off "h" is the support H here; cells have edge >= H_max;
@@ -598,6 +601,98 @@ int or_backward_cells(int64_t n, const double* pos, const double* h, const doubl
       g_h[i] = acc.gh;
     }
   }
+  grid_free(&g);
+  return 0;
+}
+
+/* The adjoint by the pseudo-Verlet sweep of the density (Section 2 second  */
+/* listing, Section 3.3 trimming), with every reach widened to cover the    */
+/* transposed term: a pair (i, j) contributes while r < max(H_i, H_j), and  */
+/* its projected separation is at most r, so particle i of cell a sweeps    */
+/* the sorted list of b up to max(H_i, Hmax_b) beyond d_i, and a is trimmed */
+/* with max(Hmax_a, Hmax_b).  Each candidate is then decided exactly by     */
+/* adj_pair (r < H_i own, r < H_j transposed).  Same result as the cell      */
+/* list up to summation order, at the cost of the sweep's candidates.        */
+int or_backward_pv(int64_t n, const double* pos, const double* h, const double* m, double L,
+                   int nc, double gamma, const double* g_rho, const double* g_D,
+                   double* g_pos, double* g_h, int nthreads) {
+  if (nc < 3) return -2;
+  set_threads(nthreads);
+  or_grid g;
+  if (grid_build(&g, n, pos, h, L, nc, gamma, 1)) return -1;
+  for (int64_t c = 0; c < g.ncell; c++)
+    if (g.Hmax[c] > g.edge) { grid_free(&g); return -3; }
+  or_gacc* acc = calloc((size_t)(n > 0 ? n : 1), sizeof(or_gacc)); /* by cell-order slot */
+  if (!acc) { grid_free(&g); return -1; }
+
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t a = 0; a < g.ncell; a++) {
+    int ca[3];
+    cell_coords(&g, a, ca);
+    const int64_t a0 = g.start[a], na = g.start[a + 1] - a0;
+    if (na == 0) continue;
+    /* one candidate pair: cell-order slots si (cell a) and sj (cell a + o) */
+#define ADJ(si_, sj_, o_)                                                             \
+    do {                                                                              \
+      const int64_t i_ = g.member[si_], j_ = g.member[sj_];                           \
+      double d_[3], r2_ = 0.0;                                                        \
+      for (int c_ = 0; c_ < 3; c_++) {                                                \
+        d_[c_] = g.off[3 * (si_) + c_] - g.off[3 * (sj_) + c_] - (o_)[c_] * g.edge;   \
+        r2_ += d_[c_] * d_[c_];                                                       \
+      }                                                                               \
+      adj_pair(&acc[si_], d_, sqrt(r2_), i_ == j_, h[i_], h[j_], m[i_], m[j_],        \
+               g_rho[i_], g_D[i_], g_rho[j_], g_D[j_], gamma);                        \
+    } while (0)
+
+    /* self: two-sided window on the sorted axis (0,0,1), reach max(H_i, Hmax_a) */
+    {
+      const double* dd = g.dist[0] + a0;
+      const int64_t* ss = g.sidx[0] + a0;
+      const int o[3] = {0, 0, 0};
+      for (int64_t t = 0; t < na; t++) {
+        const int64_t si = ss[t];
+        const double R = fmax(gamma * h[g.member[si]], g.Hmax[a]);
+        for (int64_t u = t; u >= 0 && dd[u] > dd[t] - R; u--) ADJ(si, ss[u], o);
+        for (int64_t u = t + 1; u < na && dd[u] < dd[t] + R; u++) ADJ(si, ss[u], o);
+      }
+    }
+    /* pairs: b = a + s v_k, projections as in or_density_pv */
+    for (int k = 0; k < OR_NDIR; k++) {
+      const int v2 = OR_V[k][0] * OR_V[k][0] + OR_V[k][1] * OR_V[k][1] + OR_V[k][2] * OR_V[k][2];
+      const double shift = sqrt((double)v2) * g.edge;
+      for (int s = 1; s >= -1; s -= 2) {
+        const int o[3] = {s * OR_V[k][0], s * OR_V[k][1], s * OR_V[k][2]};
+        const int64_t b = cell_id(&g, ca[0] + o[0], ca[1] + o[1], ca[2] + o[2]);
+        const int64_t b0 = g.start[b], nb = g.start[b + 1] - b0;
+        if (nb == 0) continue;
+#define A_POS(t) (s > 0 ? a0 + (t) : a0 + na - 1 - (t))
+#define B_POS(t) (s > 0 ? b0 + (t) : b0 + nb - 1 - (t))
+        const double db_first = s * g.dist[k][B_POS(0)] + shift;
+        const double reach_ab = fmax(g.Hmax[a], g.Hmax[b]);
+        int64_t first_a = na;
+        while (first_a > 0 && s * g.dist[k][A_POS(first_a - 1)] + reach_ab > db_first) first_a--;
+        for (int64_t t = first_a; t < na; t++) {
+          const int64_t si = g.sidx[k][A_POS(t)];
+          const double R = fmax(gamma * h[g.member[si]], g.Hmax[b]);
+          const double di = s * g.dist[k][A_POS(t)];
+          for (int64_t u = 0; u < nb; u++) {
+            const double dj = s * g.dist[k][B_POS(u)] + shift;
+            if (!(dj < di + R)) break;
+            ADJ(si, g.sidx[k][B_POS(u)], o);
+          }
+        }
+#undef A_POS
+#undef B_POS
+      }
+    }
+#undef ADJ
+  }
+  for (int64_t sl = 0; sl < n; sl++) {
+    const int64_t i = g.member[sl];
+    g_pos[3 * i] = acc[sl].gx; g_pos[3 * i + 1] = acc[sl].gy; g_pos[3 * i + 2] = acc[sl].gz;
+    g_h[i] = acc[sl].gh;
+  }
+  free(acc);
   grid_free(&g);
   return 0;
 }

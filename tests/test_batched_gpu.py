@@ -17,7 +17,7 @@ def _lib():
     build.build_library()
 
 
-def _run(boxes, g_seed=7):
+def _run(boxes, g_seed=7, launch_shape=None):
     """sort + density + backward of `boxes` in ONE grid; returns numpy outputs."""
     import torch
     from paper_1804_06231_gb300.pv import Grid
@@ -30,6 +30,8 @@ def _run(boxes, g_seed=7):
     gr = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
     gd = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
     with Grid([(b.n, b.L, b.nc) for b in boxes]) as g:
+        if launch_shape:
+            g.set_tuning(*launch_shape)
         g.sort(pos, h, m)
         rho, D, nn = g.density()
         gp, gh = g.backward(gr, gd)
@@ -74,6 +76,37 @@ def test_batched_vs_oracle(oracle_lib):
         ok = ref.band == 0
         assert np.array_equal(n[sl][ok], ref.n_ngb[ok])
         first += b.n
+
+
+@pytest.mark.slow
+def test_multibox_64_full_size_vs_oracle(oracle_lib):
+    """The whole 64-box mix (9,314,318 particles, N per box log-uniform in
+    [4096, 524288], uniform or clustered) in one grid at the benchmark's
+    launch shape (4 / 3 CTAs per SM): the density of every particle of every
+    box against the oracle's pseudo-Verlet sweep, and the adjoint of six
+    boxes (the three largest of each kind) against the oracle's pseudo-Verlet
+    adjoint."""
+    boxes = I.multibox()
+    (rho, D, n, gp, gh), gr, gd = _run(boxes, launch_shape=(4, 3))
+    firsts = np.concatenate([[0], np.cumsum([b.n for b in boxes])])
+    for b, f in zip(boxes, firsts):
+        sl = slice(f, f + b.n)
+        ref = oracle_lib.density_pv(b.pos, b.h, b.m, b.L, b.nc)
+        assert np.abs(rho[sl] / ref.rho - 1).max() <= 1e-5, b.name
+        assert np.all(np.abs(D[sl] - ref.drho_dh) <= 1e-4 * ref.S), b.name
+        ok = ref.band == 0
+        assert np.array_equal(n[sl][ok], ref.n_ngb[ok]), b.name
+        assert np.all(np.abs(n[sl][~ok] - ref.n_ngb[~ok]) <= ref.band[~ok]), b.name
+    rel = lambda a, c: np.linalg.norm(a - c) / np.linalg.norm(c)
+    for kind in ("uniform", "clustered"):
+        picks = sorted((i for i, b in enumerate(boxes) if kind in b.name),
+                       key=lambda i: -boxes[i].n)[:3]
+        for i in picks:
+            b, sl = boxes[i], slice(firsts[i], firsts[i] + boxes[i].n)
+            gp0, gh0 = oracle_lib.backward_pv(b.pos, b.h, b.m, gr[sl].astype(np.float64),
+                                              gd[sl].astype(np.float64), b.L, b.nc)
+            assert rel(gp[sl].astype(np.float64), gp0) <= 1e-4, b.name
+            assert rel(gh[sl].astype(np.float64), gh0) <= 1e-4, b.name
 
 
 def test_cuda_graph_replay_matches_eager():

@@ -301,6 +301,26 @@ def test_adjoint_brute_equals_cells(oracle_lib):
     np.testing.assert_allclose(gh1, gh0, rtol=0, atol=1e-12 * np.abs(gh0).max())
 
 
+@pytest.mark.parametrize("kind", ["uniform", "clustered", "test27cells"])
+def test_adjoint_pv_sweep_equals_cells_and_brute(oracle_lib, kind):
+    """The pseudo-Verlet adjoint (sorted windows widened to max(H_i, Hmax_b))
+    reaches every pair with r < max(H_i, H_j): equal to the cell-list adjoint
+    and to the O(N^2) definition up to summation order."""
+    O = oracle_lib
+    b = {"uniform": lambda: I.uniform(3000, 23, nc=None),
+         "clustered": lambda: I.clustered(5000, 24),
+         "test27cells": lambda: I.test27cells()}[kind]()
+    w, v = I.loss_weights(b.n, 23)
+    d = O.density_cells(b.pos, b.h, b.m, b.L, b.nc)
+    g, k = O.loss_upstream(d.rho, w, v)
+    gp0, gh0 = O.backward_brute(b.pos, b.h, b.m, g, k, b.L)
+    gp1, gh1 = O.backward_pv(b.pos, b.h, b.m, g, k, b.L, b.nc)
+    gp2, gh2 = O.backward_cells(b.pos, b.h, b.m, g, k, b.L, b.nc)
+    for gp, gh in ((gp1, gh1), (gp2, gh2)):
+        np.testing.assert_allclose(gp, gp0, rtol=0, atol=1e-12 * np.abs(gp0).max())
+        np.testing.assert_allclose(gh, gh0, rtol=0, atol=1e-12 * np.abs(gh0).max())
+
+
 @pytest.mark.parametrize("kind", ["uniform", "clustered"])
 def test_adjoint_matches_finite_differences(oracle_lib, kind):
     """dL/dx and dL/dh of L = sum w (rho-1)^2 + sum v drho/dh, central FD step 1e-6."""
