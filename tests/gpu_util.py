@@ -13,8 +13,10 @@ def torch_dev():
     return torch.device("cuda", 0)
 
 
-def run_density(boxes, uniform_mass=False, count_candidates=False, expect_flags=False):
-    """Runs sort + density on one or more Box objects (concatenated)."""
+def run_density(boxes, uniform_mass=False, count_candidates=False, expect_flags=False,
+                launch_shape=None):
+    """Runs sort + density on one or more Box objects (concatenated);
+    launch_shape = (density, adjoint) CTAs per SM, or None for the default."""
     import torch
     from paper_1804_06231_gb300.pv import Grid
     if not isinstance(boxes, (list, tuple)):
@@ -24,6 +26,8 @@ def run_density(boxes, uniform_mass=False, count_candidates=False, expect_flags=
     h = torch.from_numpy(np.concatenate([b.h for b in boxes])).to(dev)
     m = torch.from_numpy(np.concatenate([b.m for b in boxes])).to(dev)
     with Grid([(b.n, b.L, b.nc) for b in boxes]) as g:
+        if launch_shape:
+            g.set_tuning(*launch_shape)
         if uniform_mass:
             g.sort(pos, h, None, m_uniform=float(boxes[0].m[0]))
         else:

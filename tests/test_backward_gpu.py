@@ -122,7 +122,7 @@ def test_adjoint_1m_every_particle(oracle_lib):
     w, v = I.loss_weights(box.n, 3)
     ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
     g, k = oracle_lib.loss_upstream(ref.rho, w, v)
-    gp, gh = gpu_adjoint(box, g, k, uniform_mass=True)
+    gp, gh = gpu_adjoint(box, g, k, uniform_mass=True, launch_shape=(4, 3))
     gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g, k, 1.0, box.nc)
     assert rel_l2(gp, gp0) <= ADJ_RTOL
     assert rel_l2(gh, gh0) <= ADJ_RTOL

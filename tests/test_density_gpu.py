@@ -155,11 +155,12 @@ def test_adjoint_counts_match_oracle(oracle_lib):
 
 
 @pytest.mark.slow
-def test_uniform_1m_headline_sampled(oracle_lib):
-    """N = 1,048,576 at 15^3 cells (the benchmark's launch configuration): all
-    particles against the oracle's pseudo-Verlet sweep."""
+def test_uniform_1m_every_particle(oracle_lib):
+    """N = 1,048,576 at 15^3 cells, at the launch shape the benchmark tunes to
+    (4 / 3 CTAs per SM): all particles against the oracle's pseudo-Verlet
+    sweep."""
     box = I.cfg1()
-    rho, D, n, st, _ = run_density(box, uniform_mass=True)
+    rho, D, n, st, _ = run_density(box, uniform_mass=True, launch_shape=(4, 3))
     ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
     check_density(rho, D, n, ref)
     assert st.interactions == int(ref.n_ngb.sum()) or \
@@ -269,7 +270,7 @@ def test_clustered_4m_every_particle(oracle_lib):
     the per-axis sort of dense cells): every particle against the oracle's
     pseudo-Verlet sweep."""
     box = I.cfg2()
-    rho, D, n, st, _ = run_density(box, uniform_mass=True)
+    rho, D, n, st, _ = run_density(box, uniform_mass=True, launch_shape=(4, 3))
     ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
     check_density(rho, D, n, ref)
     assert abs(st.interactions - int(ref.n_ngb.sum())) <= int(ref.band.sum())
