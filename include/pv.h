@@ -183,7 +183,8 @@ pv_status pv_grid_stats(pv_grid* g, pv_stats* out);
    resident CTAs per SM sets each kernel's shared memory, and with it which
    cells are swept by the cell-centric kernel (their 27 windows fit) and which
    by the task kernel: fewer CTAs = more shared memory per cell, more CTAs =
-   more warps to hide latency.  0 selects the default. */
+   more warps to hide latency.  (Cells of at most 32 particles always go to
+   a warp-per-cell kernel.)  0 selects the default. */
 typedef struct {
   int32_t density_ctas_per_sm;   /* 1..4 (default 3) */
   int32_t backward_ctas_per_sm;  /* 1..3 (default 3) */

@@ -450,6 +450,64 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
   }
 }
 
+// ---- warp-per-cell kernel (cells of at most kTinyCell particles) -------------------
+// As the forward's: one warp per tiny cell a, lane l its particle ca + l; the
+// 27 windows of the (widened) plan staged one after the other with each
+// neighbour's records shifted into a's frame, and one adjoint sweep over all
+// of them.  The lane keeps its five sums in registers and writes its outputs.
+constexpr int kTinyWarpsB = 4;
+constexpr int kTinyBufB = 128;  // staged candidates per warp and pass
+
+__global__ void __launch_bounds__(kTinyWarpsB * 32, 6) k_backward_tiny(
+    GridDev g, const float* __restrict__ g_rho, const float* __restrict__ g_D,
+    float* __restrict__ g_pos, float* __restrict__ g_h) {
+  __shared__ float4 s_x[kTinyWarpsB][kTinyBufB + kPad];
+  __shared__ float4 s_a[kTinyWarpsB][kTinyBufB + kPad];
+  __shared__ int s_j[kTinyWarpsB][kTinyBufB + kPad];
+  __shared__ unsigned s_mask[kTinyWarpsB][kMaskChunks * 32];
+  __shared__ TinySlots s_slots[kTinyWarpsB];
+  if (*g.flags) return;
+  const int nt = *g.n_ycells;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* Sx = s_x[warp];
+  float4* Sa = s_a[warp];
+  int* Sj = s_j[warp];
+  TinySlots& ts = s_slots[warp];
+  const Slot self = slot_info(kSelfSlot);
+  const float munit = (float)(16.0 / 3.14159265358979323846);
+  for (int w = blockIdx.x * kTinyWarpsB + warp; w < nt; w += gridDim.x * kTinyWarpsB) {
+    const int a = g.ycells[w];
+    const int na = g.cell_count[a], ca = g.cell_start[a];
+    const BoxDev& B = g.boxes[g.cell_box[a]];
+    const float edge = B.edge_f;
+    const int total = tiny_slots(g, a, lane, ts);
+    LaneB L;
+    laneb_init(L);
+    if (lane < na) laneb_set(L, g, B, self, ca + lane);
+    int q = 0;  // slot of this lane's next staged candidate (non-decreasing)
+    for (int f0 = 0; f0 < total; f0 += kTinyBufB) {
+      const int len = min(kTinyBufB, total - f0);
+      for (int e = lane; e < len; e += 32) {
+        const int f = f0 + e;
+        while (ts.off[q + 1] <= f) q++;
+        float sx, sy, sz;
+        const int sj = tiny_candidate(g, ts, q, f, edge, sx, sy, sz);
+        const float4 xe = g.bx[sj];
+        Sx[e] = make_float4(xe.x + sx, xe.y + sy, xe.z + sz, xe.w);
+        Sa[e] = g.ba[sj];
+        Sj[e] = sj;
+      }
+      __syncwarp();
+      auto jidx = [&](int j) { return Sj[j]; };
+      sweep_bwd(L, Sx, Sa, 0, len, s_mask[warp], lane, g, B, jidx);
+      __syncwarp();  // the buffer is restaged by the next pass
+    }
+    if (lane < na)
+      write_bwd(g, ca + lane, (double)L.Sth, (double)L.Suh, (double)L.gx, (double)L.gy,
+                (double)L.gz, g_rho, g_D, g_pos, g_h, munit * g.m_max[g.cell_box[a]]);
+  }
+}
+
 // ---- task kernel (cells too dense for the cell-centric kernel) ----------------------
 
 __global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
@@ -586,6 +644,8 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
                                                                        g_h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
+  k_backward_tiny<<<num_sms * 6, kTinyWarpsB * 32, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_backward_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_bwd_finalize_t<<<num_sms * 8, 256, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);

@@ -127,9 +127,11 @@ __global__ void k_plan_slots(GridDev g, int wide) {
     }
   }
   g.plan[idx] = flagged ? make_int4(0, 0, 0, 0) : pl;
+  if (idx == 0) *g.n_ycells = 0;  // k_plan_cells fills the list of tiny cells
 }
 
-// One thread per cell: route the cell to the cell-centric kernel when its
+// One thread per cell: route a cell of at most kTinyCell particles to the
+// warp-per-cell kernel, any other cell to the cell-centric kernel when its
 // staged windows fit `smem_budget`, else to the task kernel, reserving one
 // task of kBlkI particles per block of each slot (the first task's index goes
 // to plan.w; k_plan_tasks fills the tasks in).  The list appends and the task
@@ -141,11 +143,12 @@ __global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a)
   const int lane = threadIdx.x & 31;
   int na = 0;
   int4* pl = nullptr;
-  bool fits = false;
+  bool fits = false, tiny = false;
   int nblk_tot = 0;  // task blocks of this cell (task-path cells only)
   if (a < g.ncell) {
     na = g.cell_count[a];
-    if (na > 0) {
+    tiny = na > 0 && na <= kTinyCell;
+    if (na > 0 && !tiny) {
       pl = g.plan + (size_t)a * kNSlot;
       int total = 0;
       for (int o = 0; o < kNSlot; o++) total += pl[o].z - pl[o].y;
@@ -154,17 +157,19 @@ __global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a)
         for (int o = 0; o < kNSlot; o++) nblk_tot += (pl[o].x + kBlkI - 1) / kBlkI;
     }
   }
-  const bool task = na > 0 && !fits;
+  const bool task = na > 0 && !tiny && !fits;
   const unsigned below = (1u << lane) - 1u;
   const unsigned mc = __ballot_sync(0xffffffffu, fits), mt = __ballot_sync(0xffffffffu, task);
+  const unsigned my = __ballot_sync(0xffffffffu, tiny);
   int incl = nblk_tot;  // inclusive scan of the task blocks over the warp
 #pragma unroll
   for (int s = 1; s < 32; s <<= 1) {
     const int v = __shfl_up_sync(0xffffffffu, incl, s);
     if (lane >= s) incl += v;
   }
-  int bc = 0, bt = 0, bk = 0;
+  int bc = 0, bt = 0, bk = 0, by = 0;
   if (lane == 31) {
+    if (my) by = atomicAdd(g.n_ycells, __popc(my));
     if (mc) bc = atomicAdd(g.n_ccells, __popc(mc));
     if (mt) bt = atomicAdd(g.n_tcells, __popc(mt));
     if (incl) bk = atomicAdd(g.ntask, incl);
@@ -172,6 +177,8 @@ __global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a)
   bc = __shfl_sync(0xffffffffu, bc, 31);
   bt = __shfl_sync(0xffffffffu, bt, 31);
   bk = __shfl_sync(0xffffffffu, bk, 31);
+  by = __shfl_sync(0xffffffffu, by, 31);
+  if (tiny) g.ycells[by + __popc(my & below)] = a;
   if (fits) g.ccells[bc + __popc(mc & below)] = a;
   if (!task) return;
   g.tcells[bt + __popc(mt & below)] = a;
@@ -594,6 +601,92 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
   }
 }
 
+// ---- warp-per-cell kernel (cells of at most kTinyCell particles) -------------------
+// A clustered box or a small box has tens of thousands of cells with a few
+// particles each; in the cell-centric kernel each of them costs a CTA's
+// staging and barriers plus up to 27 warp items of a few active lanes.  Here
+// one warp takes such a cell a, lane l its particle ca + l.  The 27 trimmed
+// windows of the plan are staged one after the other, each neighbour's
+// particles shifted into a's frame (x_j + o edge: the pair shift of Section
+// 3.2 applied to j instead of i), and swept in one pass: the pre-filter of a
+// lane runs over all staged candidates and the evaluation costs the largest
+// total hit count of a lane instead of a sum of per-slot maxima.  Windows
+// longer than kTinyBuf in total (a tiny cell next to a dense one) are staged
+// in passes.  Each lane keeps its particle's sums in registers across the
+// slots and writes its outputs itself.
+constexpr int kTinyWarps = 4;
+constexpr int kTinyBuf = 256;  // staged candidates per warp and pass
+
+__global__ void __launch_bounds__(kTinyWarps * 32, 6) k_density_tiny(GridDev g,
+                                                                    float* __restrict__ rho,
+                                                                    float* __restrict__ drho_dh,
+                                                                    int32_t* __restrict__ n_ngb) {
+  __shared__ float4 s_x[kTinyWarps][kTinyBuf + kPad];
+  __shared__ float s_m[kTinyWarps][kTinyBuf + kPad];
+  __shared__ int s_j[kTinyWarps][kTinyBuf + kPad];
+  __shared__ unsigned s_mask[kTinyWarps][kMaskChunks * 32];
+  __shared__ TinySlots s_slots[kTinyWarps];
+  if (*g.flags) return;
+  const int nt = *g.n_ycells;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float4* Sx = s_x[warp];
+  float* Sm = s_m[warp];
+  int* Sj = s_j[warp];
+  TinySlots& ts = s_slots[warp];
+  const Slot self = slot_info(kSelfSlot);
+  const float munit = (float)(16.0 / 3.14159265358979323846);
+  unsigned long long inter = 0;
+  int guards = 0;
+  for (int w = blockIdx.x * kTinyWarps + warp; w < nt; w += gridDim.x * kTinyWarps) {
+    const int a = g.ycells[w];
+    const int na = g.cell_count[a], ca = g.cell_start[a];
+    const BoxDev& B = g.boxes[g.cell_box[a]];
+    const float edge = B.edge_f;
+    const int total = tiny_slots(g, a, lane, ts);
+    LaneI L;
+    lane_init(L);
+    if (lane < na) lane_set(L, g, B, self, ca + lane, g.xm[ca + lane], g.hs[ca + lane]);
+    int q = 0;  // slot of this lane's next staged candidate (non-decreasing)
+    for (int f0 = 0; f0 < total; f0 += kTinyBuf) {
+      const int len = min(kTinyBuf, total - f0);
+      for (int e = lane; e < len; e += 32) {
+        const int f = f0 + e;
+        while (ts.off[q + 1] <= f) q++;
+        float sx, sy, sz;
+        const int sj = tiny_candidate(g, ts, q, f, edge, sx, sy, sz);
+        const float4 xj = g.xm[sj];
+        const float x = xj.x + sx, y = xj.y + sy, z = xj.z + sz;
+        Sx[e] = make_float4(x, y, z, fmaf(x, x, fmaf(y, y, z * z)));
+        Sm[e] = xj.w;
+        Sj[e] = sj;
+      }
+      __syncwarp();
+      auto jidx = [&](int j) { return Sj[j]; };
+      sweep_fwd(L, Sx, Sm, 0, len, s_mask[warp], lane, g, B, jidx, guards);
+      __syncwarp();  // the buffer is restaged by the next pass
+    }
+    if (lane < na) {
+      const int s = ca + lane;
+      const int i = g.orig[s];
+      const float h = g.hs[s];
+      const float H = g.gamma * h;
+      const float c = munit * g.m_max[g.cell_box[a]] / (H * H * H);
+      rho[i] = c * L.rho;
+      if (drho_dh) drho_dh[i] = -(c / h) * L.D;
+      if (n_ngb) n_ngb[i] = L.n - 1;  // the self pair j = i
+      inter += (unsigned long long)(L.n - 1);
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) {
+    inter += __shfl_xor_sync(0xffffffffu, inter, s);
+    guards += __shfl_xor_sync(0xffffffffu, guards, s);
+  }
+  if (lane == 0) {
+    if (inter) atomicAdd(&g.counters[0], inter);
+    if (guards) atomicAdd(&g.counters[1], (unsigned long long)guards);
+  }
+}
+
 // ---- task kernel (cells too dense for the cell-centric kernel) ---------------------
 
 __global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
@@ -907,6 +1000,8 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
   k_density_cells<<<num_sms * ctas_per_sm, kCellThreads, smem, st>>>(g, rho, drho_dh, n_ngb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
+  k_density_tiny<<<num_sms * 6, kTinyWarps * 32, 0, st>>>(g, rho, drho_dh, n_ngb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_finalize_t<<<num_sms * 8, 256, 0, st>>>(g, rho, drho_dh, n_ngb);

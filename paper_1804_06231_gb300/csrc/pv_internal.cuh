@@ -31,6 +31,7 @@ namespace pv {
 constexpr int kNDir = 13;   // distinct axes joining neighbouring cell centres
 constexpr int kNSlot = 27;  // neighbour offsets (ox,oy,oz) in {-1,0,1}^3
 constexpr int kSelfSlot = 13;
+constexpr int kTinyCell = 32;  // cells of at most this many particles: one warp, all 27 slots
 constexpr uint32_t kAllSlots = (1u << 27) - 1u;
 constexpr double kFixScale = 68719476736.0;         // fixed-point scale 2^36
 constexpr double kFixInv = 1.0 / 68719476736.0;
@@ -95,6 +96,8 @@ struct GridDev {
   int32_t* ccell_next;
   int32_t* tcells;   // [C] cells expanded into tasks
   int32_t* n_tcells;
+  int32_t* ycells;   // [C] cells of at most kTinyCell particles (one warp each)
+  int32_t* n_ycells;
   // tasks
   int4* tasks;
   int32_t* ntask;
@@ -393,6 +396,56 @@ __device__ __forceinline__ float proj_asc(const GridDev& g, int k, int s, int cs
 // the largest displacement since the last sort.
 __device__ __forceinline__ float window_pad(const GridDev& g, const BoxDev& B, int bx) {
   return B.pad + 2.0f * g.box_disp[bx];
+}
+
+// ---- warp-per-cell kernels (cells of at most kTinyCell particles) ----------
+// Per-warp slot table of the warp-per-cell kernels: the staged range of slot q
+// is [off[q], off[q + 1]); win[q] = {J0, cell start of b, count of b, o}.
+struct TinySlots {
+  int off[kNSlot + 1];
+  int4 win[kNSlot];
+};
+
+// Fills the slot table of cell a from the plan (lane q < 27: slot q); returns
+// the total window length (warp-uniform).
+__device__ __forceinline__ int tiny_slots(const GridDev& g, int a, int lane, TinySlots& ts) {
+  int len = 0;
+  int4 w = make_int4(0, 0, 0, 0);
+  if (lane < kNSlot) {
+    const int4 p = g.plan[(size_t)a * kNSlot + lane];
+    if (p.x > 0) {  // some particle of a reaches b
+      const int b = neighbour_cell(g, a, lane);
+      w = make_int4(p.y, g.cell_start[b], g.cell_count[b], lane);
+      len = p.z - p.y;
+    }
+  }
+  int incl = len;
+#pragma unroll
+  for (int s = 1; s < 32; s <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, s);
+    if (lane >= s) incl += v;
+  }
+  if (lane < kNSlot) {
+    ts.off[lane] = incl - len;
+    ts.win[lane] = w;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (lane == 0) ts.off[kNSlot] = total;
+  __syncwarp();
+  return total;
+}
+
+// Cell-order index of staged candidate f (slot q of the table) and the shift
+// o edge of its cell relative to a.
+__device__ __forceinline__ int tiny_candidate(const GridDev& g, const TinySlots& ts, int q, int f,
+                                              float edge, float& sx, float& sy, float& sz) {
+  const int4 w = ts.win[q];
+  const Slot sl = slot_info(w.w);
+  const int pos = order_pos(sl.s, w.x + f - ts.off[q], w.z);
+  sx = sl.ox * edge;
+  sy = sl.oy * edge;
+  sz = sl.oz * edge;
+  return w.y + (int)g.perm[(size_t)sl.k * g.n + w.y + pos];
 }
 
 // ---- host-side launchers (defined in the .cu files) ------------------------

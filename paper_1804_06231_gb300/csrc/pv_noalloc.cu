@@ -34,7 +34,7 @@ constexpr size_t scratch_bytes(int64_t n, int64_t c) {
   return align_up(sizeof(pv::BoxDev)) + align_up(sizeof(int64_t)) +
          3 * align_up(C * sizeof(int32_t)) + align_up((C + 1) * sizeof(int32_t)) +
          align_up(C * sizeof(float)) +
-         align_up(pv::kNSlot * C * sizeof(int4)) + 2 * align_up(C * sizeof(int32_t)) +  // plan
+         align_up(pv::kNSlot * C * sizeof(int4)) + 3 * align_up(C * sizeof(int32_t)) +  // plan
          2 * align_up(N * sizeof(int32_t)) +          // pcell, prank
          2 * align_up(N * sizeof(float4)) + align_up(N * sizeof(float)) +
          align_up(N * sizeof(int32_t)) + align_up(3 * N * sizeof(double)) +
@@ -137,6 +137,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.plan = carve<int4>(cur, pv::kNSlot * C);
   d.ccells = carve<int32_t>(cur, C);
   d.tcells = carve<int32_t>(cur, C);
+  d.ycells = carve<int32_t>(cur, C);
   d.pcell = carve<int32_t>(cur, N);
   d.prank = carve<int32_t>(cur, N);
   d.xm = carve<float4>(cur, N);
@@ -164,6 +165,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.n_ccells = sc + 6;
   d.ccell_next = sc + 7;
   d.n_tcells = sc + 8;
+  d.n_ycells = sc + 10;
   d.gacc = nullptr;
   d.bx = nullptr;
   d.ba = nullptr;
