@@ -198,6 +198,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   d.ccell_next = sc + 7;
   d.n_tcells = sc + 8;
   d.n_ycells = sc + 10;
+  d.ycell_next = sc + 11;
   unsigned long long* cnt;
   PV_TRY(dev_alloc(g, &cnt, 16));
   d.counters = cnt;
@@ -306,7 +307,7 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
   cudaEvent_t t0, t1;
   PV_TRY(next_pair(g, 0, &t0, &t1));
   PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, g->ctas[0], st, t0, t1));
-  g->launches += g->n > 0 ? 7 : 0;  // plan_slots, plan_cells, plan_tasks, cells, tiny, tasks, finalize_t
+  g->launches += g->n > 0 ? 6 : 0;  // plan_slots, plan_cells, plan_tasks, cells, tasks, finalize_t
   return PV_OK;
 }
 
@@ -322,7 +323,7 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
   PV_TRY(next_pair(g, 1, &t0, &t1));
   PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, g->ctas[1], st, t0,
                               t1));
-  g->launches += g->n > 0 ? 8 : 0;  // prep, plan x3, cells, tiny, tasks, finalize_t
+  g->launches += g->n > 0 ? 7 : 0;  // prep, plan x3, cells, tasks, finalize_t
   return PV_OK;
 }
 

@@ -299,6 +299,67 @@ __device__ __forceinline__ void write_bwd(const GridDev& g, int s, double Sth, d
   }
 }
 
+// ---- tiny cells (at most kTinyCell particles) ---------------------------------------
+// As in the forward sweep: once the cell-centric kernel's CTA-sized cells are
+// all taken, its warps take the tiny cells one per warp (lane l: particle ca +
+// l), stage the 27 windows of the widened plan with each neighbour's records
+// shifted into a's frame, and run one adjoint sweep over them; each lane keeps
+// its five sums in registers and writes its outputs.
+constexpr int kTinyBufB = 128;  // staged candidates per warp and pass
+constexpr int kTinyWarpBytesB =
+    (kTinyBufB + kPad) * (16 + 16 + 4) + (int)((sizeof(TinySlots) + 15) / 16 * 16);
+
+__device__ __forceinline__ void tiny_phase_bwd(const GridDev& g, unsigned char* buf,
+                                               unsigned* __restrict__ M, int lane,
+                                               const float* __restrict__ g_rho,
+                                               const float* __restrict__ g_D,
+                                               float* __restrict__ g_pos,
+                                               float* __restrict__ g_h) {
+  float4* Sx = reinterpret_cast<float4*>(buf);
+  float4* Sa = Sx + kTinyBufB + kPad;
+  int* Sj = reinterpret_cast<int*>(Sa + kTinyBufB + kPad);
+  TinySlots& ts = *reinterpret_cast<TinySlots*>(Sj + kTinyBufB + kPad);
+  const Slot self = slot_info(kSelfSlot);
+  const float munit = (float)(16.0 / 3.14159265358979323846);
+  const int nt = *g.n_ycells;
+  if (nt == 0) return;  // no tiny cells: leave the counter alone
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(g.ycell_next, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= nt) break;
+    const int a = g.ycells[w];
+    const int na = g.cell_count[a], ca = g.cell_start[a];
+    const BoxDev& B = g.boxes[g.cell_box[a]];
+    const float edge = B.edge_f;
+    const int total = tiny_slots(g, a, lane, ts);
+    LaneB L;
+    laneb_init(L);
+    if (lane < na) laneb_set(L, g, B, self, ca + lane);
+    int q = 0;  // slot of this lane's next staged candidate (non-decreasing)
+    for (int f0 = 0; f0 < total; f0 += kTinyBufB) {
+      const int len = min(kTinyBufB, total - f0);
+      for (int e = lane; e < len; e += 32) {
+        const int f = f0 + e;
+        while (ts.off[q + 1] <= f) q++;
+        float sx, sy, sz;
+        const int sj = tiny_candidate(g, ts, q, f, edge, sx, sy, sz);
+        const float4 xe = g.bx[sj];
+        Sx[e] = make_float4(xe.x + sx, xe.y + sy, xe.z + sz, xe.w);
+        Sa[e] = g.ba[sj];
+        Sj[e] = sj;
+      }
+      __syncwarp();
+      auto jidx = [&](int j) { return Sj[j]; };
+      sweep_bwd(L, Sx, Sa, 0, len, M, lane, g, B, jidx);
+      __syncwarp();  // the buffers are rewritten next
+    }
+    if (lane < na)
+      write_bwd(g, ca + lane, (double)L.Sth, (double)L.Suh, (double)L.gx, (double)L.gy,
+                (double)L.gz, g_rho, g_D, g_pos, g_h, munit * g.m_max[g.cell_box[a]]);
+  }
+}
+
 struct CellSharedB {
   int I[kNSlot], J0[kNSlot];
   int off[kNSlot + 1];
@@ -310,6 +371,8 @@ struct CellSharedB {
 
 constexpr int kCellWarps = kCellThreads / 32;
 constexpr int kCellFixedSmem = kCellWarps * kMaskChunks * 32 * 4;  // the warps' hit masks
+static_assert(kCellWarps * kTinyWarpBytesB <= kCellSmemFor[3] - kCellFixedSmem,
+              "the tiny-cell buffers fit the smallest dynamic shared memory");
 
 __device__ __forceinline__ float sproj(float4 x, float ux, float uy, float uz, int s, float off) {
   return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
@@ -448,64 +511,10 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
                 acc[4 * na + t], g_rho, g_D, g_pos, g_h, mscale);
     __syncthreads();
   }
-}
-
-// ---- warp-per-cell kernel (cells of at most kTinyCell particles) -------------------
-// As the forward's: one warp per tiny cell a, lane l its particle ca + l; the
-// 27 windows of the (widened) plan staged one after the other with each
-// neighbour's records shifted into a's frame, and one adjoint sweep over all
-// of them.  The lane keeps its five sums in registers and writes its outputs.
-constexpr int kTinyWarpsB = 4;
-constexpr int kTinyBufB = 128;  // staged candidates per warp and pass
-
-__global__ void __launch_bounds__(kTinyWarpsB * 32, 6) k_backward_tiny(
-    GridDev g, const float* __restrict__ g_rho, const float* __restrict__ g_D,
-    float* __restrict__ g_pos, float* __restrict__ g_h) {
-  __shared__ float4 s_x[kTinyWarpsB][kTinyBufB + kPad];
-  __shared__ float4 s_a[kTinyWarpsB][kTinyBufB + kPad];
-  __shared__ int s_j[kTinyWarpsB][kTinyBufB + kPad];
-  __shared__ unsigned s_mask[kTinyWarpsB][kMaskChunks * 32];
-  __shared__ TinySlots s_slots[kTinyWarpsB];
-  if (*g.flags) return;
-  const int nt = *g.n_ycells;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* Sx = s_x[warp];
-  float4* Sa = s_a[warp];
-  int* Sj = s_j[warp];
-  TinySlots& ts = s_slots[warp];
-  const Slot self = slot_info(kSelfSlot);
-  const float munit = (float)(16.0 / 3.14159265358979323846);
-  for (int w = blockIdx.x * kTinyWarpsB + warp; w < nt; w += gridDim.x * kTinyWarpsB) {
-    const int a = g.ycells[w];
-    const int na = g.cell_count[a], ca = g.cell_start[a];
-    const BoxDev& B = g.boxes[g.cell_box[a]];
-    const float edge = B.edge_f;
-    const int total = tiny_slots(g, a, lane, ts);
-    LaneB L;
-    laneb_init(L);
-    if (lane < na) laneb_set(L, g, B, self, ca + lane);
-    int q = 0;  // slot of this lane's next staged candidate (non-decreasing)
-    for (int f0 = 0; f0 < total; f0 += kTinyBufB) {
-      const int len = min(kTinyBufB, total - f0);
-      for (int e = lane; e < len; e += 32) {
-        const int f = f0 + e;
-        while (ts.off[q + 1] <= f) q++;
-        float sx, sy, sz;
-        const int sj = tiny_candidate(g, ts, q, f, edge, sx, sy, sz);
-        const float4 xe = g.bx[sj];
-        Sx[e] = make_float4(xe.x + sx, xe.y + sy, xe.z + sz, xe.w);
-        Sa[e] = g.ba[sj];
-        Sj[e] = sj;
-      }
-      __syncwarp();
-      auto jidx = [&](int j) { return Sj[j]; };
-      sweep_bwd(L, Sx, Sa, 0, len, s_mask[warp], lane, g, B, jidx);
-      __syncwarp();  // the buffer is restaged by the next pass
-    }
-    if (lane < na)
-      write_bwd(g, ca + lane, (double)L.Sth, (double)L.Suh, (double)L.gx, (double)L.gy,
-                (double)L.gz, g_rho, g_D, g_pos, g_h, munit * g.m_max[g.cell_box[a]]);
-  }
+  // then the tiny cells, one per warp, in the dynamic shared memory that the
+  // cells no longer use (at least kCellWarps * kTinyWarpBytesB of it)
+  tiny_phase_bwd(g, reinterpret_cast<unsigned char*>(var) + warp * kTinyWarpBytesB, Mw, lane,
+                 g_rho, g_D, g_pos, g_h);
 }
 
 // ---- task kernel (cells too dense for the cell-centric kernel) ----------------------
@@ -644,8 +653,6 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
                                                                        g_h);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
-  k_backward_tiny<<<num_sms * 6, kTinyWarpsB * 32, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_backward_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_bwd_finalize_t<<<num_sms * 8, 256, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);

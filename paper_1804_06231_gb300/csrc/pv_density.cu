@@ -127,7 +127,10 @@ __global__ void k_plan_slots(GridDev g, int wide) {
     }
   }
   g.plan[idx] = flagged ? make_int4(0, 0, 0, 0) : pl;
-  if (idx == 0) *g.n_ycells = 0;  // k_plan_cells fills the list of tiny cells
+  if (idx == 0) {  // k_plan_cells fills the list of tiny cells, the sweep takes them
+    *g.n_ycells = 0;
+    *g.ycell_next = 0;
+  }
 }
 
 // One thread per cell: route a cell of at most kTinyCell particles to the
@@ -422,11 +425,85 @@ __device__ __forceinline__ void write_out(const GridDev& g, int s, long long ar,
   if (n_ngb) n_ngb[i] = an - 1;  // the self pair j = i
 }
 
+// ---- warp-per-cell kernel (cells of at most kTinyCell particles) -------------------
+// A clustered box or a small box has tens of thousands of cells with a few
+// particles each; as a CTA-sized cell each of them would cost a CTA's staging
+// and barriers plus up to 27 warp items of a few active lanes.  Instead, once
+// the cell-centric kernel's CTA-sized cells are all taken, its warps take the
+// tiny cells one per warp: lane l holds the particle ca + l of cell a.  The 27 trimmed
+// windows of the plan are staged one after the other, each neighbour's
+// particles shifted into a's frame (x_j + o edge: the pair shift of Section
+// 3.2 applied to j instead of i), and swept in one pass: the pre-filter of a
+// lane runs over all staged candidates and the evaluation costs the largest
+// total hit count of a lane instead of a sum of per-slot maxima.  Windows
+// longer than kTinyBuf in total (a tiny cell next to a dense one) are staged
+// in passes.  Each lane keeps its particle's sums in registers across the
+// slots and writes its outputs itself.
+constexpr int kTinyBuf = 128;  // staged candidates per warp and pass
+
+// Bytes of a warp's tiny-cell buffers (candidates {x,y,z,|x|^2}, masses,
+// cell-order indices, slot table), carved from the cell kernel's dynamic
+// shared memory once its CTA-sized cells are done.
+constexpr int kTinyWarpBytes =
+    (kTinyBuf + kPad) * (16 + 4 + 4) + (int)((sizeof(TinySlots) + 15) / 16 * 16);
+
+template <typename Out>
+__device__ __forceinline__ void tiny_phase_fwd(const GridDev& g, unsigned char* buf,
+                                               unsigned* __restrict__ M, int lane, Out out,
+                                               unsigned long long& inter, int& guards) {
+  float4* Sx = reinterpret_cast<float4*>(buf);
+  float* Sm = reinterpret_cast<float*>(Sx + kTinyBuf + kPad);
+  int* Sj = reinterpret_cast<int*>(Sm + kTinyBuf + kPad);
+  TinySlots& ts = *reinterpret_cast<TinySlots*>(Sj + kTinyBuf + kPad);
+  const Slot self = slot_info(kSelfSlot);
+  const int nt = *g.n_ycells;
+  if (nt == 0) return;  // no tiny cells: leave the counter alone
+  for (;;) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(g.ycell_next, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= nt) break;
+    const int a = g.ycells[w];
+    const int na = g.cell_count[a], ca = g.cell_start[a];
+    const BoxDev& B = g.boxes[g.cell_box[a]];
+    const float edge = B.edge_f;
+    const int total = tiny_slots(g, a, lane, ts);
+    LaneI L;
+    lane_init(L);
+    if (lane < na) lane_set(L, g, B, self, ca + lane, g.xm[ca + lane], g.hs[ca + lane]);
+    int q = 0;  // slot of this lane's next staged candidate (non-decreasing)
+    for (int f0 = 0; f0 < total; f0 += kTinyBuf) {
+      const int len = min(kTinyBuf, total - f0);
+      for (int e = lane; e < len; e += 32) {
+        const int f = f0 + e;
+        while (ts.off[q + 1] <= f) q++;
+        float sx, sy, sz;
+        const int sj = tiny_candidate(g, ts, q, f, edge, sx, sy, sz);
+        const float4 xj = g.xm[sj];
+        const float x = xj.x + sx, y = xj.y + sy, z = xj.z + sz;
+        Sx[e] = make_float4(x, y, z, fmaf(x, x, fmaf(y, y, z * z)));
+        Sm[e] = xj.w;
+        Sj[e] = sj;
+      }
+      __syncwarp();
+      auto jidx = [&](int j) { return Sj[j]; };
+      sweep_fwd(L, Sx, Sm, 0, len, M, lane, g, B, jidx, guards);
+      __syncwarp();  // the buffers are rewritten next
+    }
+    if (lane < na) {
+      out(a, ca + lane, L);
+      inter += (unsigned long long)(L.n - 1);
+    }
+  }
+}
+
 // ---- cell-centric kernel ------------------------------------------------------------
 
 constexpr int kCellWarps = kCellThreads / 32;
 // per-CTA shared memory that does not depend on the cell: the warps' hit masks
 constexpr int kCellFixedSmem = kCellWarps * kMaskChunks * 32 * 4;
+static_assert(kCellWarps * kTinyWarpBytes <= kCellSmemFor[4] - kCellFixedSmem,
+              "the tiny-cell buffers fit the smallest dynamic shared memory");
 constexpr int kCellElemJ = 20;  // staged bytes per particle of a window: {x,y,z,|x|^2}, m
 constexpr int kCellElemA = 40;  // bytes per particle of the cell
 
@@ -591,92 +668,21 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
     }
     __syncthreads();
   }
-  for (int s = 16; s > 0; s >>= 1) {
-    inter += __shfl_xor_sync(0xffffffffu, inter, s);
-    guards += __shfl_xor_sync(0xffffffffu, guards, s);
-  }
-  if (lane == 0) {
-    if (inter) atomicAdd(&g.counters[0], inter);
-    if (guards) atomicAdd(&g.counters[1], (unsigned long long)guards);
-  }
-}
-
-// ---- warp-per-cell kernel (cells of at most kTinyCell particles) -------------------
-// A clustered box or a small box has tens of thousands of cells with a few
-// particles each; in the cell-centric kernel each of them costs a CTA's
-// staging and barriers plus up to 27 warp items of a few active lanes.  Here
-// one warp takes such a cell a, lane l its particle ca + l.  The 27 trimmed
-// windows of the plan are staged one after the other, each neighbour's
-// particles shifted into a's frame (x_j + o edge: the pair shift of Section
-// 3.2 applied to j instead of i), and swept in one pass: the pre-filter of a
-// lane runs over all staged candidates and the evaluation costs the largest
-// total hit count of a lane instead of a sum of per-slot maxima.  Windows
-// longer than kTinyBuf in total (a tiny cell next to a dense one) are staged
-// in passes.  Each lane keeps its particle's sums in registers across the
-// slots and writes its outputs itself.
-constexpr int kTinyWarps = 4;
-constexpr int kTinyBuf = 256;  // staged candidates per warp and pass
-
-__global__ void __launch_bounds__(kTinyWarps * 32, 6) k_density_tiny(GridDev g,
-                                                                    float* __restrict__ rho,
-                                                                    float* __restrict__ drho_dh,
-                                                                    int32_t* __restrict__ n_ngb) {
-  __shared__ float4 s_x[kTinyWarps][kTinyBuf + kPad];
-  __shared__ float s_m[kTinyWarps][kTinyBuf + kPad];
-  __shared__ int s_j[kTinyWarps][kTinyBuf + kPad];
-  __shared__ unsigned s_mask[kTinyWarps][kMaskChunks * 32];
-  __shared__ TinySlots s_slots[kTinyWarps];
-  if (*g.flags) return;
-  const int nt = *g.n_ycells;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* Sx = s_x[warp];
-  float* Sm = s_m[warp];
-  int* Sj = s_j[warp];
-  TinySlots& ts = s_slots[warp];
-  const Slot self = slot_info(kSelfSlot);
-  const float munit = (float)(16.0 / 3.14159265358979323846);
-  unsigned long long inter = 0;
-  int guards = 0;
-  for (int w = blockIdx.x * kTinyWarps + warp; w < nt; w += gridDim.x * kTinyWarps) {
-    const int a = g.ycells[w];
-    const int na = g.cell_count[a], ca = g.cell_start[a];
-    const BoxDev& B = g.boxes[g.cell_box[a]];
-    const float edge = B.edge_f;
-    const int total = tiny_slots(g, a, lane, ts);
-    LaneI L;
-    lane_init(L);
-    if (lane < na) lane_set(L, g, B, self, ca + lane, g.xm[ca + lane], g.hs[ca + lane]);
-    int q = 0;  // slot of this lane's next staged candidate (non-decreasing)
-    for (int f0 = 0; f0 < total; f0 += kTinyBuf) {
-      const int len = min(kTinyBuf, total - f0);
-      for (int e = lane; e < len; e += 32) {
-        const int f = f0 + e;
-        while (ts.off[q + 1] <= f) q++;
-        float sx, sy, sz;
-        const int sj = tiny_candidate(g, ts, q, f, edge, sx, sy, sz);
-        const float4 xj = g.xm[sj];
-        const float x = xj.x + sx, y = xj.y + sy, z = xj.z + sz;
-        Sx[e] = make_float4(x, y, z, fmaf(x, x, fmaf(y, y, z * z)));
-        Sm[e] = xj.w;
-        Sj[e] = sj;
-      }
-      __syncwarp();
-      auto jidx = [&](int j) { return Sj[j]; };
-      sweep_fwd(L, Sx, Sm, 0, len, s_mask[warp], lane, g, B, jidx, guards);
-      __syncwarp();  // the buffer is restaged by the next pass
-    }
-    if (lane < na) {
-      const int s = ca + lane;
-      const int i = g.orig[s];
-      const float h = g.hs[s];
-      const float H = g.gamma * h;
-      const float c = munit * g.m_max[g.cell_box[a]] / (H * H * H);
-      rho[i] = c * L.rho;
-      if (drho_dh) drho_dh[i] = -(c / h) * L.D;
-      if (n_ngb) n_ngb[i] = L.n - 1;  // the self pair j = i
-      inter += (unsigned long long)(L.n - 1);
-    }
-  }
+  // then the tiny cells, one per warp, in the dynamic shared memory that the
+  // cells no longer use (at least kCellWarps * kTinyWarpBytes of it)
+  tiny_phase_fwd(
+      g, reinterpret_cast<unsigned char*>(var) + warp * kTinyWarpBytes, Mw, lane,
+      [&](int a, int s, const LaneI& L) {
+        const int i = g.orig[s];
+        const float h = g.hs[s];
+        const float H = g.gamma * h;
+        const float c = (float)(16.0 / 3.14159265358979323846) * g.m_max[g.cell_box[a]] /
+                        (H * H * H);
+        rho[i] = c * L.rho;
+        if (drho_dh) drho_dh[i] = -(c / h) * L.D;
+        if (n_ngb) n_ngb[i] = L.n - 1;  // the self pair j = i
+      },
+      inter, guards);
   for (int s = 16; s > 0; s >>= 1) {
     inter += __shfl_xor_sync(0xffffffffu, inter, s);
     guards += __shfl_xor_sync(0xffffffffu, guards, s);
@@ -1000,8 +1006,6 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
   k_density_cells<<<num_sms * ctas_per_sm, kCellThreads, smem, st>>>(g, rho, drho_dh, n_ngb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
-  k_density_tiny<<<num_sms * 6, kTinyWarps * 32, 0, st>>>(g, rho, drho_dh, n_ngb);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_finalize_t<<<num_sms * 8, 256, 0, st>>>(g, rho, drho_dh, n_ngb);

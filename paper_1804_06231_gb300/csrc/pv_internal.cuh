@@ -98,6 +98,7 @@ struct GridDev {
   int32_t* n_tcells;
   int32_t* ycells;   // [C] cells of at most kTinyCell particles (one warp each)
   int32_t* n_ycells;
+  int32_t* ycell_next;  // next entry of ycells to take
   // tasks
   int4* tasks;
   int32_t* ntask;

@@ -166,6 +166,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.ccell_next = sc + 7;
   d.n_tcells = sc + 8;
   d.n_ycells = sc + 10;
+  d.ycell_next = sc + 11;
   d.gacc = nullptr;
   d.bx = nullptr;
   d.ba = nullptr;
