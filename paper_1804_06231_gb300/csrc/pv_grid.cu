@@ -510,6 +510,30 @@ __global__ void __launch_bounds__(kSortTinyWarps * 32) k_cell_sort_tiny(
     if (lane == 0) g.cell_Hmax[c] = hmax;
     if (cnt == 0) continue;
     __syncwarp();
+    if (cnt <= 32) {
+      // one key per lane: its rank is the number of keys before it in
+      // (projection, caller index) order, counted over shuffles (the order
+      // of the bucket sort below, without its buckets)
+      const float4 xl = lane < cnt ? wx[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const int ol = lane < cnt ? orig[lane] : 0;
+      for (int k = 0; k < kNDir; k++) {
+        float ux, uy, uz;
+        axis_u(k, ux, uy, uz);
+        const float kl = project(xl, ux, uy, uz);
+        int r = 0;
+        for (int u = 0; u < cnt; u++) {
+          const float ku = __shfl_sync(0xffffffffu, kl, u);
+          const int ou = __shfl_sync(0xffffffffu, ol, u);
+          r += key_less(ku, ou, kl, ol) ? 1 : 0;
+        }
+        if (lane < cnt) {
+          const size_t base = (size_t)k * g.n + cs;
+          g.perm[base + r] = (uint16_t)lane;
+          g.dist[base + r] = kl;
+        }
+      }
+      continue;
+    }
     int nb = 32;
     while (nb < cnt) nb <<= 1;
     for (int k = 0; k < kNDir; k++) {
