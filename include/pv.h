@@ -262,9 +262,10 @@ pv_status pv_grid_sweep_times(pv_grid* g, double* ms, int64_t* launches);
    or freed, by this library or by any library it calls.
    Limits: n <= PV_STATIC_MAX_PARTICLES and nc^3 <= PV_STATIC_MAX_CELLS;
    larger inputs return PV_ERR_TOO_LARGE before any work is queued.
-   The first call on each device looks up that device's address of the array
-   (cudaGetSymbolAddress, with the device current); make that first call
-   before any stream capture.  All calls share the one array: calls whose
+   Every call looks up the current device's address of the array
+   (cudaGetSymbolAddress, a host-side query: the address may change after
+   cudaDeviceReset); the first call on a device may load the library's
+   kernels there, so make it before any stream capture.  All calls share the one array: calls whose
    work overlaps on the GPU (other streams, other host threads) race and
    corrupt each other's results; serialise them. */
 #define PV_STATIC_MAX_PARTICLES 65536

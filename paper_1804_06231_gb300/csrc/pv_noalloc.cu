@@ -16,7 +16,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "pv_internal.cuh"
 
@@ -55,27 +54,10 @@ static __device__ __align__(256) unsigned char g_pv_static_scratch[kScratchBytes
 
 namespace {
 
-std::mutex g_mu;
-constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device, looked up once per
-// device (the first call on a device does it, with that device current).
-cudaError_t static_scratch(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_pv_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
-  return cudaSuccess;
-}
+// Device address of the scratch on the current device.  Looked up on every
+// call, not cached: after cudaDeviceReset the module is loaded again and the
+// array may sit at another address.
+cudaError_t static_scratch(void** out) { return cudaGetSymbolAddress(out, g_pv_static_scratch); }
 
 template <typename T>
 T* carve(unsigned char*& cur, size_t count) {
