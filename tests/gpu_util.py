@@ -39,8 +39,9 @@ def run_density(boxes, uniform_mass=False, count_candidates=False, expect_flags=
     if not expect_flags:
         assert st.device_flags == 0, f"device flags {st.device_flags}"
 
-    return (rho.cpu().numpy().astype(np.float64), D.cpu().numpy().astype(np.float64),
-            n.cpu().numpy(), st, cand)
+    # Widened on the device: with flags latched the outputs are unwritten, and
+    # numpy warns when it widens arbitrary bit patterns.
+    return (rho.double().cpu().numpy(), D.double().cpu().numpy(), n.cpu().numpy(), st, cand)
 
 
 def check_density(rho, D, n, ref, idx=None):
