@@ -29,6 +29,15 @@
  * PV_ERR_DEVICE.
  *
  * Thread safety: a pv_grid may be used by one host thread at a time.
+ *
+ * CUDA graphs: the launches of pv_sort_cells, pv_density and
+ * pv_density_backward may be captured into a graph once each call has run
+ * eagerly in the same CUDA context (the eager call sets the kernels'
+ * shared-memory limits, which cannot be set inside a capture; a captured
+ * call without it returns PV_ERR_CUDA).  After cudaDeviceReset, grids
+ * created before it are invalid (their device memory is gone: destroy them);
+ * new grids and pv_density_static work, the limits being set again by the
+ * next eager call.
  */
 #ifndef PV_H
 #define PV_H
@@ -74,7 +83,7 @@ typedef struct {
 typedef struct {
   int32_t n_boxes;          /* >= 1 */
   const pv_box_desc* boxes; /* host array [n_boxes]; copied, the caller keeps ownership */
-  double gamma;             /* H = gamma h; <= 0 selects 1.825742 */
+  double gamma;             /* H = gamma h; <= 0 or NaN selects 1.825742 */
   uint32_t flags;           /* must be 0 */
 } pv_grid_desc;
 
@@ -253,7 +262,7 @@ pv_status pv_grid_sweep_times(pv_grid* g, double* ms, int64_t* launches);
    pv_density on a one-box grid, with the same arguments' meaning and layout
    (pos device double [n][3], h device float [n], m device float [n] or NULL
    for m_uniform, outputs device float/int32 [n] in the caller's order; box
-   [0, L)^3 with nc^3 cells; gamma <= 0 selects 1.825742).  flags_out, if not
+   [0, L)^3 with nc^3 cells; gamma <= 0 or NaN selects 1.825742).  flags_out, if not
    NULL, is a device uint32 that receives the PV_FLAG_* bits the kernels
    latched (0 = inputs valid; outputs are not written otherwise).
    Memory: every intermediate array lives in one fixed device array inside

@@ -41,6 +41,12 @@ pv_status cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? PV_ERR_OUT_OF_MEMORY : PV_ERR_CUDA;
 }
 
+}  // namespace
+
+pv_status pv::record_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+
+namespace {
+
 #define PV_CUDA(call)                                  \
   do {                                                 \
     cudaError_t e_ = (call);                           \

@@ -637,9 +637,8 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
                             cudaStream_t st, cudaEvent_t t0, cudaEvent_t t1) {
   if (g.n == 0) return cudaSuccess;
   if (ctas_per_sm < 1 || ctas_per_sm > 3) return cudaErrorInvalidValue;
-  static std::atomic<unsigned long long> smem_done{0};
-  cudaError_t e = set_max_dynamic_smem(smem_done, reinterpret_cast<const void*>(&k_backward_cells),
-                                       kCellSmemFor[1]);
+  cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(&k_backward_cells),
+                                       kCellSmemFor[1], st);
   if (e != cudaSuccess) return e;
   const int smem = kCellSmemFor[ctas_per_sm];
   const int nb = (g.n + 255) / 256;

@@ -994,9 +994,8 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
                            cudaEvent_t t1) {
   if (g.n == 0) return cudaSuccess;
   if (ctas_per_sm < 1 || ctas_per_sm > 4) return cudaErrorInvalidValue;
-  static std::atomic<unsigned long long> smem_done{0};
-  cudaError_t e = set_max_dynamic_smem(smem_done, reinterpret_cast<const void*>(&k_density_cells),
-                                       kCellSmemFor[1]);
+  cudaError_t e = set_max_dynamic_smem(reinterpret_cast<const void*>(&k_density_cells),
+                                       kCellSmemFor[1], st);
   if (e != cudaSuccess) return e;
   const int smem = kCellSmemFor[ctas_per_sm];
   if ((e = launch_plan(g, 0, smem - kCellFixedSmem, kCellElemJ, kCellElemA,

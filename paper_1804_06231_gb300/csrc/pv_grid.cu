@@ -722,19 +722,17 @@ cudaError_t launch_clear(const GridDev& g, cudaStream_t st) {
 
 cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, const float* m,
                         float m_uniform, cudaStream_t st) {
-  static std::atomic<unsigned long long> smem_done{0};
   constexpr int smem = (int)sort_small_smem<kSortSmallMax>();
-  cudaError_t e = set_max_dynamic_smem(
-      smem_done, reinterpret_cast<const void*>(&k_cell_sort<kSortSmallMax>), smem);
+  cudaError_t e =
+      set_max_dynamic_smem(reinterpret_cast<const void*>(&k_cell_sort<kSortSmallMax>), smem, st);
   if (e != cudaSuccess) return e;
   k_cell_sort<kSortSmallMax><<<g.ncell, kSortThreads, smem, st>>>(g, pos, h, m, m_uniform);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_cell_sort_tiny<<<(g.ncell + kSortTinyWarps - 1) / kSortTinyWarps, kSortTinyWarps * 32, 0,
                      st>>>(g, pos, h, m, m_uniform);
   if ((e = cudaGetLastError()) != cudaSuccess || g.n == 0) return e;
-  static std::atomic<unsigned long long> big_done{0};
-  if ((e = set_max_dynamic_smem(big_done, reinterpret_cast<const void*>(&k_sort_big<true>),
-                                (int)kSortBigDynSmem)) != cudaSuccess)
+  if ((e = set_max_dynamic_smem(reinterpret_cast<const void*>(&k_sort_big<true>),
+                                (int)kSortBigDynSmem, st)) != cudaSuccess)
     return e;
   // persistent grids over (big cell, axis): two CTAs per SM for the staged
   // instance, one for the rare cells above kSortBigSmem

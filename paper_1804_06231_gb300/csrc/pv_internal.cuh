@@ -20,7 +20,6 @@
 
 #include <cuda_runtime.h>
 
-#include <atomic>
 #include <cmath>
 #include <stdint.h>
 
@@ -480,20 +479,25 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
                             cudaStream_t st, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 constexpr int kDensityCtasDefault = 3, kBackwardCtasDefault = 3;
 
-// Raises `func`'s dynamic shared-memory limit to `bytes` the first time it is
-// called on a device (bit `dev` of `done` records it; devices >= 64 set it on
-// every call).  Kept off CUDA-graph captures by the eager first launch.
-inline cudaError_t set_max_dynamic_smem(std::atomic<unsigned long long>& done, const void* func,
-                                        int bytes) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+// Raises `func`'s dynamic shared-memory limit to `bytes`.  The limit is an
+// attribute of the kernel in the current CUDA context, so it is set again on
+// every launch: a context created after cudaDeviceReset gets it too.  While
+// `st` is being captured into a CUDA graph the call only checks that an
+// earlier launch in this context set the limit, and returns
+// cudaErrorStreamCaptureUnsupported if none did (make one eager call first).
+inline cudaError_t set_max_dynamic_smem(const void* func, int bytes, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
   if (e != cudaSuccess) return e;
-  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
-  if (bit && (done.load() & bit)) return cudaSuccess;
-  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done.fetch_or(bit);
-  return e;
+  if (cs == cudaStreamCaptureStatusNone)
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, func)) != cudaSuccess) return e;
+  return fa.maxDynamicSharedSizeBytes >= bytes ? cudaSuccess : cudaErrorStreamCaptureUnsupported;
 }
+// Records `e` and `what` as the calling thread's last CUDA error (the text
+// pv_last_cuda_error returns) and maps `e` to a status code.
+pv_status record_cuda_error(cudaError_t e, const char* what);
 cudaError_t launch_count_candidates(const GridDev& g, cudaStream_t st);
 cudaError_t launch_raw_density(const float4* xi, int ni, const float4* xj, int nj, float H,
                                int reps, float2* out, cudaStream_t st);

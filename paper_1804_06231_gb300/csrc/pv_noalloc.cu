@@ -79,9 +79,8 @@ __global__ void k_static_setup(pv::BoxDev* box, pv::BoxDev val, int64_t* first, 
   if (i < ncell) cell_box[i] = 0;
 }
 
-pv_status fail(cudaError_t e, const char*) {
-  return e == cudaErrorMemoryAllocation ? PV_ERR_OUT_OF_MEMORY : PV_ERR_CUDA;
-}
+// the same error record as the other entry points (pv_last_cuda_error)
+pv_status fail(cudaError_t e, const char* what) { return pv::record_cuda_error(e, what); }
 
 }  // namespace
 
@@ -95,7 +94,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   if (n > kMaxParticles || ncell > kMaxCells) return PV_ERR_TOO_LARGE;
   if (n > 0 && (!pos || !h || !rho)) return PV_ERR_INVALID_ARGUMENT;
   if (!m && !(m_uniform >= 0.0f && m_uniform < 3.0e38f)) return PV_ERR_INVALID_ARGUMENT;
-  if (gamma <= 0.0) gamma = 1.825742;
+  if (!(gamma > 0.0)) gamma = 1.825742;  // also maps a NaN to the default
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   void* base = nullptr;

@@ -8,6 +8,7 @@ from paper_1804_06231_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 ADJ_RTOL = 1e-4   # relative L2 error of dL/dx and of dL/dh
+ADJ_PTOL = 1e-4   # per particle: error below this fraction of the largest component
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,6 +45,18 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def check_adjoint(gp, gh, gp0, gh0):
+    """Relative L2 <= ADJ_RTOL for dL/dx and dL/dh, and every particle within
+    ADJ_PTOL of the largest component, so that an error on a few particles
+    cannot hide inside the norm."""
+    assert rel_l2(gp, gp0) <= ADJ_RTOL, f"dL/dx rel L2 {rel_l2(gp, gp0):.3e}"
+    assert rel_l2(gh, gh0) <= ADJ_RTOL, f"dL/dh rel L2 {rel_l2(gh, gh0):.3e}"
+    ep = np.abs(gp - gp0).max() / np.abs(gp0).max()
+    eh = np.abs(gh - gh0).max() / np.abs(gh0).max()
+    assert ep <= ADJ_PTOL, f"dL/dx worst particle {ep:.3e} of the largest component"
+    assert eh <= ADJ_PTOL, f"dL/dh worst particle {eh:.3e} of the largest component"
+
+
 def _upstream(oracle_lib, box, seed):
     w, v = I.loss_weights(box.n, seed)
     ref = oracle_lib.density_cells(box.pos, box.h, box.m, 1.0, box.nc)
@@ -57,8 +70,7 @@ def test_adjoint_vs_oracle(oracle_lib, kind):
     w, v, g, k = _upstream(oracle_lib, box, 3)
     gp, gh = gpu_adjoint(box, g, k)
     gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g, k, 1.0, box.nc)
-    assert rel_l2(gp, gp0) <= ADJ_RTOL
-    assert rel_l2(gh, gh0) <= ADJ_RTOL
+    check_adjoint(gp, gh, gp0, gh0)
 
 
 def test_adjoint_rho_only_and_large_cells(oracle_lib):
@@ -66,8 +78,7 @@ def test_adjoint_rho_only_and_large_cells(oracle_lib):
     w, v, g, k = _upstream(oracle_lib, box, 11)
     gp, gh = gpu_adjoint(box, g, None)
     gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g, np.zeros(box.n), 1.0, 3)
-    assert rel_l2(gp, gp0) <= ADJ_RTOL
-    assert rel_l2(gh, gh0) <= ADJ_RTOL
+    check_adjoint(gp, gh, gp0, gh0)
 
 
 def test_adjoint_differentiation_workload(oracle_lib):
@@ -77,8 +88,7 @@ def test_adjoint_differentiation_workload(oracle_lib):
     w, v, g, k = _upstream(oracle_lib, box, I.SEEDS["cfg3"])
     gp, gh = gpu_adjoint(box, g, k, uniform_mass=True)
     gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g, k, 1.0, box.nc)
-    assert rel_l2(gp, gp0) <= ADJ_RTOL
-    assert rel_l2(gh, gh0) <= ADJ_RTOL
+    check_adjoint(gp, gh, gp0, gh0)
     rng = np.random.default_rng(64)
     idx = rng.choice(box.n, 64, replace=False)
     fd = np.array([[oracle_lib.fd_loss_grad(box.pos, box.h, box.m, w, v, p, c, 1e-6)
@@ -117,17 +127,14 @@ def test_autograd_function(oracle_lib):
 def test_adjoint_1m_every_particle(oracle_lib):
     """The benchmark workload (N = 1,048,576 uniform, 15^3 cells): the whole
     adjoint against the oracle's cell-list adjoint (relative L2 <= 1e-4 for
-    dL/dx and dL/dh) and per particle within 1e-3 of the largest component."""
+    dL/dx and dL/dh) and per particle within 1e-4 of the largest component."""
     box = I.cfg1()
     w, v = I.loss_weights(box.n, 3)
     ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
     g, k = oracle_lib.loss_upstream(ref.rho, w, v)
     gp, gh = gpu_adjoint(box, g, k, uniform_mass=True, launch_shape=(4, 3))
     gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g, k, 1.0, box.nc)
-    assert rel_l2(gp, gp0) <= ADJ_RTOL
-    assert rel_l2(gh, gh0) <= ADJ_RTOL
-    assert np.abs(gp - gp0).max() <= 1e-3 * np.abs(gp0).max()
-    assert np.abs(gh - gh0).max() <= 1e-3 * np.abs(gh0).max()
+    check_adjoint(gp, gh, gp0, gh0)
 
 
 @pytest.mark.slow
@@ -136,17 +143,14 @@ def test_adjoint_clustered_4m_every_particle(oracle_lib):
     21,392 in a cell), at the launch shape the benchmark tunes to for it (4 / 3
     CTAs per SM): dense cells run on the task kernel.  The whole adjoint
     against the oracle's pseudo-Verlet adjoint (relative L2 <= 1e-4 for dL/dx
-    and dL/dh, and per particle within 1e-3 of the largest component)."""
+    and dL/dh, and per particle within 1e-4 of the largest component)."""
     box = I.cfg2()
     w, v = I.loss_weights(box.n, 3)
     ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, box.nc)
     g, k = oracle_lib.loss_upstream(ref.rho, w, v)
     gp, gh = gpu_adjoint(box, g, k, uniform_mass=True, launch_shape=(4, 3))
     gp0, gh0 = oracle_lib.backward_pv(box.pos, box.h, box.m, g, k, 1.0, box.nc)
-    assert rel_l2(gp, gp0) <= ADJ_RTOL
-    assert rel_l2(gh, gh0) <= ADJ_RTOL
-    assert np.abs(gp - gp0).max() <= 1e-3 * np.abs(gp0).max()
-    assert np.abs(gh - gh0).max() <= 1e-3 * np.abs(gh0).max()
+    check_adjoint(gp, gh, gp0, gh0)
 
 
 def test_adjoint_box_of_other_size_with_unwrapped_positions(oracle_lib):
@@ -159,5 +163,4 @@ def test_adjoint_box_of_other_size_with_unwrapped_positions(oracle_lib):
     g, k = oracle_lib.loss_upstream(ref.rho, w, v)
     gp, gh = gpu_adjoint(box, g, k)
     gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g, k, box.L, box.nc)
-    assert rel_l2(gp, gp0) <= ADJ_RTOL
-    assert rel_l2(gh, gh0) <= ADJ_RTOL
+    check_adjoint(gp, gh, gp0, gh0)
