@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
           return cb + (int)g.perm[(size_t)sl.k * g.n + cb + pos];
         },
         [](int sj) { return sj; },
-        [&](int f, int sj) {  // cp.async: both records straight to shared memory
+        [&](int f, int, int sj) {  // cp.async: both records straight to shared memory
           cp_async16(&Sx[f], &g.bx[sj]);
           cp_async16(&Sa[f], &g.ba[sj]);
         });
@@ -644,7 +644,7 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   const int nb = (g.n + 255) / 256;
   k_bwd_prep<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_plan(g, 1, smem - kCellFixedSmem, kElemJ, kElemA, st)) !=
+  if ((e = launch_plan(g, 1, smem - kCellFixedSmem, kElemJ, kElemA, 0, st)) !=
       cudaSuccess)
     return e;
   if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;

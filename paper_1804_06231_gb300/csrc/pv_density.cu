@@ -140,7 +140,7 @@ __global__ void k_plan_slots(GridDev g, int wide) {
 // to plan.w; k_plan_tasks fills the tasks in).  The list appends and the task
 // reservations are aggregated per warp (one atomic per warp and list instead
 // of one per cell: a clustered box has tens of thousands of cells).
-__global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a) {
+__global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a, int elem_i) {
   if (*g.flags) return;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -153,9 +153,12 @@ __global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a)
     tiny = na > 0 && na <= kTinyCell;
     if (na > 0 && !tiny) {
       pl = g.plan + (size_t)a * kNSlot;
-      int total = 0;
-      for (int o = 0; o < kNSlot; o++) total += pl[o].z - pl[o].y;
-      fits = elem_j * (total + kPad) + elem_a * na <= smem_budget;
+      int total = 0, sum_i = 0;  // windows padded to groups of four
+      for (int o = 0; o < kNSlot; o++) {
+        total += (pl[o].z - pl[o].y + 3) & ~3;
+        sum_i += pl[o].x;
+      }
+      fits = elem_j * (total + kPad + 4) + elem_a * na + elem_i * sum_i + 16 <= smem_budget;
       if (!fits)
         for (int o = 0; o < kNSlot; o++) nblk_tot += (pl[o].x + kBlkI - 1) / kBlkI;
     }
@@ -257,140 +260,220 @@ __global__ void k_plan_tasks(GridDev g, int wide) {
 }
 
 // ---- the sweep ------------------------------------------------------------------
+//
+// Staged candidates are kept in groups of four: group g (80 bytes) holds the
+// negated x, y, z offsets, W = |x|^2 and the normalised mass M of candidates
+// 4g .. 4g+3 as five 16-byte vectors (negated, so that the differences
+// x_i - x_j are packed additions with no constant operand).  The pre-filter reads one vector per field for four
+// candidates and tests them two at a time with packed FP32 (fma.rn.f32x2: two
+// FP32 operations per issued instruction); the evaluation reads a hit's four
+// fields at fixed offsets from one address.  The sweep addresses shared memory
+// through 32-bit shared-window addresses.
+constexpr int kGroup = 20;  // floats per group of four staged candidates
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ float4 lds4(unsigned a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float lds1(unsigned a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+// byte offset of candidate c from the start of its group-aligned run
+__device__ __forceinline__ unsigned cand_off(int c) {
+  return (unsigned)((c >> 2) * (kGroup * 4) + ((c & 3) << 2));
+}
+// field offsets within a group (bytes): -x, -y, -z, W, M
+constexpr unsigned kOffY = 16, kOffZ = 32, kOffW = 48, kOffM = 64;
+
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
 struct LaneI {
-  float x, y, z;           // position of i in b's frame: x'_i - o edge
-  float nx, ny, nz, ci;    // -2 x_i and H_i^2 + guard - |x_i|^2 + margin (prefilter)
-  float Hsq_hi, Hsq_lo;    // guard band around H_i^2 (-1: inactive lane)
-  float Hinv2;             // 1 / H_i^2
-  int si;                  // cell-order index of i
-  float rho, D;            // sum_j m_j wh, sum_j m_j th
-  int n;                   // pairs with r < H_i (j = i included)
+  float2 x2, y2, z2;        // i in b's frame (x'_i - o edge), each twice (packed pairs)
+  float2 px2, py2, pz2;     // 2 x_i (pre-filter, against the negated staged x_j), twice
+  float2 nc2;               // -(H_i^2 + guard - |x_i|^2 + margin), twice (pre-filter)
+  float2 hinv2;             // 1 / H_i^2, twice
+  float dq;                 // hits with |1 - q| < dq are re-decided in FP64
+  int si;                   // cell-order index of i
+  float2 accW, accE, accN;  // per half of the hit pairs: sum m wh, sum m (s^2 - 2 t^2), count
+  int ncorr;                // FP64 corrections of the count
 };
 
+// An inactive lane's pre-filter bound never passes (d >= 3e38).
 __device__ __forceinline__ void lane_init(LaneI& L) {
-  L.x = L.y = L.z = 0.0f;
-  L.nx = L.ny = L.nz = 0.0f;
-  L.ci = -3.0e38f;
-  L.Hsq_hi = -1.0f; L.Hsq_lo = -1.0f; L.Hinv2 = 0.0f; L.si = 0;
-  L.rho = 0.0f; L.D = 0.0f; L.n = 0;
+  L.x2 = L.y2 = L.z2 = dup2(0.0f);
+  L.px2 = L.py2 = L.pz2 = dup2(0.0f);
+  L.nc2 = dup2(3.0e38f);
+  L.hinv2 = dup2(0.0f);
+  L.dq = 0.0f;
+  L.si = 0;
+  L.accW = L.accE = L.accN = dup2(0.0f);
+  L.ncorr = 0;
 }
 
-__device__ __forceinline__ void lane_set(LaneI& L, const GridDev& g, const BoxDev& B,
-                                         const Slot& sl, int si, float4 xi, float h) {
-  const float H = g.gamma * h;
+// xh = {x', y', z', h} of particle i (cell order index si), slot sl of box B.
+__device__ __forceinline__ void lane_set(LaneI& L, const BoxDev& B, float gamma, const Slot& sl,
+                                         int si, float4 xh) {
+  const float H = gamma * xh.w;
+  const float x = xh.x - sl.ox * B.edge_f;
+  const float y = xh.y - sl.oy * B.edge_f;
+  const float z = xh.z - sl.oz * B.edge_f;
   L.si = si;
-  L.x = xi.x - sl.ox * B.edge_f;
-  L.y = xi.y - sl.oy * B.edge_f;
-  L.z = xi.z - sl.oz * B.edge_f;
+  L.x2 = dup2(x);
+  L.y2 = dup2(y);
+  L.z2 = dup2(z);
+  L.px2 = dup2(2.0f * x);
+  L.py2 = dup2(2.0f * y);
+  L.pz2 = dup2(2.0f * z);
   const float Hsq = H * H, gb = guard_band(H, B.edge_f);
-  L.Hsq_hi = Hsq + gb;
-  L.Hsq_lo = Hsq - gb;
-  L.Hinv2 = __fdividef(1.0f, Hsq);
-  L.nx = -2.0f * L.x;
-  L.ny = -2.0f * L.y;
-  L.nz = -2.0f * L.z;
-  // prefilter r^2 < Hsq_hi as |x_j|^2 - 2 x_i.x_j < Hsq_hi - |x_i|^2.  Its FP32
+  const float hinv = __fdividef(1.0f, Hsq);
+  L.hinv2 = dup2(hinv);
+  // |1 - q| < gb / H^2 holds for every pair whose FP32 r^2 lies within the
+  // guard band gb of H^2 (the band is at least 3.2e-6 H^2, twice the square
+  // root's share plus the rounding of q), so a count decided by q < 1 outside
+  // it agrees with the FP64 decision
+  L.dq = gb * hinv;
+  // pre-filter r^2 < H^2 + gb as |x_j|^2 - 2 x_i.x_j < H^2 + gb - |x_i|^2.  Its FP32
   // rounding is below 3 ulp of (|x_i| + |x_j|)^2 <= 12 edge^2, i.e. < 5e-6 edge^2;
   // the margin 1e-5 edge^2 keeps every in-range pair (the exact test follows).
-  const float xi2 = fmaf(L.x, L.x, fmaf(L.y, L.y, L.z * L.z));
-  L.ci = (L.Hsq_hi - xi2) + 1.0e-5f * B.edge_f * B.edge_f;
+  const float xi2 = fmaf(x, x, fmaf(y, y, z * z));
+  L.nc2 = dup2(-((Hsq + gb - xi2) + 1.0e-5f * B.edge_f * B.edge_f));
 }
 
-constexpr int kMaskChunks = 8;  // 32-candidate chunks per segment of the sweep
-
-// exact FP32 r^2 between lane i and a staged particle {x, y, z, |x|^2}
-__device__ __forceinline__ float pair_r2(const LaneI& L, float4 q) {
-  const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
-  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+// rho, drho/dh and count sums of a lane (drho/dh from th = 6 wh - 3 (s^2 - 2 t^2))
+__device__ __forceinline__ void lane_sums(const LaneI& L, float& rho, float& D, int& n) {
+  rho = L.accW.x + L.accW.y;
+  D = fmaf(6.0f, rho, -3.0f * (L.accE.x + L.accE.y));
+  n = (int)(L.accN.x + L.accN.y) + L.ncorr;
 }
 
-// adds mj times the half-scaled kernel terms of the pair to lane i's sums
-__device__ __forceinline__ void fwd_pair(LaneI& L, float r2, float mj) {
-  const float qq = sqrt_approx(r2 * L.Hinv2);
-  float wh, th;
-  spline_half(qq, wh, th);
-  L.rho = fmaf(mj, wh, L.rho);
-  L.D = fmaf(mj, th, L.D);
+// Pre-filter of the 4 staged candidates of the group at shared address a:
+// shifts the sign of |x_j|^2 - 2 x_i.x_j - bound of each into m, first
+// candidate first.
+__device__ __forceinline__ void prefilter4(unsigned& m, unsigned a, const LaneI& L) {
+  const float4 x = lds4(a);
+  const float4 y = lds4(a + kOffY);
+  const float4 z = lds4(a + kOffZ);
+  const float4 w = lds4(a + kOffW);
+  float2 d0 = __fadd2_rn(make_float2(w.x, w.y), L.nc2);
+  float2 d1 = __fadd2_rn(make_float2(w.z, w.w), L.nc2);
+  d0 = __ffma2_rn(L.pz2, make_float2(z.x, z.y), d0);
+  d1 = __ffma2_rn(L.pz2, make_float2(z.z, z.w), d1);
+  d0 = __ffma2_rn(L.py2, make_float2(y.x, y.y), d0);
+  d1 = __ffma2_rn(L.py2, make_float2(y.z, y.w), d1);
+  d0 = __ffma2_rn(L.px2, make_float2(x.x, x.y), d0);
+  d1 = __ffma2_rn(L.px2, make_float2(x.z, x.w), d1);
+  m = __funnelshift_l(__float_as_uint(d0.x), m, 1);
+  m = __funnelshift_l(__float_as_uint(d0.y), m, 1);
+  m = __funnelshift_l(__float_as_uint(d1.x), m, 1);
+  m = __funnelshift_l(__float_as_uint(d1.y), m, 1);
 }
 
-// Sweeps the staged particles [lo, hi) for the warp's 32 particles.  Sx holds
-// {x, y, z, |x|^2} of each staged particle and Sm its mass; jidx(e) returns the
-// cell-order index of staged particle e (read only for the rare FP64
-// re-decisions near the cut-off).  M is the warp's [kMaskChunks][32] scratch.
+// Takes the highest set bit of m (candidate c of the chunk at bit 31 - c) and
+// returns c (32 when m is empty).
+__device__ __forceinline__ int take_hit(unsigned& m) {
+  const int c = __clz(m);
+  m &= ~__funnelshift_rc(0x80000000u, 0u, c);  // nothing to clear for c = 32
+  return c;
+}
+
+// Kernel terms of two hits (candidates cA, cB of the chunk at shared address
+// P; 32 for a lane with no hit left, which then reads the chunk's first
+// candidate, a staged finite value, and adds nothing), added to lane i's
+// packed sums.
+// With s = 1 - q and t = max(1/2 - q, 0): wh = s^3 - 4 t^3 and
+// 3 wh + q wh' = 6 wh - 3 (s^2 - 2 t^2).  q < 1 decides the pair (and the
+// count); mn keeps the smallest |1 - q| for the FP64 re-decision of the count
+// near the cut-off.
+__device__ __forceinline__ void eval2(LaneI& L, unsigned P, int cA, int cB, float& mn) {
+  const unsigned aA = P + cand_off(cA & 31), aB = P + cand_off(cB & 31);
+  const float2 dx = __fadd2_rn(L.x2, make_float2(lds1(aA), lds1(aB)));
+  const float2 dy = __fadd2_rn(L.y2, make_float2(lds1(aA + kOffY), lds1(aB + kOffY)));
+  const float2 dz = __fadd2_rn(L.z2, make_float2(lds1(aA + kOffZ), lds1(aB + kOffZ)));
+  const float2 mj = make_float2(lds1(aA + kOffM), lds1(aB + kOffM));
+  float2 r2 = __fmul2_rn(dz, dz);
+  r2 = __ffma2_rn(dy, dy, r2);
+  r2 = __ffma2_rn(dx, dx, r2);
+  const float2 u = __fmul2_rn(r2, L.hinv2);
+  const float qa = cA < 32 ? sqrt_approx(u.x) : 2.0f;
+  const float qb = cB < 32 ? sqrt_approx(u.y) : 2.0f;
+  const float2 nq = make_float2(-qa, -qb);
+  const float2 in = make_float2(qa < 1.0f ? 1.0f : 0.0f, qb < 1.0f ? 1.0f : 0.0f);
+  const float2 s = __fadd2_rn(dup2(1.0f), nq);
+  mn = fminf(mn, fminf(fabsf(s.x), fabsf(s.y)));
+  float2 t = __fadd2_rn(dup2(0.5f), nq);
+  t.x = fmaxf(t.x, 0.0f);
+  t.y = fmaxf(t.y, 0.0f);
+  const float2 me = __fmul2_rn(in, mj);
+  const float2 s2 = __fmul2_rn(s, s);
+  const float2 s3 = __fmul2_rn(s2, s);
+  const float2 t2 = __fmul2_rn(t, t);
+  const float2 wh = __ffma2_rn(__fmul2_rn(t, dup2(-4.0f)), t2, s3);
+  const float2 e = __ffma2_rn(t2, dup2(-2.0f), s2);
+  L.accW = __ffma2_rn(me, wh, L.accW);
+  L.accE = __ffma2_rn(me, e, L.accE);
+  L.accN = __fadd2_rn(L.accN, in);
+}
+
+// Sweeps the staged candidates [lo, hi) (groups at shared address S) for the
+// warp's 32 particles; jidx(e) returns the cell-order index of staged
+// candidate e (read only for the rare FP64 re-decisions near the cut-off).
+// Reads the staged groups from lo rounded down to a group up to the group
+// after hi + 2 (the staged arrays carry slack).
 //
-// Pass 1 pre-filters every candidate of a segment of up to 8 x 32 with four
-// FP32 instructions, |x_j|^2 - 2 x_i.x_j - (H_i^2 + guard - |x_i|^2 + margin),
-// whose sign bit is shifted into a 32-bit hit mask per chunk.  Pass 2 lets
-// each lane walk its own hits across the whole segment, so a pass costs the
-// largest number of hits of a lane, not the sum of per-chunk maxima.
-// Reads up to Sx[hi - 1 + 7] (the staged arrays carry kPad slack).
+// Chunk by chunk (32 candidates): the pre-filter gives each lane a 32-bit hit
+// mask in a register (candidate c at bit 31 - c); then the warp runs as many
+// rounds as the busiest lane has hits in the chunk, two hits per round, each
+// lane evaluating its own.
 template <typename JIndex>
-__device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ Sx,
-                                          const float* __restrict__ Sm, int lo, int hi,
-                                          unsigned* __restrict__ M, int lane, const GridDev& g,
+__device__ __forceinline__ void sweep_fwd(LaneI& L, unsigned S, int lo, int hi, const GridDev& g,
                                           const BoxDev& B, JIndex jidx, int& guards) {
-  for (int seg = lo; seg < hi; seg += 32 * kMaskChunks) {
-    const int seg_end = min(hi, seg + 32 * kMaskChunks);
-    const int nk = (seg_end - seg + 31) >> 5;
-    unsigned nz = 0;  // chunks of this lane with at least one hit
-    int tot = 0;      // hits of this lane in the segment
-    for (int k = 0; k < nk; k++) {
-      const int base = seg + 32 * k;
-      const int cnt = min(32, seg_end - base);
-      unsigned m = 0;
-      int c0 = 0;
-      const unsigned sbase = (unsigned)__cvta_generic_to_shared(Sx + base);
-#pragma unroll 1
-      for (; c0 < cnt; c0 += 8) prefilter8(m, sbase + 16u * c0, L.nx, L.ny, L.nz, L.ci);
-      m = __brev(m) >> (32 - c0);                        // candidate c at bit c
-      if (cnt < 32) m &= (1u << cnt) - 1u;
-      M[k * 32 + lane] = m;
-      nz |= (m != 0u ? 1u : 0u) << k;
-      tot += __popc(m);
-    }
-    // pass 2: as many rounds as the busiest lane has hits, without divergent
-    // branches.  A hit whose FP32 r^2 lies within rounding of H_i^2 is taken
-    // as in range here and re-decided in FP64 after the rounds.
-    for (int s = 16; s > 0; s >>= 1) tot = max(tot, __shfl_xor_sync(0xffffffffu, tot, s));
-    int k = 0;
+  for (int base = lo & ~3; base < hi; base += 32) {
+    const int cnt = min(32, hi - base);
+    const unsigned P = S + (unsigned)(base >> 2) * (kGroup * 4);
     unsigned m = 0;
-    bool amb = false;
-    // four rounds per iteration, interleaved by the compiler (2 % faster)
-#pragma unroll 4
-    for (int round = 0; round < tot; round++) {
-      if (m == 0u && nz != 0u) {
-        k = __ffs(nz) - 1;
-        nz &= nz - 1u;
-        m = M[k * 32 + lane];
-      }
-      const int c = __ffs(m) - 1;  // -1: this lane has no hit left
-      m &= m - 1u;
-      const int j = seg + 32 * k + max(c, 0);
-      const float r2 = pair_r2(L, Sx[j]);
-      const bool in = (c >= 0) && (r2 < L.Hsq_hi);
-      amb |= in && (r2 >= L.Hsq_lo);
-      fwd_pair(L, r2, in ? Sm[j] : 0.0f);
-      L.n += in ? 1 : 0;
+    if (cnt == 32) {
+#pragma unroll
+      for (int c = 0; c < 8; c++) prefilter4(m, P + c * (kGroup * 4), L);
+    } else {
+      const int n4 = (cnt + 3) >> 2;
+#pragma unroll 1
+      for (int c = 0; c < n4; c++) prefilter4(m, P + c * (kGroup * 4), L);
+      m = (m << (32 - 4 * n4)) & (0xffffffffu << (32 - cnt));
     }
-    // FP64 re-decision of the hits near the cut-off (rare): a lane walks its
-    // hits of the segment again and takes back the pairs that are out of range
-    if (__any_sync(0xffffffffu, amb)) {
-      if (amb) {
-        for (int kk = 0; kk < nk; kk++) {
-          unsigned mm = M[kk * 32 + lane];
-          while (mm != 0u) {
-            const int j = seg + 32 * kk + __ffs(mm) - 1;
-            mm &= mm - 1u;
-            const float r2 = pair_r2(L, Sx[j]);
-            if (r2 < L.Hsq_hi && r2 >= L.Hsq_lo) {
-              guards++;
-              if (!guard_inside(g.pos64, L.si, jidx(j), B.L, B.inv_L,
-                                g.gamma_d * (double)g.hs[L.si])) {
-                fwd_pair(L, r2, -Sm[j]);
-                L.n -= 1;
-              }
-            }
+    if (base < lo) m &= 0xffffffffu >> (lo - base);
+    const unsigned m0 = m;
+    const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(m));
+    float mn = 2.0f;
+#pragma unroll 1
+    for (int r = 0; r < rounds; r += 2) {
+      const int cA = take_hit(m);
+      const int cB = take_hit(m);
+      eval2(L, P, cA, cB, mn);
+    }
+    // FP64 re-decision of the count for hits near the cut-off (rare): the lane
+    // walks its hits of the chunk again
+    if (__any_sync(0xffffffffu, mn < L.dq)) {
+      if (mn < L.dq) {
+        const float xi = L.x2.x, yi = L.y2.x, zi = L.z2.x, hinv = L.hinv2.x;
+        unsigned mm = m0;
+        while (mm != 0u) {
+          const int c = take_hit(mm);
+          const unsigned a = P + cand_off(c);
+          const float dx = xi + lds1(a), dy = yi + lds1(a + kOffY), dz = zi + lds1(a + kOffZ);
+          const float q = sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) * hinv);
+          if (fabsf(1.0f + (-q)) < L.dq) {
+            guards++;
+            const bool in64 = guard_inside(g.pos64, L.si, jidx(base + c), B.L, B.inv_L,
+                                           g.gamma_d * (double)g.hs[L.si]);
+            L.ncorr += (int)in64 - (q < 1.0f ? 1 : 0);
           }
         }
       }
@@ -398,10 +481,22 @@ __device__ __forceinline__ void sweep_fwd(LaneI& L, const float4* __restrict__ S
   }
 }
 
-// staged form of a particle: {x, y, z, |x|^2}
-__device__ __forceinline__ float4 staged(float4 x) {
-  return make_float4(x.x, x.y, x.z, fmaf(x.x, x.x, fmaf(x.y, x.y, x.z * x.z)));
+// Stores particle x (cell-order record {x', y', z', m/m_max}) shifted by
+// (sx, sy, sz) as staged candidate f.
+__device__ __forceinline__ void put_staged(float* S, int f, float4 x, float sx, float sy,
+                                           float sz) {
+  float* p = S + (f >> 2) * kGroup + (f & 3);
+  const float px = x.x + sx, py = x.y + sy, pz = x.z + sz;
+  p[0] = -px;
+  p[4] = -py;
+  p[8] = -pz;
+  p[12] = fmaf(px, px, fmaf(py, py, pz * pz));
+  p[16] = x.w;
 }
+
+// floats of a staged buffer for n candidates (whole groups, with the slack the
+// sweep reads past the end)
+__host__ __device__ constexpr int staged_floats(int n) { return ((n + kPad + 3) >> 2) * kGroup; }
 
 __device__ __forceinline__ float warp_min(float v) {
   for (int s = 16; s > 0; s >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, s));
@@ -441,19 +536,17 @@ __device__ __forceinline__ void write_out(const GridDev& g, int s, long long ar,
 // slots and writes its outputs itself.
 constexpr int kTinyBuf = 128;  // staged candidates per warp and pass
 
-// Bytes of a warp's tiny-cell buffers (candidates {x,y,z,|x|^2}, masses,
-// cell-order indices, slot table), carved from the cell kernel's dynamic
-// shared memory once its CTA-sized cells are done.
-constexpr int kTinyWarpBytes =
-    (kTinyBuf + kPad) * (16 + 4 + 4) + (int)((sizeof(TinySlots) + 15) / 16 * 16);
+// Bytes of a warp's tiny-cell buffers (staged groups, cell-order indices, slot
+// table), carved from the cell kernel's dynamic shared memory once its
+// CTA-sized cells are done.
+constexpr int kTinyWarpBytes = staged_floats(kTinyBuf) * 4 + (kTinyBuf + kPad) * 4 +
+                               (int)((sizeof(TinySlots) + 15) / 16 * 16);
 
 template <typename Out>
-__device__ __forceinline__ void tiny_phase_fwd(const GridDev& g, unsigned char* buf,
-                                               unsigned* __restrict__ M, int lane, Out out,
-                                               unsigned long long& inter, int& guards) {
-  float4* Sx = reinterpret_cast<float4*>(buf);
-  float* Sm = reinterpret_cast<float*>(Sx + kTinyBuf + kPad);
-  int* Sj = reinterpret_cast<int*>(Sm + kTinyBuf + kPad);
+__device__ __forceinline__ void tiny_phase_fwd(const GridDev& g, unsigned char* buf, int lane,
+                                               Out out, unsigned long long& inter, int& guards) {
+  float* S = reinterpret_cast<float*>(buf);
+  int* Sj = reinterpret_cast<int*>(S + staged_floats(kTinyBuf));
   TinySlots& ts = *reinterpret_cast<TinySlots*>(Sj + kTinyBuf + kPad);
   const Slot self = slot_info(kSelfSlot);
   const int nt = *g.n_ycells;
@@ -470,7 +563,10 @@ __device__ __forceinline__ void tiny_phase_fwd(const GridDev& g, unsigned char* 
     const int total = tiny_slots(g, a, lane, ts);
     LaneI L;
     lane_init(L);
-    if (lane < na) lane_set(L, g, B, self, ca + lane, g.xm[ca + lane], g.hs[ca + lane]);
+    if (lane < na) {
+      const float4 xm = g.xm[ca + lane];
+      lane_set(L, B, g.gamma, self, ca + lane, make_float4(xm.x, xm.y, xm.z, g.hs[ca + lane]));
+    }
     int q = 0;  // slot of this lane's next staged candidate (non-decreasing)
     for (int f0 = 0; f0 < total; f0 += kTinyBuf) {
       const int len = min(kTinyBuf, total - f0);
@@ -479,20 +575,20 @@ __device__ __forceinline__ void tiny_phase_fwd(const GridDev& g, unsigned char* 
         while (ts.off[q + 1] <= f) q++;
         float sx, sy, sz;
         const int sj = tiny_candidate(g, ts, q, f, edge, sx, sy, sz);
-        const float4 xj = g.xm[sj];
-        const float x = xj.x + sx, y = xj.y + sy, z = xj.z + sz;
-        Sx[e] = make_float4(x, y, z, fmaf(x, x, fmaf(y, y, z * z)));
-        Sm[e] = xj.w;
+        put_staged(S, e, g.xm[sj], sx, sy, sz);
         Sj[e] = sj;
       }
       __syncwarp();
       auto jidx = [&](int j) { return Sj[j]; };
-      sweep_fwd(L, Sx, Sm, 0, len, M, lane, g, B, jidx, guards);
+      sweep_fwd(L, smem_addr(S), 0, len, g, B, jidx, guards);
       __syncwarp();  // the buffers are rewritten next
     }
     if (lane < na) {
-      out(a, ca + lane, L);
-      inter += (unsigned long long)(L.n - 1);
+      float rho, D;
+      int n;
+      lane_sums(L, rho, D, n);
+      out(a, ca + lane, rho, D, n);
+      inter += (unsigned long long)(n - 1);
     }
   }
 }
@@ -500,17 +596,20 @@ __device__ __forceinline__ void tiny_phase_fwd(const GridDev& g, unsigned char* 
 // ---- cell-centric kernel ------------------------------------------------------------
 
 constexpr int kCellWarps = kCellThreads / 32;
-// per-CTA shared memory that does not depend on the cell: the warps' hit masks
-constexpr int kCellFixedSmem = kCellWarps * kMaskChunks * 32 * 4;
-static_assert(kCellWarps * kTinyWarpBytes <= kCellSmemFor[4] - kCellFixedSmem,
+static_assert(kCellWarps * kTinyWarpBytes <= kCellSmemFor[4],
               "the tiny-cell buffers fit the smallest dynamic shared memory");
-constexpr int kCellElemJ = 20;  // staged bytes per particle of a window: {x,y,z,|x|^2}, m
-constexpr int kCellElemA = 40;  // bytes per particle of the cell
+// Staged bytes per candidate of a window (groups of four, with slack), bytes
+// per particle of the cell ({x', y', z', h} and three fixed-point sums) and per
+// entry of the slots' particle lists (16-bit index).
+constexpr int kCellElemJ = 20;
+constexpr int kCellElemA = 36;
+constexpr int kCellElemI = 2;
 
 struct CellShared {
   int I[kNSlot], J0[kNSlot];
   int off[kNSlot + 1];      // staged segment of the q-th slot of c_slot_order
   int runs[kNSlot + 1];     // prefix of run counts, same order
+  int ioff[kNSlot + 1];     // the slot's list of particles of a, same order
   int nb_[kNSlot], cb_[kNSlot];
   float offv[kNSlot];
   int cell, item_next;
@@ -518,9 +617,9 @@ struct CellShared {
 
 // projection of a staged particle in the frame of slot (k, s): the same FP32
 // expression the sort used for `dist`, so the values are bit-identical
-__device__ __forceinline__ float staged_proj(float4 x, float ux, float uy, float uz, int s,
+__device__ __forceinline__ float staged_proj(unsigned a, float ux, float uy, float uz, int s,
                                              float off) {
-  return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
+  return s * fmaf(-lds1(a), ux, fmaf(-lds1(a + kOffY), uy, -lds1(a + kOffZ) * uz)) + off;
 }
 
 __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, float* __restrict__ rho,
@@ -532,8 +631,7 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncells = *g.n_ccells;
   const float munit = (float)(16.0 / 3.14159265358979323846 * kFixInv);
-  unsigned* Mw = reinterpret_cast<unsigned*>(dsm) + warp * kMaskChunks * 32;
-  float4* var = dsm + kCellFixedSmem / 16;
+  float4* var = dsm;
   int guards = 0;
   unsigned long long inter = 0;
   for (;;) {
@@ -554,6 +652,7 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
       cs.J0[tid] = p.y;
       cs.off[tid + 1] = p.z - p.y;
       cs.runs[tid + 1] = (p.x + 31) >> 5;
+      cs.ioff[tid + 1] = p.x;
       const int b = neighbour_cell(g, a, o);
       cs.nb_[tid] = g.cell_count[b];
       cs.cb_[tid] = g.cell_start[b];
@@ -563,6 +662,7 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
     if (tid == 0) {
       cs.off[0] = 0;
       cs.runs[0] = 0;
+      cs.ioff[0] = 0;
       cs.item_next = 0;
     }
     __syncthreads();
@@ -570,21 +670,22 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
       for (int q = 0; q < kNSlot; q++) {
         cs.off[q + 1] += cs.off[q];
         cs.runs[q + 1] += cs.runs[q];
+        cs.ioff[q + 1] += cs.ioff[q];
       }
     }
     __syncthreads();
     const int total = cs.off[kNSlot];
-    // variable part: kCellElemJ (total + kPad) + kCellElemA na bytes (checked by the plan)
-    float4* Sx = var;                                          // [total + kPad]
-    float4* Ax = Sx + total + kPad;                            // [na]
-    long long* acc_r = reinterpret_cast<long long*>(Ax + na);  // [na]
-    long long* acc_d = acc_r + na;                             // [na]
-    float* Sm = reinterpret_cast<float*>(acc_d + na);          // [total + kPad]
-    float* Ah = Sm + total + kPad;                             // [na]
-    int* acc_n = reinterpret_cast<int*>(Ah + na);              // [na]
-    // stage the 27 windows in sorted order, and cell a in cell order
-    // (synchronous loads, three lookups in flight per thread: measured 2 %
-    // faster here than cp.async, which the adjoint kernel uses)
+    const int sumI = cs.ioff[kNSlot];
+    // variable part (checked by the plan): kCellElemJ (total + kPad + 4) +
+    // kCellElemA na + kCellElemI sumI bytes
+    float* S = reinterpret_cast<float*>(var);                          // staged groups
+    float4* Ax = reinterpret_cast<float4*>(S + staged_floats(total));  // [na] {x', y', z', h}
+    long long* acc_r = reinterpret_cast<long long*>(Ax + na);          // [na]
+    long long* acc_d = acc_r + na;                                     // [na]
+    int* acc_n = reinterpret_cast<int*>(acc_d + na);                   // [na]
+    uint16_t* SI = reinterpret_cast<uint16_t*>(acc_n + na);            // [sumI]
+    // stage the 27 windows in sorted order (synchronous loads, three lookups
+    // in flight per thread), the slots' particle lists of a, and cell a
     stage_flat<3>(
         cs.off, total, tid, kCellThreads,
         [&](int f, int q) {
@@ -594,13 +695,18 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
           return cb + (int)g.perm[(size_t)sl.k * g.n + cb + pos];
         },
         [&](int sj) { return g.xm[sj]; },
-        [&](int f, float4 x) {
-          Sx[f] = staged(x);
-          Sm[f] = x.w;
-        });
+        [&](int f, int, float4 x) { put_staged(S, f, x, 0.0f, 0.0f, 0.0f); });
+    for (int t = tid, q = 0; t < sumI; t += kCellThreads) {
+      while (cs.ioff[q + 1] <= t) q++;
+      const int o = c_slot_order[q];
+      const Slot sl = slot_info(o);
+      const int p = t - cs.ioff[q];
+      const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
+      SI[t] = g.perm[(size_t)sl.k * g.n + ca + pos_i];
+    }
     for (int t = tid; t < na; t += kCellThreads) {
-      Ax[t] = g.xm[ca + t];
-      Ah[t] = g.hs[ca + t];
+      const float4 xm = g.xm[ca + t];
+      Ax[t] = make_float4(xm.x, xm.y, xm.z, g.hs[ca + t]);
       acc_r[t] = 0;
       acc_d[t] = 0;
       acc_n[t] = 0;
@@ -624,13 +730,17 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
       float d_lo = 3.0e38f, d_hi = -3.0e38f;
       int il = 0;
       if (p < cs.I[q]) {
-        const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
-        const size_t kb = (size_t)sl.k * g.n + ca + pos_i;
-        il = g.perm[kb];
-        const float di = sl.s * g.dist[kb];
-        const float h = Ah[il];
-        lane_set(L, g, B, sl, ca + il, Ax[il], h);
-        const float H = g.gamma * h;
+        il = SI[cs.ioff[q] + p];
+        const float4 xh = Ax[il];
+        float di;
+        if (g.moved) {  // windows from the sort's projections
+          const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
+          di = sl.s * g.dist[(size_t)sl.k * g.n + ca + pos_i];
+        } else {
+          di = sl.s * project(xh, ux, uy, uz);
+        }
+        lane_set(L, B, g.gamma, sl, ca + il, xh);
+        const float H = g.gamma * xh.w;
         d_lo = di - H - padw;
         d_hi = di + H + padw;
       }
@@ -640,9 +750,10 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
       const int J0q = cs.J0[q], nbq = cs.nb_[q], cbq = cs.cb_[q];
       // after pv_update_positions the staged positions are no longer in sorted
       // order: the window searches then read the sort's projections
+      const unsigned Sa = smem_addr(S);
       auto proj = [&](int e) {  // projection of staged element e, as sorted
         return g.moved ? proj_asc(g, sl.k, sl.s, cbq, nbq, J0q + e, offv)
-                       : staged_proj(Sx[s0 + e], ux, uy, uz, sl.s, offv);
+                       : staged_proj(Sa + cand_off(s0 + e), ux, uy, uz, sl.s, offv);
       };
       const int lo = s0 + ((o == kSelfSlot)
                                ? warp_first_true(len, lane, [&](int e) { return proj(e) > w_lo; })
@@ -652,13 +763,16 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
       auto jidx = [&](int j) {
         return cbq + (int)g.perm[kbq + order_pos(sl.s, J0q + j - s0, nbq)];
       };
-      sweep_fwd(L, Sx, Sm, lo, hi, Mw, lane, g, B, jidx, guards);
-      if (p < cs.I[q] && L.n > 0) {
+      sweep_fwd(L, smem_addr(S), lo, hi, g, B, jidx, guards);
+      float prho, pD;
+      int pn;
+      lane_sums(L, prho, pD, pn);
+      if (p < cs.I[q] && pn > 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&acc_r[il]),
-                  (unsigned long long)__float2ll_rn(L.rho * (float)kFixScale));
+                  (unsigned long long)__float2ll_rn(prho * (float)kFixScale));
         atomicAdd(reinterpret_cast<unsigned long long*>(&acc_d[il]),
-                  (unsigned long long)__float2ll_rn(L.D * (float)kFixScale));
-        atomicAdd(&acc_n[il], L.n);
+                  (unsigned long long)__float2ll_rn(pD * (float)kFixScale));
+        atomicAdd(&acc_n[il], pn);
       }
     }
     __syncthreads();
@@ -671,16 +785,16 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
   // then the tiny cells, one per warp, in the dynamic shared memory that the
   // cells no longer use (at least kCellWarps * kTinyWarpBytes of it)
   tiny_phase_fwd(
-      g, reinterpret_cast<unsigned char*>(var) + warp * kTinyWarpBytes, Mw, lane,
-      [&](int a, int s, const LaneI& L) {
+      g, reinterpret_cast<unsigned char*>(var) + warp * kTinyWarpBytes, lane,
+      [&](int a, int s, float prho, float pD, int pn) {
         const int i = g.orig[s];
         const float h = g.hs[s];
         const float H = g.gamma * h;
         const float c = (float)(16.0 / 3.14159265358979323846) * g.m_max[g.cell_box[a]] /
                         (H * H * H);
-        rho[i] = c * L.rho;
-        if (drho_dh) drho_dh[i] = -(c / h) * L.D;
-        if (n_ngb) n_ngb[i] = L.n - 1;  // the self pair j = i
+        rho[i] = c * prho;
+        if (drho_dh) drho_dh[i] = -(c / h) * pD;
+        if (n_ngb) n_ngb[i] = pn - 1;  // the self pair j = i
       },
       inter, guards);
   for (int s = 16; s > 0; s >>= 1) {
@@ -696,11 +810,9 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
 // ---- task kernel (cells too dense for the cell-centric kernel) ---------------------
 
 __global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
-  __shared__ float4 s_x[kTileJ + kPad];
-  __shared__ float s_m[kTileJ + kPad];
+  __shared__ __align__(16) float s_S[staged_floats(kTileJ)];
   __shared__ float s_d[kTileJ];
   __shared__ int s_j[kTileJ + kPad];
-  __shared__ unsigned s_mask[kBlkI / 32][kMaskChunks * 32];
   __shared__ int s_task;
   if (*g.flags) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -731,7 +843,8 @@ __global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
       const int pos_i = (o == kSelfSlot) ? p : order_pos(sl.s, na - 1 - p, na);
       const int si = ca + g.perm[kbase + ca + pos_i];
       const float h = g.hs[si];
-      lane_set(L, g, B, sl, si, g.xm[si], h);
+      const float4 xm = g.xm[si];
+      lane_set(L, B, g.gamma, sl, si, make_float4(xm.x, xm.y, xm.z, h));
       const float di = sl.s * g.dist[kbase + ca + pos_i];
       const float H = g.gamma * h;
       d_lo = di - H - window_pad(g, B, g.cell_box[a]);
@@ -743,9 +856,7 @@ __global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
       for (int e = threadIdx.x; e < len; e += blockDim.x) {
         const int pos_j = order_pos(sl.s, j0 + e, nb);
         const int jl = g.perm[kbase + cb + pos_j];
-        const float4 xj = g.xm[cb + jl];
-        s_x[e] = staged(xj);
-        s_m[e] = xj.w;
+        put_staged(s_S, e, g.xm[cb + jl], 0.0f, 0.0f, 0.0f);
         s_d[e] = sl.s * g.dist[kbase + cb + pos_j] + off;
         s_j[e] = cb + jl;
       }
@@ -754,17 +865,20 @@ __global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
         const int lo = (o == kSelfSlot) ? upper_bound_f(s_d, len, w_lo) : 0;
         const int hi = lower_bound_f(s_d, len, w_hi);
         auto jidx = [&](int j) { return s_j[j]; };
-        sweep_fwd(L, s_x, s_m, lo, hi, s_mask[warp], lane, g, B, jidx, guards);
+        sweep_fwd(L, smem_addr(s_S), lo, hi, g, B, jidx, guards);
       }
       __syncthreads();
     }
-    if (valid && L.n > 0) {
+    float prho, pD;
+    int pn;
+    lane_sums(L, prho, pD, pn);
+    if (valid && pn > 0) {
       atomicAdd(reinterpret_cast<unsigned long long*>(&g.acc[L.si]),
-                (unsigned long long)__float2ll_rn(L.rho * (float)kFixScale));
+                (unsigned long long)__float2ll_rn(prho * (float)kFixScale));
       atomicAdd(reinterpret_cast<unsigned long long*>(&g.acc[(size_t)g.n + L.si]),
-                (unsigned long long)__float2ll_rn(L.D * (float)kFixScale));
+                (unsigned long long)__float2ll_rn(pD * (float)kFixScale));
       atomicAdd(reinterpret_cast<unsigned long long*>(&g.acc[2 * (size_t)g.n + L.si]),
-                (unsigned long long)L.n);
+                (unsigned long long)pn);
     }
   }
   for (int s = 16; s > 0; s >>= 1) guards += __shfl_xor_sync(0xffffffffu, guards, s);
@@ -972,12 +1086,12 @@ __global__ void k_count_classes(GridDev g) {
 }  // namespace
 
 cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
-                        cudaStream_t st) {
+                        int elem_i, cudaStream_t st) {
   const int nthr = g.ncell * kNSlot;
   k_plan_slots<<<(nthr + 255) / 256, 256, 0, st>>>(g, wide);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_plan_cells<<<(g.ncell + 127) / 128, 128, 0, st>>>(g, smem_budget, elem_j, elem_a);
+  k_plan_cells<<<(g.ncell + 127) / 128, 128, 0, st>>>(g, smem_budget, elem_j, elem_a, elem_i);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // one warp per (task cell, slot): enough warps that the big cells' many
   // (cell, slot) pairs do not queue behind each other
@@ -998,8 +1112,7 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
                                        kCellSmemFor[1], st);
   if (e != cudaSuccess) return e;
   const int smem = kCellSmemFor[ctas_per_sm];
-  if ((e = launch_plan(g, 0, smem - kCellFixedSmem, kCellElemJ, kCellElemA,
-                       st)) != cudaSuccess)
+  if ((e = launch_plan(g, 0, smem, kCellElemJ, kCellElemA, kCellElemI, st)) != cudaSuccess)
     return e;
   if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
   k_density_cells<<<num_sms * ctas_per_sm, kCellThreads, smem, st>>>(g, rho, drho_dh, n_ngb);

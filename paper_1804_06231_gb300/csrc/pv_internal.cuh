@@ -359,20 +359,22 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // stays full across window boundaries), follows its window index forward
 // instead of searching for it, and keeps U elements in flight: index(f, q)
 // for U elements (the sorted-order lookups), then fetch(sj) for the U (the
-// particle data), then put(f, value).
+// particle data), then put(f, q, value).
 template <int U, typename Index, typename Fetch, typename Put>
 __device__ __forceinline__ void stage_flat(const int* off, int total, int tid, int nthr,
                                            Index index, Fetch fetch, Put put) {
   int q = 0;
   for (int f0 = tid; f0 < total; f0 += U * nthr) {
-    int sj[U];
+    int sj[U], sq[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int f = f0 + u * nthr;
       sj[u] = -1;
+      sq[u] = 0;
       if (f < total) {
         while (off[q + 1] <= f) q++;
         sj[u] = index(f, q);
+        sq[u] = q;
       }
     }
     decltype(fetch(0)) v[U];
@@ -381,7 +383,7 @@ __device__ __forceinline__ void stage_flat(const int* off, int total, int tid, i
       if (sj[u] >= 0) v[u] = fetch(sj[u]);
 #pragma unroll
     for (int u = 0; u < U; u++)
-      if (sj[u] >= 0) put(f0 + u * nthr, v[u]);
+      if (sj[u] >= 0) put(f0 + u * nthr, sq[u], v[u]);
   }
 }
 
@@ -463,9 +465,10 @@ cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, con
 cudaError_t launch_update(const GridDev& g, const double* pos, const float* h, cudaStream_t st);
 // Per-(cell, slot) plan, then per-cell routing: cells whose staged windows fit
 // `smem_budget` bytes (elem_j bytes per staged particle, elem_a per particle
-// of the cell) go to the cell-centric kernel, the others are split into tasks.
+// of the cell, elem_i per entry of the slots' lists of reaching particles) go
+// to the cell-centric kernel, the others are split into tasks.
 cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
-                        cudaStream_t st);
+                        int elem_i, cudaStream_t st);
 int64_t max_tasks_for(int64_t n, int64_t ncell);
 // ctas_per_sm: resident CTAs of the cell-centric sweep kernel per SM (1..4
 // forward, 1..3 adjoint); it sets the kernel's shared memory and so which
