@@ -39,6 +39,12 @@ WORKLOAD = "uniform N=1048576, 15^3 cells, h=1.2348 N^-1/3 U(0.9,1.1), sort+dens
 # the union the three gradient FMAs (6).
 FWD_FLOP_CAND, FWD_FLOP_PAIR = 9, 23
 BWD_FLOP_CAND, BWD_FLOP_OWN, BWD_FLOP_TRANS, BWD_FLOP_PAIR = 10, 24, 11, 6
+# The same work in algorithmic FP32-pipe instructions (one FMA = one
+# instruction): a distance test is 7 (3 sub, 1 mul, 2 fma, 1 compare), the
+# kernel terms of a pair in range 15; the adjoint evaluates about twice the
+# per-pair terms (own and transposed), 30.
+FWD_INST_CAND, FWD_INST_PAIR = 7, 15
+BWD_INST_CAND, BWD_INST_PAIR = 7, 30
 FP32_LANES_PER_SM = 128
 CSRC = os.path.join(ROOT, "paper_1804_06231_gb300", "csrc")
 # sweep kernel -> (ncu summary under profiles/, sources whose hash it was taken on)
@@ -225,7 +231,39 @@ def timed_steps(step, flush, K: int, W: int = 3) -> float:
     return statistics.median(ts)
 
 
-def workload_extras(dev, flush, K: int = 5) -> dict:
+def phase_times(grid, step_args, flush, K: int) -> tuple:
+    """Median CUDA-event times (ms) of sort, density and backward over K steps
+    (after 2 warm-ups, L2 flushed before each step), with the sweep kernels'
+    own times from the grid's event hooks."""
+    import torch
+    pos, h, m, gr, gd, rho, D, nn, gp, gh = step_args
+    for _ in range(2):
+        grid.sort(pos, h, m)
+        grid.density(rho, D, nn)
+        grid.backward(gr, gd, gp, gh)
+    stream = torch.cuda.current_stream()
+    grid.time_sweeps(True)
+    ts = []
+    for _ in range(K):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        grid.sort(pos, h, m)
+        e[1].record(stream)
+        grid.density(rho, D, nn)
+        e[2].record(stream)
+        grid.backward(gr, gd, gp, gh)
+        e[3].record(stream)
+        e[3].synchronize()
+        ts.append([e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3]),
+                   e[0].elapsed_time(e[3])])
+    k_dens, k_bwd = grid.sweep_times()
+    grid.time_sweeps(False)
+    med = [statistics.median(col) for col in zip(*ts)]
+    return med[0], med[1], med[2], med[3], k_dens, k_bwd
+
+
+def workload_extras(dev, flush, probe: dict, peak_derived: float, K: int = 5) -> dict:
     """The other two throughput workloads of the method: 4,194,304 clustered
     particles on the finest grid (one box), and the 64-box mix as one batched
     grid, as 64 separate grids, and as a CUDA-graph replay of the batched step.
@@ -259,11 +297,28 @@ def workload_extras(dev, flush, K: int = 5) -> dict:
         tr = tune.autotune(g, gr, gd, reps=3)
         t = timed_steps(step, flush, K)
         inter = g.stats().interactions
+        cand = g.count_candidates()
+        stc = g.stats()
+        t_sort, t_dens, t_bwd, t_step, k_dens, k_bwd = phase_times(
+            g, (pos, h, m, gr, gd, rho, D, nn, gp, gh), flush, K)
+        fw, bw = sweep_work(box.n, cand, inter, stc.candidates_adjoint, stc.pairs_adjoint)
+        # the dense cells run on the task kernels: the roofline covers the
+        # whole pass (plan, cell-centric, warp-per-cell and task kernels)
         out["clustered_4m"] = {
             "workload": f"clustered N={box.n}, {box.nc}^3 cells, 64 Gaussians + 20% uniform",
             "ms_per_step": t, "value": inter / (t * 1e-3), "unit": UNIT,
             "launch_shape": [tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"]],
-            "max_cell_count": g.stats().max_cell_count}
+            "max_cell_count": stc.max_cell_count,
+            "breakdown_ms": {"sort": t_sort, "density": t_dens, "backward": t_bwd,
+                             "step": t_step, "density_cell_kernel": k_dens,
+                             "backward_cell_kernel": k_bwd},
+            "fwd_bwd_over_fwd": t_step / (t_sort + t_dens),
+            "candidates": cand, "interactions": inter,
+            "candidates_adjoint": stc.candidates_adjoint, "pairs_adjoint": stc.pairs_adjoint,
+            "roofline_density_pass": sweep_roofline("pv_density (all its kernels)", fw[0], fw[1],
+                                                    t_dens, probe, peak_derived),
+            "roofline_adjoint_pass": sweep_roofline("pv_density_backward (all its kernels)",
+                                                    bw[0], bw[1], t_bwd, probe, peak_derived)}
     del pos, h, m, gr, gd, rho, D, nn, gp, gh
     torch.cuda.empty_cache()
 
@@ -314,6 +369,66 @@ def workload_extras(dev, flush, K: int = 5) -> dict:
         "value": inter / (t_g * 1e-3), "unit": UNIT,
         "launch_shape": [tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"]]}
     return out
+
+
+def fp32_probe(dev, props) -> dict:
+    """FP32 peak of this GPU, measured: pv_fp32_probe with 8 CTAs of 256
+    threads per SM, each thread running 8 independent FMA chains, timed with
+    CUDA events (best of 5 launches after 2 warm-ups), as scalar FFMA and as
+    packed fma.rn.f32x2."""
+    import torch
+    from paper_1804_06231_gb300.pv import pv_fp32_probe
+    threads = props.multi_processor_count * 8 * 256
+    sink = torch.empty(threads, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    iters = 16384
+    out = {"threads": threads, "iters": iters, "chains_per_thread": 8}
+    for packed, key in ((0, "ffma_tflops"), (1, "ffma2_tflops")):
+        best = 0.0
+        for rep in range(7):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            flops = pv_fp32_probe(packed, iters, sink.data_ptr(), threads, stream.cuda_stream)
+            b.record(stream)
+            b.synchronize()
+            if rep >= 2:
+                best = max(best, flops / (a.elapsed_time(b) * 1e-3) / 1e12)
+        out[key] = best
+    out["ffma_inst_per_s"] = out["ffma_tflops"] * 1e12 / 2.0
+    return out
+
+
+def sweep_work(n: int, candidates: int, interactions: int, cand_adj: int, pairs_adj: int):
+    """(flops, FP32 instructions) of the density pass and of the adjoint pass:
+    window candidates and in-range pairs (j = i included) for the forward,
+    adjoint candidates and pairs for the adjoint."""
+    pairs = interactions + n
+    fwd = (FWD_FLOP_CAND * candidates + FWD_FLOP_PAIR * pairs,
+           FWD_INST_CAND * candidates + FWD_INST_PAIR * interactions)
+    bwd = (BWD_FLOP_CAND * cand_adj + (BWD_FLOP_OWN + BWD_FLOP_TRANS) * interactions
+           + BWD_FLOP_PAIR * (pairs_adj - n),
+           BWD_INST_CAND * cand_adj + BWD_INST_PAIR * interactions)
+    return fwd, bwd
+
+
+def sweep_roofline(kernel: str, flops: float, insts: float, ms: float, probe: dict,
+                   derived_tflops: float, traffic=None) -> dict:
+    """FP32 roofline of a sweep: algorithmic FP32 work per launch over its
+    CUDA-event time, against the FFMA peak measured by pv_fp32_probe in this
+    run; `instructions` is the same in FP32 instructions (an FMA counts once)."""
+    a = flops / (ms * 1e-3) / 1e12
+    peak = probe["ffma_tflops"]
+    ai = insts / (ms * 1e-3) / 1e12
+    pi = probe["ffma_inst_per_s"] / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": a, "peak": peak, "unit": "TFLOP/s",
+            "frac": a / peak, "traffic": traffic, "flop_per_launch": flops,
+            "ms_per_launch": ms,
+            "peak_source": "pv_fp32_probe: scalar FFMA chains on every SM, measured in this run "
+                           "(of measured)",
+            "peak_derived_tflops": derived_tflops,
+            "instructions": {"achieved": ai, "peak": pi, "unit": "T FP32 inst/s",
+                             "frac": ai / pi, "inst_per_launch": insts}}
 
 
 def raw_ceiling(dev, props, peak_tflops: float) -> dict:
@@ -666,23 +781,18 @@ def main():
     # sweep is the dominant kernel of the step
     peaks = measured_peaks()
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    peak_src = f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
+    peak_derived = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    probe = fp32_probe(dev, props)
+    peak_tflops = probe["ffma_tflops"]
     default_size = not (args.particles or args.cells) and args.workload == "uniform1m"
-    pairs = interactions + n  # in-range pairs evaluated, including j = i
-    fwd_flops = FWD_FLOP_CAND * candidates + FWD_FLOP_PAIR * pairs
-    bwd_flops = (BWD_FLOP_CAND * cand_adj + (BWD_FLOP_OWN + BWD_FLOP_TRANS) * interactions
-                 + BWD_FLOP_PAIR * (pairs_adj - n))
+    fw, bw = sweep_work(n, candidates, interactions, cand_adj, pairs_adj)
 
-    def roof(kernel, flops, ms):
-        a = flops / (ms * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": kernel, "achieved": a, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": a / peak_tflops,
-                "traffic": profiled_traffic(kernel) if default_size else None,
-                "flop_per_launch": flops, "ms_per_launch": ms, "peak_source": peak_src}
+    def roof(kernel, work, ms):
+        return sweep_roofline(kernel, work[0], work[1], ms, probe, peak_derived,
+                              profiled_traffic(kernel) if default_size else None)
 
-    roofline = roof("k_backward_cells", bwd_flops, k_bwd)
-    roofline_fwd = roof("k_density_cells", fwd_flops, k_dens)
+    roofline = roof("k_backward_cells", bw, k_bwd)
+    roofline_fwd = roof("k_density_cells", fw, k_dens)
 
     extras = None
     if rank == 0 and ws == 1 and not args.no_extras and default_size:
@@ -693,7 +803,7 @@ def main():
                   "sort_reuse": sort_reuse(grid, box, pos, h, m_uniform, flush,
                                            lambda: grid.density(rho, drho, nngb),
                                            lambda: grid.backward(g_rho, g_d, gpos, gh), dev)}
-        extras.update(workload_extras(dev, flush))
+        extras.update(workload_extras(dev, flush, probe, peak_derived))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -741,6 +851,7 @@ def main():
             "candidates_adjoint": cand_adj, "pairs_adjoint": pairs_adj,
             "candidates_per_interaction": candidates / max(interactions, 1),
             "guard_pairs": st.guard_pairs, "wall_s_timed_loop": wall,
+            "fp32_probe": probe,
         }
         if extras:
             line.update(extras)

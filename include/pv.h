@@ -59,13 +59,14 @@ typedef enum {
   PV_ERR_TOO_LARGE = 7         /* more than 2^31 - 1 particles or cells */
 } pv_status;
 
-/* Bits of pv_stats.device_flags (set by the kernels of pv_sort_cells and
-   pv_update_positions; cleared by pv_sort_cells). */
+/* Bits of pv_stats.device_flags (set by the kernels of pv_sort_cells,
+   pv_update_positions and pv_density_backward; cleared by pv_sort_cells). */
 #define PV_FLAG_SUPPORT_EXCEEDS_CELL 1u /* gamma h_i > L/nc for some particle */
 #define PV_FLAG_BAD_POSITION 2u         /* non-finite position coordinate */
 #define PV_FLAG_BAD_SMOOTHING 4u        /* h_i not finite or not > 0, or m_i not finite */
 #define PV_FLAG_CELL_OVERFLOW 8u        /* a cell holds more than PV_MAX_CELL_COUNT particles */
 #define PV_FLAG_SKIN_EXCEEDED 16u       /* pv_update_positions: H_max + 2 x displacement > edge */
+#define PV_FLAG_BAD_GRADIENT 32u        /* pv_density_backward: a non-finite upstream gradient */
 
 /* Largest number of particles one cell may hold (cell-local indices are 16-bit). */
 #define PV_MAX_CELL_COUNT 65535
@@ -150,7 +151,11 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
                                              + m_i (g_j dW/dr(r,H_j) + k_j d2W/dhdr(r,h_j)) [r < H_j] ]
    (g = g_rho, k = g_drho_dh), computed by re-sweeping the same sorted cell
    pairs as a gather (the transposed term is a second gather, no atomics on
-   the outputs).  Requires a prior pv_sort_cells.  Masses are constants. */
+   the outputs).  Requires a prior pv_sort_cells.  Masses are constants.
+   Deterministic: partial sums are combined in fixed point (scaled by bounds
+   of the terms, per cell and per box), so the result does not depend on
+   scheduling.  A non-finite g_rho or g_drho_dh latches PV_FLAG_BAD_GRADIENT
+   and leaves g_pos and g_h untouched. */
 pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drho_dh,
                               float* g_pos, float* g_h, void* stream);
 
@@ -235,6 +240,20 @@ pv_status pv_grid_set_slot_mask(pv_grid* g, uint32_t mask);
    PV_ERR_CUDA (launch failure). */
 pv_status pv_raw_interactions(const float* xi, int64_t n_i, const float* xj, int64_t n_j,
                               float H, int32_t reps, float* out, void* stream);
+
+/* FP32 throughput probe (a measurement aid; the paper has no counterpart):
+   queues one kernel of `threads` threads (a multiple of 256; the caller sizes
+   it to fill the GPU), each running 8 independent dependent chains of
+   4 x iters fused multiply-adds, as scalar FFMA (packed = 0) or as packed
+   fma.rn.f32x2 pairs (packed != 0), and writing one float per thread to the
+   device array sink[threads].  *flops (host) receives the FP32 operations of
+   the launch (an FMA counts 2).  The caller times the launch on `stream`
+   (CUDA events); flops / time is the FP32 peak that the sweep kernels' FP32
+   work is compared with.  Errors: PV_ERR_INVALID_ARGUMENT (iters < 1,
+   threads negative or not a multiple of 256, NULL flops, NULL sink with
+   threads > 0), PV_ERR_TOO_LARGE, PV_ERR_CUDA (launch failure). */
+pv_status pv_fp32_probe(int32_t packed, int32_t iters, float* sink, int64_t threads,
+                        double* flops, void* stream);
 
 /* Per-kernel timing of the two sweeps (a measurement aid; the paper has no
    counterpart).  With enable != 0, every later pv_density and

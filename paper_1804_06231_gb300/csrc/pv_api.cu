@@ -179,6 +179,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_TRY(dev_alloc(g, &d.gacc, 5 * N));
   PV_TRY(dev_alloc(g, &d.bx, N));
   PV_TRY(dev_alloc(g, &d.ba, N));
+  PV_TRY(dev_alloc(g, &d.bwd_cmax, C));
   PV_TRY(dev_alloc(g, &d.plan, (size_t)pv::kNSlot * C));
   PV_TRY(dev_alloc(g, &d.ccells, C));
   PV_TRY(dev_alloc(g, &d.tcells, C));
@@ -410,6 +411,16 @@ pv_status pv_raw_interactions(const float* xi, int64_t n_i, const float* xj, int
                                  reinterpret_cast<const float4*>(xj), (int)n_j, H, reps,
                                  reinterpret_cast<float2*>(out),
                                  static_cast<cudaStream_t>(stream)));
+  return PV_OK;
+}
+
+pv_status pv_fp32_probe(int32_t packed, int32_t iters, float* sink, int64_t threads,
+                        double* flops, void* stream) {
+  if (iters < 1 || threads < 0 || threads % 256 || !flops || (threads > 0 && !sink))
+    return PV_ERR_INVALID_ARGUMENT;
+  if (threads / 256 > 0x7fffffff) return PV_ERR_TOO_LARGE;
+  PV_CUDA(pv::launch_fp32_probe(packed != 0, iters, sink, threads, flops,
+                                static_cast<cudaStream_t>(stream)));
   return PV_OK;
 }
 

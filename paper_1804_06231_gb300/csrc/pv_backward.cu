@@ -25,11 +25,13 @@
 // Mapping: the cell-centric kernel of the forward pass (one CTA per cell, 27
 // staged windows, warps pulling (slot, run) items, candidates pre-filtered 8
 // at a time into bit masks), with both the own and the transposed cut-off in
-// the pre-filter; per-particle sums in FP32 shared-memory accumulators (one
-// addition per particle and work item).  A staged particle takes 32 bytes
-// ({x, y, z, H^2 + guard} and {m, G', K, H}), so three CTAs fit an SM.  Cells
-// whose windows exceed the shared-memory budget run as tasks (cell, slot,
-// block of 128 particles) with FP64 global accumulators.
+// the pre-filter; per-particle sums in 32-bit fixed-point shared-memory
+// accumulators (one integer addition per particle and work item, so the
+// result does not depend on which warp took which item).  A staged particle
+// takes 32 bytes ({x, y, z, H^2 + guard} and {m, G', K, H}), so three CTAs fit
+// an SM.  Cells whose windows exceed the shared-memory budget run as tasks
+// (cell, slot, block of 128 particles) with 64-bit fixed-point global
+// accumulators.
 #include <cuda_runtime.h>
 
 #include "pv_internal.cuh"
@@ -46,7 +48,7 @@ constexpr int kCellThreads = 256;
 constexpr int kCellSmemFor[4] = {0, 200 * 1024, 110 * 1024, 72 * 1024};
 constexpr int kPad = 32;
 constexpr int kElemJ = 32;   // staged bytes per particle of a window: {x,y,z,E}, {m,G,K,H}
-constexpr int kElemA = 20;   // bytes per particle of the cell: five FP32 sums
+constexpr int kElemA = 32;   // bytes per particle of the cell: 3 x 64-bit + 2 x 32-bit fixed point
 
 __constant__ int8_t c_border[kNSlot] = {13, 4,  10, 12, 14, 16, 22, 1,  3,  5,  7,  9, 11, 15,
                                         17, 19, 21, 23, 25, 0,  2,  6,  8,  18, 20, 24, 26};
@@ -70,23 +72,66 @@ __device__ __forceinline__ TaskB decode_b(int4 t) {
 // sweep, in the form the sweeps stage them: bx = {x', y', z', E = H^2 +
 // guard} and ba = {m / m_max, G' = G - 4K, K, H} with G = g/H^5 and
 // K = k/(h H^5).
+// A non-finite upstream gradient latches PV_FLAG_BAD_GRADIENT (the sweeps
+// then leave the outputs untouched); every particle raises its cell's bound
+// (|G'| + |K|) H of the fixed-point units.
 __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
                            const float* __restrict__ g_D) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.n || *g.flags) return;
-  const int i = g.orig[s];
-  const BoxDev& B = g.boxes[box_of_particle(g, i)];
-  const float h = g.hs[s];
-  const float H = g.gamma * h;
-  const float H2 = H * H;
-  const float iH5 = 1.0f / (H2 * H2 * H);
-  const float gi = g_rho[i];
-  const float ki = g_D ? g_D[i] : 0.0f;
-  const float gb = guard_band(H, B.edge_f);
-  const float4 xm = g.xm[s];
-  const float K = ki * iH5 / h;
-  g.bx[s] = make_float4(xm.x, xm.y, xm.z, H2 + gb);
-  g.ba[s] = make_float4(xm.w, fmaf(-4.0f, K, gi * iH5), K, H);
+  if (*g.flags) return;  // the same for the whole warp
+  int cell = -1;
+  float bound = 0.0f;
+  if (s < g.n) {
+    const int i = g.orig[s];
+    const BoxDev& B = g.boxes[box_of_particle(g, i)];
+    const float h = g.hs[s];
+    const float H = g.gamma * h;
+    const float H2 = H * H;
+    const float iH5 = 1.0f / (H2 * H2 * H);
+    const float gi = g_rho[i];
+    const float ki = g_D ? g_D[i] : 0.0f;
+    if (!isfinite(gi) || !isfinite(ki)) atomicOr(g.flags, PV_FLAG_BAD_GRADIENT);
+    const float gb = guard_band(H, B.edge_f);
+    const float4 xm = g.xm[s];
+    const float K = ki * iH5 / h;
+    const float Gp = fmaf(-4.0f, K, gi * iH5);
+    g.bx[s] = make_float4(xm.x, xm.y, xm.z, H2 + gb);
+    g.ba[s] = make_float4(xm.w, Gp, K, H);
+    cell = g.pcell[i];
+    bound = (fabsf(Gp) + fabsf(K)) * H;
+  }
+  // particles are in cell order, so a warp spans a few cells: one atomic per
+  // cell and warp (non-negative floats order as their bit patterns)
+  const unsigned same = __match_any_sync(0xffffffffu, cell);
+  const unsigned mx = __reduce_max_sync(same, __float_as_uint(bound));
+  if (cell >= 0 && (threadIdx.x & 31) == __ffs(same) - 1)
+    atomic_max_nonneg(&g.bwd_cmax[cell], __uint_as_float(mx));
+}
+
+// Fixed-point units of the adjoint sums.  Per pair, with normalised masses
+// m <= 1: |th| <= 3/2 and |uh| <= 6; the own gradient term is at most
+// 6 (|G'_i| + |K_i|) r with r < H_i and the transposed one 6 (|G'_j| + |K_j|) r
+// with r < H_j (|vr|, |w6| <= 6), so |cc dx| <= 13 Bn, Bn being the largest
+// (|G'| + |K|) H in the 27 cells around the particle's cell (the 13 instead of
+// 12 covers the guard band of the cut-offs).  A cell-centric cell meets each of
+// its particles with at most `staged` + 1 partners, a task-path cell at most
+// 27 x 65535: the units below keep every sum under 2^30 (32-bit th, uh sums of
+// a cell-centric cell), 2^62 (64-bit gradient sums) and 2^62 (64-bit th, uh
+// sums of the task path, units 2^-36).  A bound per neighbourhood, not per box,
+// keeps the resolution fine where the supports of a clustered box span
+// orders of magnitude.
+__device__ __forceinline__ float fix_scale_s32(int staged) { return 1073741824.0f / (6.0f * (staged + 1)); }
+__device__ __forceinline__ float fix_scale_g64(float bn, float pairs) {
+  return 4611686018427387904.0f / (13.0f * fmaxf(bn, 1.0e-30f) * pairs);  // 2^62 / (13 Bn pairs)
+}
+constexpr float kTaskPairs = 27.0f * 65535.0f + 1.0f;
+constexpr double kFixS64 = 68719476736.0;  // 2^36
+
+// Bn of cell a: the largest per-cell bound over a and its 26 neighbours.
+__device__ __forceinline__ float nbhd_bound(const GridDev& g, int a) {
+  float bn = 0.0f;
+  for (int o = 0; o < kNSlot; o++) bn = fmaxf(bn, g.bwd_cmax[neighbour_cell(g, a, o)]);
+  return bn;
 }
 
 // Half-scaled kernel factors of the adjoint, without branches.  With
@@ -366,6 +411,8 @@ struct CellSharedB {
   int runs[kNSlot + 1];
   int nb_[kNSlot], cb_[kNSlot];
   float offv[kNSlot], Hmaxb[kNSlot];
+  float cmx[kNSlot];  // the neighbour cells' bounds of the adjoint terms
+  float bn;           // their largest: the unit of the cell's gradient sums
   int cell, item_next;
 };
 
@@ -411,6 +458,7 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
       cs.nb_[tid] = g.cell_count[b];
       cs.cb_[tid] = g.cell_start[b];
       cs.Hmaxb[tid] = g.cell_Hmax[b];
+      cs.cmx[tid] = g.bwd_cmax[b];
       const Slot sl = slot_info(o);
       cs.offv[tid] = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
     }
@@ -421,17 +469,24 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
     }
     __syncthreads();
     if (tid == 0) {
+      float bn = 0.0f;
       for (int q = 0; q < kNSlot; q++) {
         cs.off[q + 1] += cs.off[q];
         cs.runs[q + 1] += cs.runs[q];
+        bn = fmaxf(bn, cs.cmx[q]);
       }
+      cs.bn = bn;
     }
     __syncthreads();
     const int total = cs.off[kNSlot];
     // variable carve: kElemJ (total + kPad) + kElemA na bytes, checked by the plan
     float4* Sx = var;                                  // [total + kPad] {x, y, z, E}
     float4* Sa = Sx + total + kPad;                    // [total + kPad] {m, G', K, H}
-    float* acc = reinterpret_cast<float*>(Sa + total + kPad);  // [5][na]
+    // fixed-point sums: gx, gy, gz (64-bit), th, uh (32-bit)
+    long long* accg = reinterpret_cast<long long*>(Sa + total + kPad);  // [3][na]
+    int* accs = reinterpret_cast<int*>(accg + 3 * na);                  // [2][na]
+    const float ks = fix_scale_s32(total);
+    const float kg = fix_scale_g64(cs.bn, (float)(total + 1));
     stage_flat<4>(
         cs.off, total, tid, kCellThreads,
         [&](int f, int q) {
@@ -445,7 +500,8 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
           cp_async16(&Sx[f], &g.bx[sj]);
           cp_async16(&Sa[f], &g.ba[sj]);
         });
-    for (int t = tid; t < 5 * na; t += kCellThreads) acc[t] = 0.0f;
+    for (int t = tid; t < 3 * na; t += kCellThreads) accg[t] = 0;
+    for (int t = tid; t < 2 * na; t += kCellThreads) accs[t] = 0;
     cp_async_wait_all();
     __syncthreads();
     const int nitems = cs.runs[kNSlot];
@@ -498,17 +554,21 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
       // lanes whose windows held no pair in range have nothing to add
       if (valid && (L.Sth != 0.0f || L.Suh != 0.0f || L.gx != 0.0f || L.gy != 0.0f ||
                     L.gz != 0.0f)) {
-        atomicAdd(&acc[0 * na + il], L.Sth);
-        atomicAdd(&acc[1 * na + il], L.Suh);
-        atomicAdd(&acc[2 * na + il], L.gx);
-        atomicAdd(&acc[3 * na + il], L.gy);
-        atomicAdd(&acc[4 * na + il], L.gz);
+        atomicAdd(&accs[il], __float2int_rn(L.Sth * ks));
+        atomicAdd(&accs[na + il], __float2int_rn(L.Suh * ks));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&accg[il]),
+                  (unsigned long long)__float2ll_rn(L.gx * kg));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&accg[na + il]),
+                  (unsigned long long)__float2ll_rn(L.gy * kg));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&accg[2 * na + il]),
+                  (unsigned long long)__float2ll_rn(L.gz * kg));
       }
     }
     __syncthreads();
+    const double is = 1.0 / (double)ks, ig = 1.0 / (double)kg;
     for (int t = tid; t < na; t += kCellThreads)
-      write_bwd(g, ca + t, acc[t], acc[na + t], acc[2 * na + t], acc[3 * na + t],
-                acc[4 * na + t], g_rho, g_D, g_pos, g_h, mscale);
+      write_bwd(g, ca + t, accs[t] * is, accs[na + t] * is, accg[t] * ig, accg[na + t] * ig,
+                accg[2 * na + t] * ig, g_rho, g_D, g_pos, g_h, mscale);
     __syncthreads();
   }
   // then the tiny cells, one per warp, in the dynamic shared memory that the
@@ -582,13 +642,16 @@ __global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
     }
     if (valid && (L.Sth != 0.0f || L.Suh != 0.0f || L.gx != 0.0f || L.gy != 0.0f ||
                   L.gz != 0.0f)) {
-      double* acc = reinterpret_cast<double*>(g.gacc);
+      // 64-bit fixed point: the sum does not depend on the order of the tasks
+      unsigned long long* acc = reinterpret_cast<unsigned long long*>(g.gacc);
       const size_t N = (size_t)g.n;
-      atomicAdd(&acc[L.si], (double)L.Sth);
-      atomicAdd(&acc[N + L.si], (double)L.Suh);
-      atomicAdd(&acc[2 * N + L.si], (double)L.gx);
-      atomicAdd(&acc[3 * N + L.si], (double)L.gy);
-      atomicAdd(&acc[4 * N + L.si], (double)L.gz);
+      const float ks = (float)kFixS64;
+      const float kg = fix_scale_g64(nbhd_bound(g, a), kTaskPairs);
+      atomicAdd(&acc[L.si], (unsigned long long)__float2ll_rn(L.Sth * ks));
+      atomicAdd(&acc[N + L.si], (unsigned long long)__float2ll_rn(L.Suh * ks));
+      atomicAdd(&acc[2 * N + L.si], (unsigned long long)__float2ll_rn(L.gx * kg));
+      atomicAdd(&acc[3 * N + L.si], (unsigned long long)__float2ll_rn(L.gy * kg));
+      atomicAdd(&acc[4 * N + L.si], (unsigned long long)__float2ll_rn(L.gz * kg));
     }
   }
 }
@@ -598,13 +661,15 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
                                  float* __restrict__ g_h) {
   if (*g.flags) return;
   const float munit = (float)(16.0 / 3.14159265358979323846);
-  double* acc = reinterpret_cast<double*>(g.gacc);
+  long long* acc = g.gacc;
   const size_t N = (size_t)g.n;
   const int lane = threadIdx.x & 31;
-  auto fin = [&](int s, float mscale) {
-    write_bwd(g, s, acc[s], acc[N + s], acc[2 * N + s], acc[3 * N + s], acc[4 * N + s], g_rho,
-              g_D, g_pos, g_h, mscale);
-    for (int q = 0; q < 5; q++) acc[q * N + s] = 0.0;
+  // units as in k_backward_tasks (the float rounding of the scale is the same)
+  auto fin = [&](int s, float ig, float mscale) {
+    const double is = 1.0 / (double)(float)kFixS64;
+    write_bwd(g, s, acc[s] * is, acc[N + s] * is, acc[2 * N + s] * ig, acc[3 * N + s] * ig,
+              acc[4 * N + s] * ig, g_rho, g_D, g_pos, g_h, mscale);
+    for (int q = 0; q < 5; q++) acc[q * N + s] = 0;
   };
   // as the forward finalize: one warp per self-slot task (blocks of kBlkI
   // cell-local indices), or one block per task cell when the self slot is
@@ -617,7 +682,8 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
       if (tk.o != kSelfSlot) continue;
       const int ca = g.cell_start[tk.a];
       const float mscale = munit * g.m_max[g.cell_box[tk.a]];
-      for (int t = tk.p0 + lane; t < tk.p1; t += 32) fin(ca + t, mscale);
+      const float ig = 1.0f / fix_scale_g64(nbhd_bound(g, tk.a), kTaskPairs);
+      for (int t = tk.p0 + lane; t < tk.p1; t += 32) fin(ca + t, ig, mscale);
     }
   } else {
     const int nt = *g.n_tcells;
@@ -625,7 +691,8 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
       const int a = g.tcells[c];
       const int ca = g.cell_start[a], na = g.cell_count[a];
       const float mscale = munit * g.m_max[g.cell_box[a]];
-      for (int t = threadIdx.x; t < na; t += blockDim.x) fin(ca + t, mscale);
+      const float ig = 1.0f / fix_scale_g64(nbhd_bound(g, a), kTaskPairs);
+      for (int t = threadIdx.x; t < na; t += blockDim.x) fin(ca + t, ig, mscale);
     }
   }
 }
@@ -642,6 +709,7 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   if (e != cudaSuccess) return e;
   const int smem = kCellSmemFor[ctas_per_sm];
   const int nb = (g.n + 255) / 256;
+  if ((e = cudaMemsetAsync(g.bwd_cmax, 0, g.ncell * sizeof(float), st)) != cudaSuccess) return e;
   k_bwd_prep<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_plan(g, 1, smem - kCellFixedSmem, kElemJ, kElemA, 0, st)) !=

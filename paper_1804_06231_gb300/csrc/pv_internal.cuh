@@ -84,8 +84,11 @@ struct GridDev {
   float* dist;     // [13][N]
   // density accumulators (cell order), fixed point
   long long* acc;    // [3][N]: rho, drho/dh (2^36 scale), n
-  // backward accumulators (cell order), FP64 [5][N]: sum m th, sum m uh, gx, gy, gz
+  // adjoint accumulators of the task path (cell order), 64-bit fixed point
+  // [5][N]: sum m th, sum m uh (units 2^-36), gx, gy, gz (units set per cell
+  // by the bound of its neighbourhood's terms)
   long long* gacc;
+  float* bwd_cmax;   // [C] largest (|G'| + |K|) H of the cell's particles (adjoint term bound)
   float4* bx;        // [N] backward, cell order: {x', y', z', H^2 + guard}
   float4* ba;        // [N] backward, cell order: {m/m_max, g/H^5, k/(h H^5), H}
   // plan: per (cell, slot) {reachable count of a, window [J0, J1) of b, 0}
@@ -502,6 +505,8 @@ inline cudaError_t set_max_dynamic_smem(const void* func, int bytes, cudaStream_
 // pv_last_cuda_error returns) and maps `e` to a status code.
 pv_status record_cuda_error(cudaError_t e, const char* what);
 cudaError_t launch_count_candidates(const GridDev& g, cudaStream_t st);
+cudaError_t launch_fp32_probe(int packed, int iters, float* sink, int64_t threads,
+                              double* flops, cudaStream_t st);
 cudaError_t launch_raw_density(const float4* xi, int ni, const float4* xj, int nj, float H,
                                int reps, float2* out, cudaStream_t st);
 

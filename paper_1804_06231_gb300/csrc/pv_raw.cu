@@ -47,7 +47,60 @@ __global__ void __launch_bounds__(kRawThreads) k_raw_density(const float4* __res
   if (i < ni) out[i] = make_float2(rho, D);
 }
 
+// FP32 throughput probe: every thread runs kProbeChains independent chains
+// a <- a b + c (b just below 1, so the values stay bounded), as scalar FFMA or
+// as packed fma.rn.f32x2 pairs, and writes their sum so nothing is dropped.
+constexpr int kProbeChains = 8;
+constexpr int kProbeUnroll = 4;
+
+template <bool Packed>
+__global__ void __launch_bounds__(256) k_fp32_probe(int iters, float* __restrict__ sink) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const float b = 0.99999994f, c = 1.0e-7f;
+  float acc = 0.0f;
+  if (Packed) {
+    float2 a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; k++) a[k] = make_float2(t * 1e-9f + k, t * 1e-9f - k);
+    const float2 b2 = make_float2(b, b), c2 = make_float2(c, c);
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+      for (int u = 0; u < kProbeUnroll; u++)
+#pragma unroll
+        for (int k = 0; k < kProbeChains; k++) a[k] = __ffma2_rn(a[k], b2, c2);
+    }
+#pragma unroll
+    for (int k = 0; k < kProbeChains; k++) acc += a[k].x + a[k].y;
+  } else {
+    float a[kProbeChains];
+#pragma unroll
+    for (int k = 0; k < kProbeChains; k++) a[k] = t * 1e-9f + k;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+      for (int u = 0; u < kProbeUnroll; u++)
+#pragma unroll
+        for (int k = 0; k < kProbeChains; k++) a[k] = fmaf(a[k], b, c);
+    }
+#pragma unroll
+    for (int k = 0; k < kProbeChains; k++) acc += a[k];
+  }
+  sink[t] = acc;
+}
+
 }  // namespace
+
+cudaError_t launch_fp32_probe(int packed, int iters, float* sink, int64_t threads,
+                              double* flops, cudaStream_t st) {
+  const int blocks = (int)(threads / 256);
+  *flops = 2.0 * (packed ? 2.0 : 1.0) * kProbeChains * kProbeUnroll * (double)iters *
+           (double)blocks * 256.0;
+  if (blocks == 0) return cudaSuccess;
+  if (packed)
+    k_fp32_probe<true><<<blocks, 256, 0, st>>>(iters, sink);
+  else
+    k_fp32_probe<false><<<blocks, 256, 0, st>>>(iters, sink);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_raw_density(const float4* xi, int ni, const float4* xj, int nj, float H,
                                int reps, float2* out, cudaStream_t st) {

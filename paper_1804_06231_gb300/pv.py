@@ -32,7 +32,8 @@ EXPORTS = ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
            "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
            "pv_status_str", "pv_last_cuda_error", "pv_density_static", "pv_grid_time_sweeps",
            "pv_grid_sweep_times", "pv_grid_set_tuning", "pv_grid_get_tuning",
-           "pv_grid_set_slot_mask", "pv_raw_interactions", "pv_update_positions")
+           "pv_grid_set_slot_mask", "pv_raw_interactions", "pv_update_positions",
+           "pv_fp32_probe")
 STATIC_MAX_PARTICLES = 65536
 STATIC_MAX_CELLS = 4096
 
@@ -96,6 +97,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pv_update_positions.argtypes = [vp, vp, vp, vp]
     lib.pv_raw_interactions.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int64, ctypes.c_float,
                                         ctypes.c_int32, vp, vp]
+    lib.pv_fp32_probe.argtypes = [i32, i32, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                  vp]
     lib.pv_grid_set_tuning.argtypes = [vp, ctypes.POINTER(pv_tuning)]
     lib.pv_grid_get_tuning.argtypes = [vp, ctypes.POINTER(pv_tuning)]
     lib.pv_grid_sweep_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -104,7 +107,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                  "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
                  "pv_grid_time_sweeps", "pv_grid_sweep_times", "pv_grid_set_tuning",
                  "pv_grid_get_tuning", "pv_grid_set_slot_mask", "pv_raw_interactions",
-                 "pv_update_positions"):
+                 "pv_update_positions", "pv_fp32_probe"):
         getattr(lib, name).restype = i32
     lib.pv_status_str.argtypes = [i32]
     lib.pv_status_str.restype = ctypes.c_char_p
@@ -194,6 +197,7 @@ def pv_grid_get_tuning(grid: int) -> tuple[int, int]:
 
 SLOT_MASK_ALL = (1 << 27) - 1
 FLAG_SKIN_EXCEEDED = 16
+FLAG_BAD_GRADIENT = 32
 
 
 def pv_update_positions(grid: int, pos: int, h: int, stream: int = 0) -> None:
@@ -204,6 +208,14 @@ def pv_raw_interactions(xi: int, n_i: int, xj: int, n_j: int, H: float, reps: in
                         stream: int = 0) -> None:
     _check(load_library().pv_raw_interactions(xi, int(n_i), xj, int(n_j), ctypes.c_float(H),
                                               int(reps), out, stream), "pv_raw_interactions")
+
+
+def pv_fp32_probe(packed: int, iters: int, sink: int, threads: int, stream: int = 0) -> float:
+    """Queues the FP32 throughput probe; returns its FP32 operations (FMA = 2)."""
+    flops = ctypes.c_double(0.0)
+    _check(load_library().pv_fp32_probe(int(packed), int(iters), sink, int(threads),
+                                        ctypes.byref(flops), stream), "pv_fp32_probe")
+    return flops.value
 
 
 def raw_interactions(xi, xj, H: float, reps: int = 1, out=None, stream=None):

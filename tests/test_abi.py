@@ -19,7 +19,7 @@ def lib():
 def header_functions():
     src = (ROOT / "include" / "pv.h").read_text()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pv_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(pv_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_symbols_exported(lib):
@@ -75,6 +75,12 @@ def test_argument_errors_return_before_device_work(lib):
     assert lib.pv_raw_interactions(None, 4, None, 4, ctypes.c_float(1.0), 1, None, None) == 1
     assert lib.pv_raw_interactions(None, -1, None, 4, ctypes.c_float(1.0), 1, None, None) == 1
     assert lib.pv_raw_interactions(None, 0, None, 0, ctypes.c_float(0.0), 1, None, None) == 1
+    fl = ctypes.c_double(0.0)
+    assert lib.pv_fp32_probe(0, 0, None, 256, ctypes.byref(fl), None) == 1      # iters < 1
+    assert lib.pv_fp32_probe(0, 10, None, 100, ctypes.byref(fl), None) == 1     # not 256k
+    assert lib.pv_fp32_probe(0, 10, None, 256, ctypes.byref(fl), None) == 1     # no sink
+    assert lib.pv_fp32_probe(1, 10, None, 256, None, None) == 1                 # no flops
+    assert lib.pv_fp32_probe(1, 10, None, 0, ctypes.byref(fl), None) == 0       # nothing queued
     t = pv.pv_tuning(3, 2)
     assert lib.pv_grid_set_tuning(None, ctypes.byref(t)) == 1
     assert lib.pv_grid_get_tuning(None, ctypes.byref(t)) == 1

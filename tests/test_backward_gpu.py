@@ -164,3 +164,57 @@ def test_adjoint_box_of_other_size_with_unwrapped_positions(oracle_lib):
     gp, gh = gpu_adjoint(box, g, k)
     gp0, gh0 = oracle_lib.backward_cells(box.pos, box.h, box.m, g, k, box.L, box.nc)
     check_adjoint(gp, gh, gp0, gh0)
+
+
+def test_adjoint_deterministic():
+    """The adjoint is bit-reproducible: fixed-point sums make it independent
+    of which warp or CTA took which work item.  Twice on one grid and once on
+    a fresh grid, for a clustered box (dense cells on the task path, tiny
+    cells on the warp path) and for a batched grid of several boxes."""
+    import torch
+    from paper_1804_06231_gb300.pv import Grid
+    dev = torch.device("cuda", 0)
+    cases = [[I.clustered(50000, 21)], I.multibox(n_boxes=5, scale=0.3, seed=22)]
+    for boxes in cases:
+        pos = torch.from_numpy(np.concatenate([b.pos for b in boxes])).to(dev)
+        h = torch.from_numpy(np.concatenate([b.h for b in boxes])).to(dev)
+        m = torch.from_numpy(np.concatenate([b.m for b in boxes])).to(dev)
+        rng = np.random.default_rng(23)
+        gr = torch.from_numpy(rng.standard_normal(pos.shape[0]).astype(np.float32)).to(dev)
+        gd = torch.from_numpy(rng.standard_normal(pos.shape[0]).astype(np.float32)).to(dev)
+        outs = []
+        grid = None
+        for fresh in (True, False, True):
+            if fresh:
+                if grid is not None:
+                    grid.close()
+                grid = Grid([(b.n, b.L, b.nc) for b in boxes])
+                grid.sort(pos, h, m)
+            gp, gh = grid.backward(gr, gd)
+            grid.sync()
+            outs.append((gp.cpu().numpy(), gh.cpu().numpy()))
+        grid.close()
+        for gp, gh in outs[1:]:
+            assert np.array_equal(gp, outs[0][0])
+            assert np.array_equal(gh, outs[0][1])
+
+
+def test_adjoint_non_finite_gradient_is_flagged():
+    """A NaN upstream gradient latches PV_FLAG_BAD_GRADIENT and leaves the
+    outputs untouched."""
+    import torch
+    from paper_1804_06231_gb300 import pv
+    from paper_1804_06231_gb300.pv import Grid
+    dev = torch.device("cuda", 0)
+    box = I.uniform(8000, 24, nc=6)
+    gr = np.ones(box.n, np.float32)
+    gr[123] = np.nan
+    with Grid((box.n, box.L, box.nc)) as g:
+        g.sort(torch.from_numpy(box.pos).to(dev), torch.from_numpy(box.h).to(dev),
+               torch.from_numpy(box.m).to(dev))
+        gp = torch.full((box.n, 3), 7.0, dtype=torch.float32, device=dev)
+        gh = torch.full((box.n,), 7.0, dtype=torch.float32, device=dev)
+        g.backward(torch.from_numpy(gr).to(dev), None, gp, gh)
+        st = g.stats(raise_on_flags=False)
+    assert st.device_flags & pv.FLAG_BAD_GRADIENT
+    assert torch.all(gp == 7.0) and torch.all(gh == 7.0)
