@@ -315,6 +315,7 @@ def workload_extras(dev, flush, probe: dict, peak_derived: float, K: int = 5) ->
             "fwd_bwd_over_fwd": t_step / (t_sort + t_dens),
             "candidates": cand, "interactions": inter,
             "candidates_adjoint": stc.candidates_adjoint, "pairs_adjoint": stc.pairs_adjoint,
+            "symmetric_update": symmetric_update(g, flush, rho, D, nn),
             "roofline_density_pass": sweep_roofline("pv_density (all its kernels)", fw[0], fw[1],
                                                     t_dens, probe, peak_derived),
             "roofline_adjoint_pass": sweep_roofline("pv_density_backward (all its kernels)",
@@ -501,6 +502,15 @@ def graph_step(step, flush, K: int = 20) -> dict:
     with torch.cuda.graph(graph):
         step()
     return {"ms_per_step": timed_steps(graph.replay, flush, K)}
+
+
+def symmetric_update(grid, flush, rho, drho, nngb, K: int = 5) -> dict:
+    """The density pass as the gather (pv_density) against the paper's
+    symmetric pair update (pv_density_symmetric) on the same sorted grid."""
+    t_g = timed_steps(lambda: grid.density(rho, drho, nngb), flush, K)
+    t_s = timed_steps(lambda: grid.density(rho, drho, nngb, symmetric=True), flush, K)
+    return {"density_ms_gather": t_g, "density_ms_symmetric": t_s,
+            "symmetric_over_gather": t_s / t_g}
 
 
 def orientation_breakdown(grid, st, flush, density, K: int = 5) -> dict:
@@ -800,6 +810,7 @@ def main():
                       grid, st_c, flush, lambda: grid.density(rho, drho, nngb)),
                   "raw_interaction_ceiling": raw_ceiling(dev, props, peak_tflops),
                   "cuda_graph_step": graph_step(step, flush),
+                  "symmetric_update": symmetric_update(grid, flush, rho, drho, nngb),
                   "sort_reuse": sort_reuse(grid, box, pos, h, m_uniform, flush,
                                            lambda: grid.density(rho, drho, nngb),
                                            lambda: grid.backward(g_rho, g_d, gpos, gh), dev)}

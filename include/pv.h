@@ -139,6 +139,18 @@ pv_status pv_sort_cells(pv_grid* g, const double* pos, const float* h, const flo
    Deterministic: the result does not depend on scheduling. */
 pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, void* stream);
 
+/* The same rho, drho_dh and n_ngb as pv_density (same arguments, layout and
+   requirements), computed with the paper's symmetric pair update (Section
+   3.3, last paragraph): each pair of neighbouring cells is swept once, in one
+   direction, with the window reaching the larger of the two particles'
+   supports, and every pair (i, j) found in range is evaluated once and
+   updates both particles (i when r < H_i, j when r < H_j).  The pairs of
+   each cell pair are counted once instead of twice; the kernel terms are
+   still evaluated per side.  Deterministic (64-bit fixed-point sums).  The
+   gather form, pv_density, is the faster of the two on this GPU. */
+pv_status pv_density_symmetric(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb,
+                               void* stream);
+
 /* Adjoint of pv_density (not in the paper).  Given the upstream gradients
      g_rho      device float [N]   dL/drho_i
      g_drho_dh  device float [N]   dL/d(drho_dh)_i   (NULL: zero)

@@ -318,6 +318,21 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
   return PV_OK;
 }
 
+pv_status pv_density_symmetric(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb,
+                               void* stream) {
+  if (!g) return PV_ERR_INVALID_ARGUMENT;
+  if (g->n > 0 && !rho) return PV_ERR_INVALID_ARGUMENT;
+  if (!g->sorted) return PV_ERR_NOT_SORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GridDev& d = g->d;
+  PV_CUDA(cudaMemsetAsync(d.ntask, 0, 5 * sizeof(int32_t), st));  // ccell_next among them
+  PV_CUDA(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned long long), st));
+  if (g->n) PV_CUDA(cudaMemsetAsync(d.acc, 0, 3 * (size_t)g->n * sizeof(long long), st));
+  PV_CUDA(pv::launch_density_symmetric(d, rho, drho_dh, n_ngb, g->num_sms, st));
+  g->launches += g->n > 0 ? 3 : 0;  // plan_slots, sweep, finalize
+  return PV_OK;
+}
+
 pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drho_dh,
                               float* g_pos, float* g_h, void* stream) {
   if (!g) return PV_ERR_INVALID_ARGUMENT;

@@ -1085,6 +1085,13 @@ __global__ void k_count_classes(GridDev g) {
 
 }  // namespace
 
+cudaError_t launch_plan_slots(const GridDev& g, int wide, cudaStream_t st) {
+  const int nthr = g.ncell * kNSlot;
+  if (nthr == 0) return cudaSuccess;
+  k_plan_slots<<<(nthr + 255) / 256, 256, 0, st>>>(g, wide);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
                         int elem_i, cudaStream_t st) {
   const int nthr = g.ncell * kNSlot;

@@ -472,7 +472,13 @@ cudaError_t launch_update(const GridDev& g, const double* pos, const float* h, c
 // to the cell-centric kernel, the others are split into tasks.
 cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
                         int elem_i, cudaStream_t st);
+// Only the per-(cell, slot) plan (no routing), as launch_plan's first kernel.
+cudaError_t launch_plan_slots(const GridDev& g, int wide, cudaStream_t st);
 int64_t max_tasks_for(int64_t n, int64_t ncell);
+// The density by the symmetric pair update (pv_symmetric.cu); the grid's
+// fixed-point sums `acc` and the counter ccell_next must be zero.
+cudaError_t launch_density_symmetric(const GridDev& g, float* rho, float* drho_dh,
+                                     int32_t* n_ngb, int num_sms, cudaStream_t st);
 // ctas_per_sm: resident CTAs of the cell-centric sweep kernel per SM (1..4
 // forward, 1..3 adjoint); it sets the kernel's shared memory and so which
 // cells the plan routes to it.  t0/t1 (optional): events recorded on `st`

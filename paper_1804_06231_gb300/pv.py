@@ -33,7 +33,7 @@ EXPORTS = ("pv_grid_create", "pv_grid_destroy", "pv_sort_cells", "pv_density",
            "pv_status_str", "pv_last_cuda_error", "pv_density_static", "pv_grid_time_sweeps",
            "pv_grid_sweep_times", "pv_grid_set_tuning", "pv_grid_get_tuning",
            "pv_grid_set_slot_mask", "pv_raw_interactions", "pv_update_positions",
-           "pv_fp32_probe")
+           "pv_fp32_probe", "pv_density_symmetric")
 STATIC_MAX_PARTICLES = 65536
 STATIC_MAX_CELLS = 4096
 
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pv_sort_cells.argtypes = [vp, vp, vp, vp, ctypes.c_float, vp]
     lib.pv_density.argtypes = [vp, vp, vp, vp, vp]
     lib.pv_density_backward.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.pv_density_symmetric.argtypes = [vp, vp, vp, vp, vp]
     lib.pv_count_candidates.argtypes = [vp, vp]
     lib.pv_grid_sync.argtypes = [vp, vp]
     lib.pv_grid_stats.argtypes = [vp, ctypes.POINTER(pv_stats)]
@@ -107,7 +108,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                  "pv_density_backward", "pv_count_candidates", "pv_grid_sync", "pv_grid_stats",
                  "pv_grid_time_sweeps", "pv_grid_sweep_times", "pv_grid_set_tuning",
                  "pv_grid_get_tuning", "pv_grid_set_slot_mask", "pv_raw_interactions",
-                 "pv_update_positions", "pv_fp32_probe"):
+                 "pv_update_positions", "pv_fp32_probe", "pv_density_symmetric"):
         getattr(lib, name).restype = i32
     lib.pv_status_str.argtypes = [i32]
     lib.pv_status_str.restype = ctypes.c_char_p
@@ -158,6 +159,12 @@ def pv_sort_cells(grid: int, pos: int, h: int, m: int | None, m_uniform: float =
 def pv_density(grid: int, rho: int, drho_dh: int | None, n_ngb: int | None,
                stream: int = 0) -> None:
     _check(load_library().pv_density(grid, rho, drho_dh, n_ngb, stream), "pv_density")
+
+
+def pv_density_symmetric(grid: int, rho: int, drho_dh: int | None, n_ngb: int | None,
+                         stream: int = 0) -> None:
+    _check(load_library().pv_density_symmetric(grid, rho, drho_dh, n_ngb, stream),
+           "pv_density_symmetric")
 
 
 def pv_density_backward(grid: int, g_rho: int, g_drho_dh: int | None, g_pos: int,
@@ -359,14 +366,16 @@ class Grid:
         hp = self._dev(h, torch.float32, (self.n,), "h")
         pv_update_positions(self.handle, p, hp, self._stream(stream))
 
-    def density(self, rho=None, drho_dh=None, n_ngb=None, stream=None):
+    def density(self, rho=None, drho_dh=None, n_ngb=None, stream=None, symmetric=False):
+        """pv_density (or, with symmetric=True, pv_density_symmetric)."""
         import torch
         if rho is None:
             dev = torch.device("cuda", torch.cuda.current_device())
             rho = torch.empty(self.n, dtype=torch.float32, device=dev)
             drho_dh = torch.empty(self.n, dtype=torch.float32, device=dev)
             n_ngb = torch.empty(self.n, dtype=torch.int32, device=dev)
-        pv_density(self.handle, self._dev(rho, torch.float32, (self.n,), "rho"),
+        (pv_density_symmetric if symmetric else pv_density)(
+                   self.handle, self._dev(rho, torch.float32, (self.n,), "rho"),
                    None if drho_dh is None else self._dev(drho_dh, torch.float32, (self.n,),
                                                           "drho_dh"),
                    None if n_ngb is None else self._dev(n_ngb, torch.int32, (self.n,), "n_ngb"),

@@ -65,6 +65,7 @@ def test_argument_errors_return_before_device_work(lib):
     assert lib.pv_grid_create(ctypes.byref(desc), ctypes.byref(out)) == 1   # flags != 0
     assert lib.pv_sort_cells(None, None, None, None, ctypes.c_float(0), None) == 1
     assert lib.pv_density(None, None, None, None, None) == 1
+    assert lib.pv_density_symmetric(None, None, None, None, None) == 1
     assert lib.pv_density_backward(None, None, None, None, None, None) == 1
     assert lib.pv_count_candidates(None, None) == 1
     assert lib.pv_grid_sync(None, None) == 1
