@@ -95,7 +95,7 @@ __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
     const float4 xm = g.xm[s];
     const float K = ki * iH5 / h;
     const float Gp = fmaf(-4.0f, K, gi * iH5);
-    g.bx[s] = make_float4(xm.x, xm.y, xm.z, H2 + gb);
+    g.bx[s] = make_float4(-xm.x, -xm.y, -xm.z, H2 + gb);  // negated offsets
     g.ba[s] = make_float4(xm.w, Gp, K, H);
     cell = g.pcell[i];
     bound = (fabsf(Gp) + fabsf(K)) * H;
@@ -170,31 +170,58 @@ __device__ __forceinline__ float warp_max_b(float v) {
   return v;
 }
 
+// shared-memory loads through 32-bit shared-window addresses
+__device__ __forceinline__ unsigned smem_addr_b(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ float4 lds4_b(unsigned a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a));
+  return v;
+}
+
 struct LaneB {
-  float x, y, z;         // i in b's frame
+  float2 xy;             // x, y of i in b's frame (a packed pair)
+  float z;
   float Hsq_hi, Hsq_lo, Hinv, H, G, K, m;  // G holds G' = G - 4K
   int si;
   float Sth, Suh, gx, gy, gz;
+  float2 Sth2, Suh2, g2x, g2y, g2z;  // sums of the packed rounds (halves added at the end)
 };
+
+// folds the packed rounds' sums into the scalar ones
+__device__ __forceinline__ void laneb_fold(LaneB& L) {
+  L.Sth += L.Sth2.x + L.Sth2.y;
+  L.Suh += L.Suh2.x + L.Suh2.y;
+  L.gx += L.g2x.x + L.g2x.y;
+  L.gy += L.g2y.x + L.g2y.y;
+  L.gz += L.g2z.x + L.g2z.y;
+  L.Sth2 = L.Suh2 = L.g2x = L.g2y = L.g2z = make_float2(0.0f, 0.0f);
+}
 
 // An inactive lane sits far outside every window (its r^2 is ~1e36), so the
 // pre-filter gives it no hits.
 __device__ __forceinline__ void laneb_init(LaneB& L) {
-  L.x = L.y = L.z = 1.0e18f;
+  L.xy = make_float2(1.0e18f, 1.0e18f);
+  L.z = 1.0e18f;
   L.Hsq_hi = L.Hsq_lo = -1.0f;
   L.Hinv = L.H = L.G = L.K = L.m = 0.0f;
   L.si = 0;
   L.Sth = L.Suh = L.gx = L.gy = L.gz = 0.0f;
+  L.Sth2 = L.Suh2 = L.g2x = L.g2y = L.g2z = make_float2(0.0f, 0.0f);
 }
 
+// The staged records hold the negated offsets (bx = {-x', -y', -z', E}), so
+// that x_i - x_j is an addition.
 __device__ __forceinline__ void laneb_set(LaneB& L, const GridDev& g, const BoxDev& B,
                                           const Slot& sl, int si) {
   const float4 xe = g.bx[si];
   const float4 ak = g.ba[si];
   L.si = si;
-  L.x = xe.x - sl.ox * B.edge_f;
-  L.y = xe.y - sl.oy * B.edge_f;
-  L.z = xe.z - sl.oz * B.edge_f;
+  L.xy = make_float2(-xe.x - sl.ox * B.edge_f, -xe.y - sl.oy * B.edge_f);
+  L.z = -xe.z - sl.oz * B.edge_f;
   L.m = ak.x; L.G = ak.y; L.K = ak.z; L.H = ak.w;
   L.Hsq_hi = xe.w;
   // H^2 - guard = 2 H^2 - (H^2 + guard), to within an ulp: the band only has
@@ -202,8 +229,6 @@ __device__ __forceinline__ void laneb_set(LaneB& L, const GridDev& g, const BoxD
   L.Hsq_lo = fmaf(2.0f * L.H, L.H, -xe.w);
   L.Hinv = 1.0f / L.H;
 }
-
-constexpr int kMaskChunks = 8;  // 32-candidate chunks per segment of the sweep
 
 // Adds the own (scaled by mo = m_j or 0) and transposed (mt = m_i or 0) terms
 // of the pair (i, j) to lane i's five sums (aj = {m_j, G'_j, K_j, H_j}).
@@ -222,102 +247,158 @@ __device__ __forceinline__ void bwd_pair(LaneB& L, float dx, float dy, float dz,
   L.gz = fmaf(cc, dz, L.gz);
 }
 
-// Pre-filter of 8 staged candidates {x, y, z, E_j = H_j^2 + guard_j} for the
-// adjoint: shifts the sign of r^2 - max(H_i^2 + guard_i, E_j) into `m`, first
-// candidate first.  r^2 is the same FP32 expression as in the evaluation, so
-// a hit is exactly a pair that is in range of the own or the transposed test.
-__device__ __forceinline__ void prefilter8_bwd(unsigned& m, const float4* __restrict__ X,
-                                               const LaneB& L) {
-#pragma unroll
-  for (int c = 0; c < 8; c++) {
-    const float4 q = X[c];
-    const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float d = r2 - fmaxf(L.Hsq_hi, q.w);
-    m = __funnelshift_l(__float_as_uint(d), m, 1);
-  }
+// Two pairs at once in packed FP32 (fma.rn.f32x2).  The factors come from
+// the half-scaled shape function w = s^3 - 4 t^3 (s = max(1 - q, 0),
+// t = max(1/2 - q, 0), the two cubic pieces without a branch) and its
+// derivatives w' = 12 t^2 - 3 s^2, w'' = 6 s - 24 t:
+//   th = 3 w + q w',  uh = 12 w + 8 q w' + q^2 w'',  vr = w' / q,  w6 = w''
+// (the same values as spline_bwd: on q < 1/2, w' = 9 q^2 - 6 q).
+__device__ __forceinline__ float2 max0(float2 v) {
+  return make_float2(fmaxf(v.x, 0.0f), fmaxf(v.y, 0.0f));
+}
+__device__ __forceinline__ void wprime2(float2 q, float2& s, float2& s2, float2& w1, float2& w2) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  s = max0(__ffma2_rn(q, m1, make_float2(1.0f, 1.0f)));
+  const float2 t = max0(__ffma2_rn(q, m1, make_float2(0.5f, 0.5f)));
+  s2 = __fmul2_rn(s, s);
+  const float2 t2 = __fmul2_rn(t, t);
+  w1 = __ffma2_rn(t2, make_float2(12.0f, 12.0f), __fmul2_rn(s2, make_float2(-3.0f, -3.0f)));
+  w2 = __ffma2_rn(t, make_float2(-24.0f, -24.0f), __fmul2_rn(s, make_float2(6.0f, 6.0f)));
+  s = __fmul2_rn(s2, s);  // s^3
+  s2 = __fmul2_rn(t2, t);  // t^3
 }
 
-// Adjoint sweep over staged particles [lo, hi): Sx {x, y, z, E_j = H_j^2 +
-// guard_j}, Sa {m_j, G'_j, K_j, H_j}; jidx(e) gives the cell-order index of
-// staged particle e (read only for FP64 re-decisions near a cut-off).  Same
-// two passes as the forward sweep: the pre-filter keeps the candidates with
-// r < max(H_i, H_j) (the windows themselves reach max(H_i, H_max of the other
-// cell)), then each lane walks its own hits and applies the exact own
-// (r < H_i) and transposed (r < H_j) tests.
+// The own and transposed terms of two pairs A and B (records qA/aA, qB/aB;
+// differences dxy, dz as bwd_r2 forms them) with masses mo (own: m_j or 0)
+// and mt (transposed: m_i or 0), added to lane i's five sums.
+__device__ __forceinline__ void bwd_pair2(LaneB& L, float2 r2, float2 dx, float2 dy, float2 dz,
+                                          float4 aA, float4 aB, float2 mo, float2 mt) {
+  const float2 rinv = make_float2(rsqrtf(fmaxf(r2.x, 1e-30f)), rsqrtf(fmaxf(r2.y, 1e-30f)));
+  const float2 r = __fmul2_rn(r2, rinv);
+  // own side, q = r / H_i
+  const float2 q = __fmul2_rn(r, make_float2(L.Hinv, L.Hinv));
+  float2 s3, t3, w1, w2;
+  wprime2(q, s3, t3, w1, w2);
+  const float2 w = __ffma2_rn(t3, make_float2(-4.0f, -4.0f), s3);
+  const float2 qw1 = __fmul2_rn(q, w1);
+  const float2 th = __ffma2_rn(w, make_float2(3.0f, 3.0f), qw1);
+  const float2 uh = __ffma2_rn(__fmul2_rn(q, q), w2,
+                               __ffma2_rn(w, make_float2(12.0f, 12.0f),
+                                          __fmul2_rn(qw1, make_float2(8.0f, 8.0f))));
+  const float2 qinv = __fmul2_rn(make_float2(L.H, L.H), rinv);
+  const float2 vr = __fmul2_rn(w1, qinv);
+  // transposed side, q_j = r / H_j
+  const float2 Hj = make_float2(aA.w, aB.w);
+  const float2 qj = make_float2(__fdividef(r.x, Hj.x), __fdividef(r.y, Hj.y));
+  float2 sj3, tj3, wj1, wj2;
+  wprime2(qj, sj3, tj3, wj1, wj2);
+  const float2 vrj = __fmul2_rn(wj1, __fmul2_rn(Hj, rinv));
+  L.Sth2 = __ffma2_rn(mo, th, L.Sth2);
+  L.Suh2 = __ffma2_rn(mo, uh, L.Suh2);
+  const float2 co = __ffma2_rn(make_float2(L.G, L.G), vr, __fmul2_rn(make_float2(-L.K, -L.K), w2));
+  const float2 ct = __ffma2_rn(make_float2(aA.y, aB.y), vrj,
+                               __fmul2_rn(make_float2(-aA.z, -aB.z), wj2));
+  const float2 cc = __ffma2_rn(mo, co, __fmul2_rn(mt, ct));
+  L.g2x = __ffma2_rn(cc, dx, L.g2x);
+  L.g2y = __ffma2_rn(cc, dy, L.g2y);
+  L.g2z = __ffma2_rn(cc, dz, L.g2z);
+}
+
+// r^2 of lane i and a staged record q = {-x_j, -y_j, -z_j, E_j}, and the
+// differences: the same FP32 expression in the pre-filter and the
+// evaluation, so a hit is exactly a pair in range of the own or the
+// transposed test.
+__device__ __forceinline__ float bwd_r2(const LaneB& L, float4 q, float2& dxy, float& dz) {
+  dxy = __fadd2_rn(L.xy, make_float2(q.x, q.y));
+  dz = L.z + q.z;
+  const float2 sq = __fmul2_rn(dxy, dxy);
+  return fmaf(dz, dz, sq.x) + sq.y;
+}
+
+// Adjoint sweep over the staged records [lo, hi) (Sx {-x, -y, -z, E_j = H_j^2 +
+// guard_j} and Sa {m_j, G'_j, K_j, H_j} at shared addresses, 16 bytes each);
+// jidx(e) gives the cell-order index of staged particle e (read only for FP64
+// re-decisions near a cut-off).  Chunk by chunk (32 candidates): the
+// pre-filter keeps the candidates with r < max(H_i, H_j) (plus guard; the
+// windows themselves reach max(H_i, H_max of the other cell)) in a per-lane
+// hit mask held in a register (candidate c at bit 31 - c), then the warp runs
+// as many rounds as its busiest lane has hits and each lane applies the exact
+// own (r < H_i) and transposed (r < H_j) tests to its own hits.
 template <typename JIndex>
-__device__ __forceinline__ void sweep_bwd(LaneB& L, const float4* __restrict__ Sx,
-                                          const float4* __restrict__ Sa, int lo, int hi,
-                                          unsigned* __restrict__ M, int lane, const GridDev& g,
-                                          const BoxDev& B, JIndex jidx) {
-  for (int seg = lo; seg < hi; seg += 32 * kMaskChunks) {
-    const int seg_end = min(hi, seg + 32 * kMaskChunks);
-    const int nk = (seg_end - seg + 31) >> 5;
-    unsigned nz = 0;
-    int tot = 0;
-    for (int k = 0; k < nk; k++) {
-      const int base = seg + 32 * k;
-      const int cnt = min(32, seg_end - base);
-      unsigned m = 0;
-      int c0 = 0;
-#pragma unroll 1
-      for (; c0 < cnt; c0 += 8) prefilter8_bwd(m, Sx + base + c0, L);
-      m = __brev(m) >> (32 - c0);
-      if (cnt < 32) m &= (1u << cnt) - 1u;
-      M[k * 32 + lane] = m;
-      nz |= (m != 0u ? 1u : 0u) << k;
-      tot += __popc(m);
-    }
-    for (int s = 16; s > 0; s >>= 1) tot = max(tot, __shfl_xor_sync(0xffffffffu, tot, s));
-    int k = 0;
+__device__ __forceinline__ void sweep_bwd(LaneB& L, unsigned Sx, unsigned Sa, int lo, int hi,
+                                          const GridDev& g, const BoxDev& B, JIndex jidx) {
+  for (int base = lo; base < hi; base += 32) {
+    const int cnt = min(32, hi - base);
+    const unsigned px = Sx + 16u * base;
     unsigned m = 0;
-    bool amb = false;
-    // four rounds per iteration: their kernel evaluations are independent, so
-    // the compiler interleaves them (within the 80 registers of three CTAs
-    // per SM)
-#pragma unroll 4
-    for (int round = 0; round < tot; round++) {
-      if (m == 0u && nz != 0u) {
-        k = __ffs(nz) - 1;
-        nz &= nz - 1u;
-        m = M[k * 32 + lane];
+    if (cnt == 32) {
+#pragma unroll
+      for (int c = 0; c < 32; c++) {
+        float2 dxy;
+        float dz;
+        const float4 q = lds4_b(px + 16u * c);
+        const float d = bwd_r2(L, q, dxy, dz) - fmaxf(L.Hsq_hi, q.w);
+        m = __funnelshift_l(__float_as_uint(d), m, 1);
       }
-      const int c = __ffs(m) - 1;
-      m &= m - 1u;
-      const int j = seg + 32 * k + max(c, 0);
-      const float4 q = Sx[j];    // x_j, y_j, z_j, E_j
-      const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const float4 aj = Sa[j];   // m_j, G'_j, K_j, H_j
+    } else {
+#pragma unroll 1
+      for (int c = 0; c < cnt; c++) {
+        float2 dxy;
+        float dz;
+        const float4 q = lds4_b(px + 16u * c);
+        const float d = bwd_r2(L, q, dxy, dz) - fmaxf(L.Hsq_hi, q.w);
+        m = __funnelshift_l(__float_as_uint(d), m, 1);
+      }
+      m <<= 32 - cnt;
+    }
+    const unsigned m0 = m;
+    const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(m));
+    bool amb = false;
+    // two hits per round, evaluated as packed pairs
+#pragma unroll 1
+    for (int round = 0; round < rounds; round += 2) {
+      const int cA = __clz(m);  // 32: this lane has no hit left
+      m &= ~__funnelshift_rc(0x80000000u, 0u, cA);
+      const int cB = __clz(m);
+      m &= ~__funnelshift_rc(0x80000000u, 0u, cB);
+      const unsigned oA = 16u * (unsigned)(base + (cA & 31)), oB = 16u * (unsigned)(base + (cB & 31));
+      const float4 qA = lds4_b(Sx + oA), qB = lds4_b(Sx + oB);
+      const float4 aA = lds4_b(Sa + oA), aB = lds4_b(Sa + oB);
+      float2 dA, dB;
+      float zA, zB;
+      const float rA = bwd_r2(L, qA, dA, zA), rB = bwd_r2(L, qB, dB, zB);
       // pairs within rounding of a cut-off count as in range here and are
       // re-decided in FP64 after the rounds (H_j^2 - guard_j = 2 H_j^2 - E_j)
-      const bool own = (c >= 0) && (r2 < L.Hsq_hi);
-      const bool trans = (c >= 0) && (r2 < q.w);
-      amb |= (own && r2 >= L.Hsq_lo) || (trans && r2 >= fmaf(2.0f * aj.w, aj.w, -q.w));
-      bwd_pair(L, dx, dy, dz, r2, aj, own ? aj.x : 0.0f, trans ? L.m : 0.0f);
+      const bool oAin = (cA < 32) && (rA < L.Hsq_hi), tAin = (cA < 32) && (rA < qA.w);
+      const bool oBin = (cB < 32) && (rB < L.Hsq_hi), tBin = (cB < 32) && (rB < qB.w);
+      amb |= (oAin && rA >= L.Hsq_lo) || (tAin && rA >= fmaf(2.0f * aA.w, aA.w, -qA.w)) ||
+             (oBin && rB >= L.Hsq_lo) || (tBin && rB >= fmaf(2.0f * aB.w, aB.w, -qB.w));
+      bwd_pair2(L, make_float2(rA, rB), make_float2(dA.x, dB.x), make_float2(dA.y, dB.y),
+                make_float2(zA, zB), aA, aB, make_float2(oAin ? aA.x : 0.0f, oBin ? aB.x : 0.0f),
+                make_float2(tAin ? L.m : 0.0f, tBin ? L.m : 0.0f));
     }
     if (__any_sync(0xffffffffu, amb)) {
       if (amb) {
-        for (int kk = 0; kk < nk; kk++) {
-          unsigned mm = M[kk * 32 + lane];
-          while (mm != 0u) {
-            const int j = seg + 32 * kk + __ffs(mm) - 1;
-            mm &= mm - 1u;
-            const float4 q = Sx[j];
-            const float dx = L.x - q.x, dy = L.y - q.y, dz = L.z - q.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float4 aj = Sa[j];
-            const bool gown = r2 < L.Hsq_hi && r2 >= L.Hsq_lo;
-            const bool gtr = r2 < q.w && r2 >= fmaf(2.0f * aj.w, aj.w, -q.w);
-            if (gown || gtr) {
-              const int sj = jidx(j);
-              const bool out_o = gown && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L,
-                                                     g.gamma_d * (double)g.hs[L.si]);
-              const bool out_t = gtr && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L,
-                                                     g.gamma_d * (double)g.hs[sj]);
-              if (out_o || out_t)
-                bwd_pair(L, dx, dy, dz, r2, aj, out_o ? -aj.x : 0.0f, out_t ? -L.m : 0.0f);
-            }
+        unsigned mm = m0;
+        while (mm != 0u) {
+          const int c = __clz(mm);
+          mm &= ~(0x80000000u >> c);
+          const int e = base + c;
+          const float4 q = lds4_b(Sx + 16u * e);
+          const float4 aj = lds4_b(Sa + 16u * e);
+          float2 dxy;
+          float dz;
+          const float r2 = bwd_r2(L, q, dxy, dz);
+          const bool gown = r2 < L.Hsq_hi && r2 >= L.Hsq_lo;
+          const bool gtr = r2 < q.w && r2 >= fmaf(2.0f * aj.w, aj.w, -q.w);
+          if (gown || gtr) {
+            const int sj = jidx(e);
+            const bool out_o = gown && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L,
+                                                   g.gamma_d * (double)g.hs[L.si]);
+            const bool out_t = gtr && !guard_inside(g.pos64, L.si, sj, B.L, B.inv_L,
+                                                   g.gamma_d * (double)g.hs[sj]);
+            if (out_o || out_t)
+              bwd_pair(L, dxy.x, dxy.y, dz, r2, aj, out_o ? -aj.x : 0.0f, out_t ? -L.m : 0.0f);
           }
         }
       }
@@ -354,8 +435,7 @@ constexpr int kTinyBufB = 128;  // staged candidates per warp and pass
 constexpr int kTinyWarpBytesB =
     (kTinyBufB + kPad) * (16 + 16 + 4) + (int)((sizeof(TinySlots) + 15) / 16 * 16);
 
-__device__ __forceinline__ void tiny_phase_bwd(const GridDev& g, unsigned char* buf,
-                                               unsigned* __restrict__ M, int lane,
+__device__ __forceinline__ void tiny_phase_bwd(const GridDev& g, unsigned char* buf, int lane,
                                                const float* __restrict__ g_rho,
                                                const float* __restrict__ g_D,
                                                float* __restrict__ g_pos,
@@ -389,16 +469,17 @@ __device__ __forceinline__ void tiny_phase_bwd(const GridDev& g, unsigned char* 
         while (ts.off[q + 1] <= f) q++;
         float sx, sy, sz;
         const int sj = tiny_candidate(g, ts, q, f, edge, sx, sy, sz);
-        const float4 xe = g.bx[sj];
-        Sx[e] = make_float4(xe.x + sx, xe.y + sy, xe.z + sz, xe.w);
+        const float4 xe = g.bx[sj];  // negated offsets
+        Sx[e] = make_float4(xe.x - sx, xe.y - sy, xe.z - sz, xe.w);
         Sa[e] = g.ba[sj];
         Sj[e] = sj;
       }
       __syncwarp();
       auto jidx = [&](int j) { return Sj[j]; };
-      sweep_bwd(L, Sx, Sa, 0, len, M, lane, g, B, jidx);
+      sweep_bwd(L, smem_addr_b(Sx), smem_addr_b(Sa), 0, len, g, B, jidx);
       __syncwarp();  // the buffers are rewritten next
     }
+    laneb_fold(L);
     if (lane < na)
       write_bwd(g, ca + lane, (double)L.Sth, (double)L.Suh, (double)L.gx, (double)L.gy,
                 (double)L.gz, g_rho, g_D, g_pos, g_h, munit * g.m_max[g.cell_box[a]]);
@@ -417,12 +498,13 @@ struct CellSharedB {
 };
 
 constexpr int kCellWarps = kCellThreads / 32;
-constexpr int kCellFixedSmem = kCellWarps * kMaskChunks * 32 * 4;  // the warps' hit masks
-static_assert(kCellWarps * kTinyWarpBytesB <= kCellSmemFor[3] - kCellFixedSmem,
+static_assert(kCellWarps * kTinyWarpBytesB <= kCellSmemFor[3],
               "the tiny-cell buffers fit the smallest dynamic shared memory");
 
+// projection of a staged record (negated offsets) in the frame of slot (k, s):
+// the same FP32 expression the sort used for `dist`
 __device__ __forceinline__ float sproj(float4 x, float ux, float uy, float uz, int s, float off) {
-  return s * fmaf(x.x, ux, fmaf(x.y, uy, x.z * uz)) + off;
+  return s * fmaf(-x.x, ux, fmaf(-x.y, uy, -x.z * uz)) + off;
 }
 
 __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
@@ -434,8 +516,7 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ncells = *g.n_ccells;
   const float munit = (float)(16.0 / 3.14159265358979323846);
-  unsigned* Mw = reinterpret_cast<unsigned*>(dsm) + warp * kMaskChunks * 32;
-  float4* var = dsm + kCellFixedSmem / 16;
+  float4* var = dsm;
   for (;;) {
     if (tid == 0) cs.cell = atomicAdd(g.ccell_next, 1);
     __syncthreads();
@@ -550,8 +631,9 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
       auto jidx = [&](int j) {
         return cbq + (int)g.perm[kbq + order_pos(sl.s, J0q + j - s0, nbq)];
       };
-      sweep_bwd(L, Sx, Sa, lo, hi, Mw, lane, g, B, jidx);
+      sweep_bwd(L, smem_addr_b(Sx), smem_addr_b(Sa), lo, hi, g, B, jidx);
       // lanes whose windows held no pair in range have nothing to add
+      laneb_fold(L);
       if (valid && (L.Sth != 0.0f || L.Suh != 0.0f || L.gx != 0.0f || L.gy != 0.0f ||
                     L.gz != 0.0f)) {
         atomicAdd(&accs[il], __float2int_rn(L.Sth * ks));
@@ -573,7 +655,7 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
   }
   // then the tiny cells, one per warp, in the dynamic shared memory that the
   // cells no longer use (at least kCellWarps * kTinyWarpBytesB of it)
-  tiny_phase_bwd(g, reinterpret_cast<unsigned char*>(var) + warp * kTinyWarpBytesB, Mw, lane,
+  tiny_phase_bwd(g, reinterpret_cast<unsigned char*>(var) + warp * kTinyWarpBytesB, lane,
                  g_rho, g_D, g_pos, g_h);
 }
 
@@ -584,7 +666,6 @@ __global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
   __shared__ float4 s_a[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
   __shared__ int s_j[kTileJ + kPad];
-  __shared__ unsigned s_mask[kBlkI / 32][kMaskChunks * 32];
   __shared__ int s_task;
   if (*g.flags) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -636,10 +717,11 @@ __global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
         const int lo = (o == kSelfSlot) ? upper_bound_f(s_d, len, w_lo) : 0;
         const int hi = lower_bound_f(s_d, len, w_hi);
         auto jidx = [&](int j) { return s_j[j]; };
-        sweep_bwd(L, s_x, s_a, lo, hi, s_mask[warp], lane, g, B, jidx);
+        sweep_bwd(L, smem_addr_b(s_x), smem_addr_b(s_a), lo, hi, g, B, jidx);
       }
       __syncthreads();
     }
+    laneb_fold(L);
     if (valid && (L.Sth != 0.0f || L.Suh != 0.0f || L.gx != 0.0f || L.gy != 0.0f ||
                   L.gz != 0.0f)) {
       // 64-bit fixed point: the sum does not depend on the order of the tasks
@@ -712,7 +794,7 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   if ((e = cudaMemsetAsync(g.bwd_cmax, 0, g.ncell * sizeof(float), st)) != cudaSuccess) return e;
   k_bwd_prep<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_plan(g, 1, smem - kCellFixedSmem, kElemJ, kElemA, 0, st)) !=
+  if ((e = launch_plan(g, 1, smem, kElemJ, kElemA, 0, st)) !=
       cudaSuccess)
     return e;
   if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
