@@ -23,9 +23,9 @@
 //   dL/dh_i = (16/pi)/(h_i H_i^3) [ -g_i sum_j m_j th_i + (k_i/h_i) sum_j m_j uh_i ]
 //
 // Mapping: the cell-centric kernel of the forward pass (one CTA per cell, 27
-// staged windows, warps pulling (slot, run) items, candidates pre-filtered 8
-// at a time into bit masks), with both the own and the transposed cut-off in
-// the pre-filter; per-particle sums in 32-bit fixed-point shared-memory
+// staged windows, warps pulling (slot, run) items, candidates pre-filtered 32
+// at a time into per-lane hit masks held in registers), with both the own and
+// the transposed cut-off in the pre-filter; per-particle sums in 32-bit fixed-point shared-memory
 // accumulators (one integer addition per particle and work item, so the
 // result does not depend on which warp took which item).  A staged particle
 // takes 32 bytes ({x, y, z, H^2 + guard} and {m, G', K, H}), so three CTAs fit
