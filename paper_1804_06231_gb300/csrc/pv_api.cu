@@ -308,10 +308,7 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
   if (!g->sorted) return PV_ERR_NOT_SORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GridDev& d = g->d;
-  // ntask, task_next, n_ccells, ccell_next, n_tcells
-  PV_CUDA(cudaMemsetAsync(d.ntask, 0, 5 * sizeof(int32_t), st));
-  PV_CUDA(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned long long), st));
-  cudaEvent_t t0, t1;
+  cudaEvent_t t0, t1;  // (the plan kernel clears the pass's counters)
   PV_TRY(next_pair(g, 0, &t0, &t1));
   PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, g->ctas[0], st, t0, t1));
   g->launches += g->n > 0 ? 6 : 0;  // plan_slots, plan_cells, plan_tasks, cells, tasks, finalize_t
@@ -340,12 +337,11 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
   if (!g->sorted) return PV_ERR_NOT_SORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GridDev& d = g->d;
-  PV_CUDA(cudaMemsetAsync(d.ntask, 0, 5 * sizeof(int32_t), st));
   cudaEvent_t t0, t1;
   PV_TRY(next_pair(g, 1, &t0, &t1));
   PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, g->ctas[1], st, t0,
                               t1));
-  g->launches += g->n > 0 ? 7 : 0;  // prep, plan x3, cells, tasks, finalize_t
+  g->launches += g->n > 0 ? 7 : 0;  // plan x3, prep, cells, tasks, finalize_t
   return PV_OK;
 }
 

@@ -77,6 +77,7 @@ __device__ __forceinline__ TaskB decode_b(int4 t) {
 // (|G'| + |K|) H of the fixed-point units.
 __global__ void k_bwd_prep(GridDev g, const float* __restrict__ g_rho,
                            const float* __restrict__ g_D) {
+  pdl_enter();
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (*g.flags) return;  // the same for the whole warp
   int cell = -1;
@@ -510,6 +511,7 @@ __device__ __forceinline__ float sproj(float4 x, float ux, float uy, float uz, i
 __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
     GridDev g, const float* __restrict__ g_rho, const float* __restrict__ g_D,
     float* __restrict__ g_pos, float* __restrict__ g_h) {
+  pdl_enter();
   extern __shared__ float4 dsm[];
   __shared__ CellSharedB cs;
   if (*g.flags) return;
@@ -662,6 +664,7 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
 // ---- task kernel (cells too dense for the cell-centric kernel) ----------------------
 
 __global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
+  pdl_enter();
   __shared__ float4 s_x[kTileJ + kPad];
   __shared__ float4 s_a[kTileJ + kPad];
   __shared__ float s_d[kTileJ];
@@ -741,6 +744,7 @@ __global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
 __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
                                  const float* __restrict__ g_D, float* __restrict__ g_pos,
                                  float* __restrict__ g_h) {
+  pdl_enter();
   if (*g.flags) return;
   const float munit = (float)(16.0 / 3.14159265358979323846);
   long long* acc = g.gacc;
@@ -791,21 +795,17 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   if (e != cudaSuccess) return e;
   const int smem = kCellSmemFor[ctas_per_sm];
   const int nb = (g.n + 255) / 256;
-  if ((e = cudaMemsetAsync(g.bwd_cmax, 0, g.ncell * sizeof(float), st)) != cudaSuccess) return e;
-  k_bwd_prep<<<nb, 256, 0, st>>>(g, g_rho, g_drho_dh);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_plan(g, 1, smem, kElemJ, kElemA, 0, st)) !=
-      cudaSuccess)
-    return e;
+  // the plan (which also clears bwd_cmax) needs nothing of k_bwd_prep's
+  if ((e = launch_plan(g, 1, smem, kElemJ, kElemA, 0, st)) != cudaSuccess) return e;
+  PV_LAUNCH(k_bwd_prep, nb, 256, 0, st, g, g_rho, g_drho_dh);
   if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
-  k_backward_cells<<<num_sms * ctas_per_sm, kCellThreads, smem, st>>>(g, g_rho, g_drho_dh, g_pos,
-                                                                       g_h);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  PV_LAUNCH(k_backward_cells, num_sms * ctas_per_sm, kCellThreads, smem, st,
+            g, g_rho, g_drho_dh, g_pos, g_h);
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
-  k_backward_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_bwd_finalize_t<<<num_sms * 8, 256, 0, st>>>(g, g_rho, g_drho_dh, g_pos, g_h);
-  return cudaGetLastError();
+  PV_LAUNCH(k_backward_tasks, num_sms * 8, kBlkI, 0, st, g);
+  PV_LAUNCH(k_bwd_finalize_t, num_sms * 8, 256, 0, st, g, g_rho, g_drho_dh, g_pos,
+            g_h);
+  return cudaSuccess;
 }
 
 }  // namespace pv

@@ -84,7 +84,10 @@ __device__ __forceinline__ int count_below(const GridDev& g, int k, int s, int c
 // searches are independent and run in lockstep, so that their global loads
 // are in flight together; a grid with latched input errors gets empty plans.
 __global__ void k_plan_slots(GridDev g, int wide) {
+  pdl_enter();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  // the adjoint's per-cell term bounds are max-reduced afresh by k_bwd_prep
+  if (wide && g.bwd_cmax && idx < g.ncell) g.bwd_cmax[idx] = 0.0f;
   if (idx >= g.ncell * kNSlot) return;
   const uint32_t flagged = *g.flags;
   const int a = idx / kNSlot, o = idx % kNSlot;
@@ -127,9 +130,15 @@ __global__ void k_plan_slots(GridDev g, int wide) {
     }
   }
   g.plan[idx] = flagged ? make_int4(0, 0, 0, 0) : pl;
-  if (idx == 0) {  // k_plan_cells fills the list of tiny cells, the sweep takes them
+  if (idx == 0) {  // the routing lists and work counters of the pass start empty
     *g.n_ycells = 0;
     *g.ycell_next = 0;
+    *g.ntask = 0;
+    *g.task_next = 0;
+    *g.n_ccells = 0;
+    *g.ccell_next = 0;
+    *g.n_tcells = 0;
+    if (!wide) g.counters[0] = g.counters[1] = 0ull;  // interactions, FP64 re-decisions
   }
 }
 
@@ -141,6 +150,7 @@ __global__ void k_plan_slots(GridDev g, int wide) {
 // reservations are aggregated per warp (one atomic per warp and list instead
 // of one per cell: a clustered box has tens of thousands of cells).
 __global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a, int elem_i) {
+  pdl_enter();
   if (*g.flags) return;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -205,6 +215,7 @@ __global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a,
 // each task gets its particles [p0, p1) of a in the slot's order and the
 // window [j0, j1) of b that they can reach.
 __global__ void k_plan_tasks(GridDev g, int wide) {
+  pdl_enter();
   if (*g.flags) return;
   const int nt = *g.n_tcells;
   const int lane = threadIdx.x & 31;
@@ -625,6 +636,7 @@ __device__ __forceinline__ float staged_proj(unsigned a, float ux, float uy, flo
 __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, float* __restrict__ rho,
                                                                 float* __restrict__ drho_dh,
                                                                 int32_t* __restrict__ n_ngb) {
+  pdl_enter();
   extern __shared__ float4 dsm[];
   __shared__ CellShared cs;
   if (*g.flags) return;
@@ -810,6 +822,7 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
 // ---- task kernel (cells too dense for the cell-centric kernel) ---------------------
 
 __global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
+  pdl_enter();
   __shared__ __align__(16) float s_S[staged_floats(kTileJ)];
   __shared__ float s_d[kTileJ];
   __shared__ int s_j[kTileJ + kPad];
@@ -892,6 +905,7 @@ __global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
 // self slot has no such tasks: one block per task cell then.)
 __global__ void k_finalize_t(GridDev g, float* __restrict__ rho, float* __restrict__ drho_dh,
                              int32_t* __restrict__ n_ngb) {
+  pdl_enter();
   if (*g.flags) return;
   const int lane = threadIdx.x & 31;
   const float munit = (float)(16.0 / 3.14159265358979323846 * kFixInv);
@@ -934,6 +948,7 @@ __global__ void k_finalize_t(GridDev g, float* __restrict__ rho, float* __restri
 // window, no padding): |d_j - d_i| < H_i for the self slot, d_j < d_i + H_i
 // for a neighbour slot.
 __global__ void k_count_candidates(GridDev g) {
+  pdl_enter();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long cnt = 0;
   if (idx < g.ncell * kNSlot && !*g.flags) {
@@ -970,6 +985,7 @@ __global__ void k_count_candidates(GridDev g) {
 // ("candidates", counters[3]) and those with r_ij < max(H_i, H_j) (counters[4]),
 // j = i included.
 __global__ void k_count_adjoint(GridDev g) {
+  pdl_enter();
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   unsigned long long cand = 0, pairs = 0;
@@ -1030,6 +1046,7 @@ __global__ void k_count_adjoint(GridDev g) {
 // j != i with r < H_i into counters[9 + 2c].  One warp per (cell, slot), lanes
 // over the particles of the cell (diagnostic).
 __global__ void k_count_classes(GridDev g) {
+  pdl_enter();
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   unsigned long long cand = 0, inter = 0;
@@ -1088,22 +1105,20 @@ __global__ void k_count_classes(GridDev g) {
 cudaError_t launch_plan_slots(const GridDev& g, int wide, cudaStream_t st) {
   const int nthr = g.ncell * kNSlot;
   if (nthr == 0) return cudaSuccess;
-  k_plan_slots<<<(nthr + 255) / 256, 256, 0, st>>>(g, wide);
-  return cudaGetLastError();
+  PV_LAUNCH(k_plan_slots, (nthr + 255) / 256, 256, 0, st, g, wide);
+  return cudaSuccess;
 }
 
 cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j, int elem_a,
                         int elem_i, cudaStream_t st) {
   const int nthr = g.ncell * kNSlot;
-  k_plan_slots<<<(nthr + 255) / 256, 256, 0, st>>>(g, wide);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_plan_cells<<<(g.ncell + 127) / 128, 128, 0, st>>>(g, smem_budget, elem_j, elem_a, elem_i);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  PV_LAUNCH(k_plan_slots, (nthr + 255) / 256, 256, 0, st, g, wide);
+  PV_LAUNCH(k_plan_cells, (g.ncell + 127) / 128, 128, 0, st,
+            g, smem_budget, elem_j, elem_a, elem_i);
   // one warp per (task cell, slot): enough warps that the big cells' many
   // (cell, slot) pairs do not queue behind each other
-  k_plan_tasks<<<2048, 256, 0, st>>>(g, wide);
-  return cudaGetLastError();
+  PV_LAUNCH(k_plan_tasks, 2048, 256, 0, st, g, wide);
+  return cudaSuccess;
 }
 
 int64_t max_tasks_for(int64_t n, int64_t ncell) {
@@ -1122,25 +1137,21 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
   if ((e = launch_plan(g, 0, smem, kCellElemJ, kCellElemA, kCellElemI, st)) != cudaSuccess)
     return e;
   if (t0 && (e = cudaEventRecord(t0, st)) != cudaSuccess) return e;
-  k_density_cells<<<num_sms * ctas_per_sm, kCellThreads, smem, st>>>(g, rho, drho_dh, n_ngb);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  PV_LAUNCH(k_density_cells, num_sms * ctas_per_sm, kCellThreads, smem, st, g, rho, drho_dh,
+            n_ngb);
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
-  k_density_tasks<<<num_sms * 8, kBlkI, 0, st>>>(g);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_finalize_t<<<num_sms * 8, 256, 0, st>>>(g, rho, drho_dh, n_ngb);
-  return cudaGetLastError();
+  PV_LAUNCH(k_density_tasks, num_sms * 8, kBlkI, 0, st, g);
+  PV_LAUNCH(k_finalize_t, num_sms * 8, 256, 0, st, g, rho, drho_dh, n_ngb);
+  return cudaSuccess;
 }
 
 cudaError_t launch_count_candidates(const GridDev& g, cudaStream_t st) {
   const int nthr = g.ncell * kNSlot;
   if (nthr == 0) return cudaSuccess;
-  k_count_candidates<<<(nthr + 255) / 256, 256, 0, st>>>(g);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_count_adjoint<<<(nthr * 32 + 255) / 256, 256, 0, st>>>(g);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_count_classes<<<(nthr * 32 + 255) / 256, 256, 0, st>>>(g);
-  return cudaGetLastError();
+  PV_LAUNCH(k_count_candidates, (nthr + 255) / 256, 256, 0, st, g);
+  PV_LAUNCH(k_count_adjoint, (nthr * 32 + 255) / 256, 256, 0, st, g);
+  PV_LAUNCH(k_count_classes, (nthr * 32 + 255) / 256, 256, 0, st, g);
+  return cudaSuccess;
 }
 
 }  // namespace pv

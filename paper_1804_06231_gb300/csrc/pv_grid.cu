@@ -66,6 +66,7 @@ __device__ __forceinline__ double wrap_coord(double x, double L) {
 }
 
 __global__ void k_clear(GridDev g) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < g.ncell) g.cell_count[i] = 0;
   if (i < g.n_boxes) {
@@ -81,6 +82,7 @@ __global__ void k_clear(GridDev g) {
 
 __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
                       const float* __restrict__ m, float m_uniform) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   float mw = 0.0f;
   int bx = -1;
@@ -121,6 +123,7 @@ __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __
 // Single-CTA exclusive scan of the cell occupancies (C is at most a few
 // million; each thread scans a contiguous chunk).
 __global__ void __launch_bounds__(1024) k_scan(GridDev g) {
+  pdl_enter();
   __shared__ int s_part[1024];
   __shared__ int s_max[32];
   const int C = g.ncell, T = blockDim.x, t = threadIdx.x;
@@ -160,6 +163,7 @@ __global__ void __launch_bounds__(1024) k_scan(GridDev g) {
 }
 
 __global__ void k_scatter(GridDev g) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < g.n) g.orig[g.cell_start[g.pcell[p]] + g.prank[p]] = p;
 }
@@ -170,6 +174,7 @@ __global__ void k_scatter(GridDev g) {
 // sort raises the box's largest displacement.
 __global__ void k_update(GridDev g, const double* __restrict__ pos,
                          const float* __restrict__ h) {
+  pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   float disp = 0.0f;
   int bx = -1;
@@ -221,6 +226,7 @@ __global__ void k_update(GridDev g, const double* __restrict__ pos,
 // largest displacement since the sort), else the 27-cell stencil of the last
 // sort no longer holds all pairs in range.
 __global__ void k_update_check(GridDev g) {
+  pdl_enter();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell || g.cell_count[c] == 0) return;
   const int bx = g.cell_box[c];
@@ -362,6 +368,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g,
                                                             const float* __restrict__ h,
                                                             const float* __restrict__ m,
                                                             float m_uniform) {
+  pdl_enter();
   constexpr int kB = sort_small_buckets<kMax>();
   extern __shared__ float4 smem4[];
   __shared__ unsigned int s_hmax;
@@ -461,6 +468,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g,
 __global__ void __launch_bounds__(kSortTinyWarps * 32) k_cell_sort_tiny(
     GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
     const float* __restrict__ m, float m_uniform) {
+  pdl_enter();
   constexpr int kPer = kSortTinyMax / 32;
   __shared__ float4 s_x[kSortTinyWarps][kSortTinyMax];
   __shared__ float s_key[kSortTinyWarps][kSortTinyMax];
@@ -591,6 +599,7 @@ constexpr size_t kSortBigDynSmem =
 
 template <bool kStaged>
 __global__ void __launch_bounds__(kSortBigThreads, kStaged ? 2 : 1) k_sort_big(GridDev g) {
+  pdl_enter();
   __shared__ int s_bkt[kSortBigBuckets + kSortBigThreads];  // bucket b at bucket_slot(b, sh)
   __shared__ float s_red[2][32];
   __shared__ int s_scan[32];
@@ -690,34 +699,32 @@ __global__ void __launch_bounds__(kSortBigThreads, kStaged ? 2 : 1) k_sort_big(G
 cudaError_t launch_bin(const GridDev& g, const double* pos, const float* h, const float* m,
                        float m_uniform, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
-  k_bin<<<(g.n + 255) / 256, 256, 0, st>>>(g, pos, h, m, m_uniform);
-  return cudaGetLastError();
+  PV_LAUNCH(k_bin, (g.n + 255) / 256, 256, 0, st, g, pos, h, m, m_uniform);
+  return cudaSuccess;
 }
 
 cudaError_t launch_scan(const GridDev& g, cudaStream_t st) {
-  k_scan<<<1, 1024, 0, st>>>(g);
-  return cudaGetLastError();
+  PV_LAUNCH(k_scan, 1, 1024, 0, st, g);
+  return cudaSuccess;
 }
 
 cudaError_t launch_scatter(const GridDev& g, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
-  k_scatter<<<(g.n + 255) / 256, 256, 0, st>>>(g);
-  return cudaGetLastError();
+  PV_LAUNCH(k_scatter, (g.n + 255) / 256, 256, 0, st, g);
+  return cudaSuccess;
 }
 
 cudaError_t launch_update(const GridDev& g, const double* pos, const float* h, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
-  k_update<<<(g.n + 255) / 256, 256, 0, st>>>(g, pos, h);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_update_check<<<(g.ncell + 255) / 256, 256, 0, st>>>(g);
-  return cudaGetLastError();
+  PV_LAUNCH(k_update, (g.n + 255) / 256, 256, 0, st, g, pos, h);
+  PV_LAUNCH(k_update_check, (g.ncell + 255) / 256, 256, 0, st, g);
+  return cudaSuccess;
 }
 
 cudaError_t launch_clear(const GridDev& g, cudaStream_t st) {
   const int n = g.ncell > g.n_boxes ? g.ncell : g.n_boxes;
-  k_clear<<<(n + 255) / 256, 256, 0, st>>>(g);
-  return cudaGetLastError();
+  PV_LAUNCH(k_clear, (n + 255) / 256, 256, 0, st, g);
+  return cudaSuccess;
 }
 
 cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, const float* m,
@@ -726,11 +733,11 @@ cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, con
   cudaError_t e =
       set_max_dynamic_smem(reinterpret_cast<const void*>(&k_cell_sort<kSortSmallMax>), smem, st);
   if (e != cudaSuccess) return e;
-  k_cell_sort<kSortSmallMax><<<g.ncell, kSortThreads, smem, st>>>(g, pos, h, m, m_uniform);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_cell_sort_tiny<<<(g.ncell + kSortTinyWarps - 1) / kSortTinyWarps, kSortTinyWarps * 32, 0,
-                     st>>>(g, pos, h, m, m_uniform);
-  if ((e = cudaGetLastError()) != cudaSuccess || g.n == 0) return e;
+  PV_LAUNCH(k_cell_sort<kSortSmallMax>, g.ncell, kSortThreads, smem, st, g, pos, h, m,
+            m_uniform);
+  PV_LAUNCH(k_cell_sort_tiny, (g.ncell + kSortTinyWarps - 1) / kSortTinyWarps,
+            kSortTinyWarps * 32, 0, st, g, pos, h, m, m_uniform);
+  if (g.n == 0) return cudaSuccess;
   if ((e = set_max_dynamic_smem(reinterpret_cast<const void*>(&k_sort_big<true>),
                                 (int)kSortBigDynSmem, st)) != cudaSuccess)
     return e;
@@ -740,10 +747,9 @@ cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, con
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  k_sort_big<true><<<2 * sms, kSortBigThreads, kSortBigDynSmem, st>>>(g);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_sort_big<false><<<sms, kSortBigThreads, 0, st>>>(g);
-  return cudaGetLastError();
+  PV_LAUNCH_PLAIN(k_sort_big<true>, 2 * sms, kSortBigThreads, kSortBigDynSmem, st, g);
+  PV_LAUNCH_PLAIN(k_sort_big<false>, sms, kSortBigThreads, 0, st, g);
+  return cudaSuccess;
 }
 
 }  // namespace pv

@@ -491,6 +491,50 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
                             cudaStream_t st, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 constexpr int kDensityCtasDefault = 3, kBackwardCtasDefault = 3;
 
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_enter(): it waits until the grids it depends on have completed and their
+// writes are visible (a no-op for a kernel launched without the attribute),
+// then allows the next kernel of the stream to be scheduled.  A kernel launched
+// by PV_LAUNCH may therefore be resident while its predecessor still runs;
+// its threads do nothing before the wait, so the stream order of the results
+// is unchanged and only the launch latency overlaps.  The next grid is
+// scheduled only once every CTA of this one has started, so waiting CTAs can
+// never hold back a CTA they depend on.  (A kernel launched without the
+// attribute waits for its predecessor as usual; pdl_enter is then a no-op.)
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch_k(bool pdl, void (*kernel)(P...), unsigned grid, unsigned block,
+                            size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A&&>(args)...);
+}
+// launch_k(true, ...) / launch_k(false, ...) in a function returning
+// cudaError_t: returns its error.  PV_LAUNCH_PLAIN is for the kernels measured
+// slower as dependents (the persistent big-cell sorts on clustered boxes).
+#define PV_LAUNCH(...)                                        \
+  do {                                                        \
+    const cudaError_t pv_le_ = pv::launch_k(true, __VA_ARGS__); \
+    if (pv_le_ != cudaSuccess) return pv_le_;                 \
+  } while (0)
+#define PV_LAUNCH_PLAIN(...)                                   \
+  do {                                                         \
+    const cudaError_t pv_le_ = pv::launch_k(false, __VA_ARGS__); \
+    if (pv_le_ != cudaSuccess) return pv_le_;                  \
+  } while (0)
+
 // Raises `func`'s dynamic shared-memory limit to `bytes`.  The limit is an
 // attribute of the kernel in the current CUDA context, so it is set again on
 // every launch: a context created after cudaDeviceReset gets it too.  While

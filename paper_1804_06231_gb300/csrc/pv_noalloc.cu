@@ -71,6 +71,7 @@ T* carve(unsigned char*& cur, size_t count) {
 // the call.
 __global__ void k_static_setup(pv::BoxDev* box, pv::BoxDev val, int64_t* first, int32_t* cell_box,
                                int ncell) {
+  pv::pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     *box = val;

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(kRawThreads) k_raw_density(const float4* __res
                                                              const float4* __restrict__ xj,
                                                              int nj, float Hinv2, int reps,
                                                              float2* __restrict__ out) {
+  pdl_enter();
   __shared__ float4 s[kRawTile];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const float4 x = i < ni ? xi[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -55,6 +56,7 @@ constexpr int kProbeUnroll = 4;
 
 template <bool Packed>
 __global__ void __launch_bounds__(256) k_fp32_probe(int iters, float* __restrict__ sink) {
+  pdl_enter();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const float b = 0.99999994f, c = 1.0e-7f;
   float acc = 0.0f;

@@ -63,6 +63,7 @@ __device__ __forceinline__ Side side_terms(float r2, float hinv2, float dq, cons
 }
 
 __global__ void __launch_bounds__(kSymThreads) k_density_sym(GridDev g) {
+  pdl_enter();
   __shared__ SymShared sh;
   if (*g.flags) return;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(kSymThreads) k_density_sym(GridDev g) {
 // sums for the next pass.
 __global__ void k_sym_finalize(GridDev g, float* __restrict__ rho, float* __restrict__ drho_dh,
                                int32_t* __restrict__ n_ngb) {
+  pdl_enter();
   if (*g.flags) return;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long inter = 0;
@@ -241,10 +243,9 @@ cudaError_t launch_density_symmetric(const GridDev& g, float* rho, float* drho_d
   if (g.n == 0) return cudaSuccess;
   cudaError_t e = launch_plan_slots(g, 1, st);
   if (e != cudaSuccess) return e;
-  k_density_sym<<<num_sms * 4, kSymThreads, 0, st>>>(g);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_sym_finalize<<<(g.n + 255) / 256, 256, 0, st>>>(g, rho, drho_dh, n_ngb);
-  return cudaGetLastError();
+  PV_LAUNCH(k_density_sym, num_sms * 4, kSymThreads, 0, st, g);
+  PV_LAUNCH(k_sym_finalize, (g.n + 255) / 256, 256, 0, st, g, rho, drho_dh, n_ngb);
+  return cudaSuccess;
 }
 
 }  // namespace pv
