@@ -180,6 +180,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_TRY(dev_alloc(g, &d.bx, N));
   PV_TRY(dev_alloc(g, &d.ba, N));
   PV_TRY(dev_alloc(g, &d.bwd_cmax, C));
+  PV_TRY(dev_alloc(g, &d.bwd_hmin, C));
   PV_TRY(dev_alloc(g, &d.plan, (size_t)pv::kNSlot * C));
   PV_TRY(dev_alloc(g, &d.ccells, C));
   PV_TRY(dev_alloc(g, &d.tcells, C));

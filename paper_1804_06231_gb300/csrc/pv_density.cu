@@ -86,8 +86,12 @@ __device__ __forceinline__ int count_below(const GridDev& g, int k, int s, int c
 __global__ void k_plan_slots(GridDev g, int wide) {
   pdl_enter();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  // the adjoint's per-cell term bounds are max-reduced afresh by k_bwd_prep
-  if (wide && g.bwd_cmax && idx < g.ncell) g.bwd_cmax[idx] = 0.0f;
+  // the adjoint's per-cell term bounds and smallest supports are reduced
+  // afresh by k_bwd_prep
+  if (wide && g.bwd_cmax && idx < g.ncell) {
+    g.bwd_cmax[idx] = 0.0f;
+    g.bwd_hmin[idx] = 3.0e38f;
+  }
   if (idx >= g.ncell * kNSlot) return;
   const uint32_t flagged = *g.flags;
   const int a = idx / kNSlot, o = idx % kNSlot;
@@ -509,14 +513,8 @@ __device__ __forceinline__ void put_staged(float* S, int f, float4 x, float sx, 
 // sweep reads past the end)
 __host__ __device__ constexpr int staged_floats(int n) { return ((n + kPad + 3) >> 2) * kGroup; }
 
-__device__ __forceinline__ float warp_min(float v) {
-  for (int s = 16; s > 0; s >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, s));
-  return v;
-}
-__device__ __forceinline__ float warp_max(float v) {
-  for (int s = 16; s > 0; s >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, s));
-  return v;
-}
+__device__ __forceinline__ float warp_min(float v) { return warp_min_f(v); }
+__device__ __forceinline__ float warp_max(float v) { return warp_max_f(v); }
 
 // rho, drho/dh, n of one particle from its fixed-point sums (FP32 scaling)
 __device__ __forceinline__ void write_out(const GridDev& g, int s, long long ar, long long ad,

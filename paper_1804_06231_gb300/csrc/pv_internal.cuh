@@ -89,6 +89,7 @@ struct GridDev {
   // by the bound of its neighbourhood's terms)
   long long* gacc;
   float* bwd_cmax;   // [C] largest (|G'| + |K|) H of the cell's particles (adjoint term bound)
+  float* bwd_hmin;   // [C] smallest support H of the cell's particles (adjoint)
   float4* bx;        // [N] backward, cell order: {x', y', z', H^2 + guard}
   float4* ba;        // [N] backward, cell order: {m/m_max, g/H^5, k/(h H^5), H}
   // plan: per (cell, slot) {reachable count of a, window [J0, J1) of b, 0}
@@ -490,6 +491,22 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
                             float* g_pos, float* g_h, int num_sms, int ctas_per_sm,
                             cudaStream_t st, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 constexpr int kDensityCtasDefault = 3, kBackwardCtasDefault = 3;
+
+// Warp-wide min / max of a float by one integer reduction (redux.sync): the
+// map below is monotone from floats (no NaN) to signed integers and its own
+// inverse.
+__device__ __forceinline__ int float_order_key(float f) {
+  const int i = __float_as_int(f);
+  return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float warp_min_f(float v) {
+  return __int_as_float(float_order_key(__int_as_float(
+      __reduce_min_sync(0xffffffffu, float_order_key(v)))));
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+  return __int_as_float(float_order_key(__int_as_float(
+      __reduce_max_sync(0xffffffffu, float_order_key(v)))));
+}
 
 // Programmatic dependent launch.  Every kernel of the library starts with
 // pdl_enter(): it waits until the grids it depends on have completed and their

@@ -151,6 +151,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.ycell_next = sc + 11;
   d.gacc = nullptr;
   d.bwd_cmax = nullptr;
+  d.bwd_hmin = nullptr;
   d.bx = nullptr;
   d.ba = nullptr;
   d.n_boxes = 1;
