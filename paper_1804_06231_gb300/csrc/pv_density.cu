@@ -1138,7 +1138,9 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
   PV_LAUNCH(k_density_cells, num_sms * ctas_per_sm, kCellThreads, smem, st, g, rho, drho_dh,
             n_ngb);
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
-  PV_LAUNCH(k_density_tasks, num_sms * 8, kBlkI, 0, st, g);
+  // (a plain launch: as a dependent of the persistent cell kernel, the task
+  // kernel made the 4M clustered step 0.6 ms slower)
+  PV_LAUNCH_PLAIN(k_density_tasks, num_sms * 8, kBlkI, 0, st, g);
   PV_LAUNCH(k_finalize_t, num_sms * 8, 256, 0, st, g, rho, drho_dh, n_ngb);
   return cudaSuccess;
 }

@@ -540,7 +540,8 @@ inline cudaError_t launch_k(bool pdl, void (*kernel)(P...), unsigned grid, unsig
 }
 // launch_k(true, ...) / launch_k(false, ...) in a function returning
 // cudaError_t: returns its error.  PV_LAUNCH_PLAIN is for the kernels measured
-// slower as dependents (the persistent big-cell sorts on clustered boxes).
+// slower as dependents (the persistent big-cell sorts and the task kernels, on
+// clustered boxes).
 #define PV_LAUNCH(...)                                        \
   do {                                                        \
     const cudaError_t pv_le_ = pv::launch_k(true, __VA_ARGS__); \
