@@ -345,9 +345,9 @@ struct ChunkSkip {
   bool on;
 };
 constexpr int kSkipMinLen = 96;  // windows this long test their chunks
-// ... when the other cell's largest support exceeds every lane's support by
-// this factor (else the reach max(H_i, H_max of b) is already close to the
-// lanes' own and few chunks would be skipped)
+// ... in tasks whose other cell's largest support exceeds the smallest support
+// of the task's cell by this factor (else the reach max(H_i, H_max of b) is
+// close to the lanes' own and few chunks would be skipped)
 constexpr float kSkipRatio = 1.5f;
 
 // The warp's skip descriptor (the whole warp calls it): lane i at projection
@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
         const int hi = lower_bound_f(s_d, len, w_hi);
         auto jidx = [&](int j) { return s_j[j]; };
         ChunkSkip sk{};
-        if (skip_task && hi - lo >= kSkipMinLen && Hmax_b > kSkipRatio * warp_max_b(L.H))
+        if (skip_task && hi - lo >= kSkipMinLen)
           sk = chunk_skip(smem_addr_b(s_bs), 0, valid, di, L.H, padw);
         sweep_bwd(L, smem_addr_b(s_x), smem_addr_b(s_a), lo, hi, g, B, jidx, sk);
       }
