@@ -95,7 +95,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
     p.add_argument("--launch-shape", default="",
-                   help="D,B: CTAs per SM of the density and adjoint sweep kernels (no tuning)")
+                   help="D,B[,TD,TB]: CTAs per SM of the density and adjoint cell kernels and "
+                        "particles per task of their task kernels (no tuning)")
     p.add_argument("--workload", default="uniform1m", choices=["uniform1m", "clustered4m"],
                    help="the timed workload (clustered4m: for profiling the dense-cell paths)")
     p.add_argument("--no-extras", action="store_true",
@@ -307,7 +308,8 @@ def workload_extras(dev, flush, probe: dict, peak_derived: float, K: int = 5) ->
         out["clustered_4m"] = {
             "workload": f"clustered N={box.n}, {box.nc}^3 cells, 64 Gaussians + 20% uniform",
             "ms_per_step": t, "value": inter / (t * 1e-3), "unit": UNIT,
-            "launch_shape": [tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"]],
+            "launch_shape": [tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"],
+                             tr["density_task_block"], tr["backward_task_block"]],
             "max_cell_count": stc.max_cell_count,
             "breakdown_ms": {"sort": t_sort, "density": t_dens, "backward": t_bwd,
                              "step": t_step, "density_cell_kernel": k_dens,
@@ -339,7 +341,8 @@ def workload_extras(dev, flush, probe: dict, peak_derived: float, K: int = 5) ->
     for b in boxes:
         sl = slice(first, first + b.n)
         gg = Grid((b.n, b.L, b.nc))
-        gg.set_tuning(tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"])
+        gg.set_tuning(tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"],
+                      tr["density_task_block"], tr["backward_task_block"])
         views.append((gg, pos[sl], h[sl], m[sl], gr[sl], gd[sl], rho[sl], D[sl], nn[sl],
                       gp[sl], gh[sl]))
         first += b.n
@@ -368,7 +371,8 @@ def workload_extras(dev, flush, probe: dict, peak_derived: float, K: int = 5) ->
                     "[4096, 524288], uniform or clustered)",
         "ms_per_step_batched": t_b, "ms_per_step_per_box": t_p, "ms_per_step_graph": t_g,
         "value": inter / (t_g * 1e-3), "unit": UNIT,
-        "launch_shape": [tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"]]}
+        "launch_shape": [tr["density_ctas_per_sm"], tr["backward_ctas_per_sm"],
+                         tr["density_task_block"], tr["backward_task_block"]]}
     return out
 
 
@@ -645,15 +649,16 @@ def main():
     shape0 = grid.tuning()
     step()  # first sort, so that the autotuner sees the sorted grid
     if args.launch_shape:
-        d_ctas, b_ctas = (int(x) for x in args.launch_shape.split(","))
-        grid.set_tuning(d_ctas, b_ctas)
-        tuning = {"density_ctas_per_sm": d_ctas, "backward_ctas_per_sm": b_ctas,
-                  "source": "given"}
+        vals = [int(x) for x in args.launch_shape.split(",")] + [0, 0]
+        grid.set_tuning(*vals[:4])
+        t = grid.tuning()
+        tuning = {"density_ctas_per_sm": t[0], "backward_ctas_per_sm": t[1],
+                  "density_task_block": t[2], "backward_task_block": t[3], "source": "given"}
     elif not args.no_tune:
         from paper_1804_06231_gb300 import tune
         tr = tune.autotune(grid, g_rho, g_d, reps=5)
-        tuning = {"density_ctas_per_sm": tr["density_ctas_per_sm"],
-                  "backward_ctas_per_sm": tr["backward_ctas_per_sm"], "source": tr["source"]}
+        tuning = {k: tr[k] for k in ("density_ctas_per_sm", "backward_ctas_per_sm",
+                                     "density_task_block", "backward_task_block", "source")}
     for _ in range(max(args.warmup, 3)):
         step()
     grid.sync()
@@ -844,6 +849,8 @@ def main():
                        "l2": "flushed between steps (512 MiB write)",
                        "launch_shape": tuning or {"density_ctas_per_sm": shape0[0],
                                                   "backward_ctas_per_sm": shape0[1],
+                                                  "density_task_block": shape0[2],
+                                                  "backward_task_block": shape0[3],
                                                   "source": "default"},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "e2e": e2e,

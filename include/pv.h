@@ -204,17 +204,24 @@ pv_status pv_grid_sync(pv_grid* g, void* stream);
    PV_ERR_DEVICE when device_flags is non-zero (out is still filled). */
 pv_status pv_grid_stats(pv_grid* g, pv_stats* out);
 
-/* Launch shape of the two cell-centric sweep kernels (the paper has no
-   counterpart; its method is the same for every value).  The number of
-   resident CTAs per SM sets each kernel's shared memory, and with it which
-   cells are swept by the cell-centric kernel (their 27 windows fit) and which
-   by the task kernel: fewer CTAs = more shared memory per cell, more CTAs =
-   more warps to hide latency.  (Cells of at most 32 particles always go to
-   a warp-per-cell kernel.)  0 selects the default. */
+/* Launch shape of the sweeps (the paper has no counterpart; its method is
+   the same for every value).  Per pass, two bins have a shape:
+   - the cells whose 27 windows fit a cell-centric CTA's shared memory: the
+     number of resident CTAs per SM sets each kernel's shared memory, and with
+     it which cells fit; fewer CTAs = more shared memory per cell, more CTAs =
+     more warps to hide latency;
+   - the other (dense) cells, split into tasks (cell, slot, block of
+     particles of a): the block size is the task's particle count and its
+     CTA's thread count (64, 128 or 256: 2, 4 or 8 warps per task), with
+     16, 8, 4 such CTAs per SM for the density and 14, 7, 3 for the adjoint.
+   (Cells of at most 32 particles always go to one warp each.)  0 selects the
+   default. */
 typedef struct {
   int32_t density_ctas_per_sm;   /* 1..4 (default 3) */
   int32_t backward_ctas_per_sm;  /* 1..3 (default 3) */
-  int32_t reserved[6];           /* must be 0 */
+  int32_t density_task_block;    /* 64, 128 or 256 (default 128) */
+  int32_t backward_task_block;   /* 64, 128 or 256 (default 128) */
+  int32_t reserved[4];           /* must be 0 */
 } pv_tuning;
 
 /* Sets the launch shape used by later pv_density / pv_density_backward calls

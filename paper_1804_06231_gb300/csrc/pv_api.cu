@@ -23,6 +23,7 @@ struct pv_grid {
   size_t bytes = 0;
   int64_t launches = 0;  // kernels launched by this grid so far
   int ctas[2] = {pv::kDensityCtasDefault, pv::kBackwardCtasDefault};  // sweep CTAs per SM
+  int task_blk[2] = {pv::kTaskBlkDefault, pv::kTaskBlkDefault};        // particles per task
   // sweep timing (pv_grid_time_sweeps): a ring of event pairs per sweep kind
   static constexpr int kRing = 64;
   bool timing = false;
@@ -188,6 +189,7 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   const int64_t mt = pv::max_tasks_for(n, ncell);
   if (mt > 0x7fffffffLL) return PV_ERR_TOO_LARGE;
   d.max_tasks = (int32_t)mt;
+  d.task_blk = pv::kTaskBlkDefault;
   d.slot_mask = pv::kAllSlots;
   d.moved = 0;
   PV_TRY(dev_alloc(g, &d.tasks, (size_t)d.max_tasks));
@@ -311,6 +313,7 @@ pv_status pv_density(pv_grid* g, float* rho, float* drho_dh, int32_t* n_ngb, voi
   GridDev& d = g->d;
   cudaEvent_t t0, t1;  // (the plan kernel clears the pass's counters)
   PV_TRY(next_pair(g, 0, &t0, &t1));
+  d.task_blk = g->task_blk[0];
   PV_CUDA(pv::launch_density(d, rho, drho_dh, n_ngb, g->num_sms, g->ctas[0], st, t0, t1));
   g->launches += g->n > 0 ? 6 : 0;  // plan_slots, plan_cells, plan_tasks, cells, tasks, finalize_t
   return PV_OK;
@@ -340,6 +343,7 @@ pv_status pv_density_backward(pv_grid* g, const float* g_rho, const float* g_drh
   GridDev& d = g->d;
   cudaEvent_t t0, t1;
   PV_TRY(next_pair(g, 1, &t0, &t1));
+  d.task_blk = g->task_blk[1];
   PV_CUDA(pv::launch_backward(d, g_rho, g_drho_dh, g_pos, g_h, g->num_sms, g->ctas[1], st, t0,
                               t1));
   g->launches += g->n > 0 ? 7 : 0;  // plan x3, prep, cells, tasks, finalize_t
@@ -396,9 +400,15 @@ pv_status pv_grid_set_tuning(pv_grid* g, const pv_tuning* t) {
     if (r != 0) return PV_ERR_INVALID_ARGUMENT;
   const int d = t->density_ctas_per_sm ? t->density_ctas_per_sm : pv::kDensityCtasDefault;
   const int b = t->backward_ctas_per_sm ? t->backward_ctas_per_sm : pv::kBackwardCtasDefault;
-  if (d < 1 || d > 4 || b < 1 || b > 3) return PV_ERR_INVALID_ARGUMENT;
+  const int td = t->density_task_block ? t->density_task_block : pv::kTaskBlkDefault;
+  const int tb = t->backward_task_block ? t->backward_task_block : pv::kTaskBlkDefault;
+  auto blk_ok = [](int v) { return v == 64 || v == 128 || v == 256; };
+  if (d < 1 || d > 4 || b < 1 || b > 3 || !blk_ok(td) || !blk_ok(tb))
+    return PV_ERR_INVALID_ARGUMENT;
   g->ctas[0] = d;
   g->ctas[1] = b;
+  g->task_blk[0] = td;
+  g->task_blk[1] = tb;
   return PV_OK;
 }
 
@@ -407,6 +417,8 @@ pv_status pv_grid_get_tuning(const pv_grid* g, pv_tuning* out) {
   std::memset(out, 0, sizeof(*out));
   out->density_ctas_per_sm = g->ctas[0];
   out->backward_ctas_per_sm = g->ctas[1];
+  out->density_task_block = g->task_blk[0];
+  out->backward_task_block = g->task_blk[1];
   return PV_OK;
 }
 

@@ -40,7 +40,6 @@ namespace pv {
 
 namespace {
 
-constexpr int kBlkI = 128;   // must match the plan kernel
 constexpr int kTileJ = 512;
 constexpr int kCellThreads = 256;
 // dynamic shared memory of k_backward_cells for 1 to 3 resident CTAs per SM
@@ -618,7 +617,7 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
     int* accs = reinterpret_cast<int*>(accg + 3 * na);                  // [2][na]
     const float ks = fix_scale_s32(total);
     const float kg = fix_scale_g64(cs.bn, (float)(total + 1));
-    stage_flat<4>(
+    stage_flat<8>(  // eight index lookups in flight per thread (latency-bound)
         cs.off, total, tid, kCellThreads,
         [&](int f, int q) {
           const Slot sl = slot_info(c_border[q]);
@@ -711,7 +710,9 @@ __global__ void __launch_bounds__(kCellThreads, 3) k_backward_cells(
 
 // ---- task kernel (cells too dense for the cell-centric kernel) ----------------------
 
-__global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
+// BlkI particles (and threads) per task, as g.task_blk (the plan's).
+template <int BlkI>
+__global__ void __launch_bounds__(BlkI, 896 / BlkI) k_backward_tasks(GridDev g) {
   pdl_enter();
   __shared__ float4 s_x[kTileJ + kPad];
   __shared__ float4 s_a[kTileJ + kPad];
@@ -770,7 +771,7 @@ __global__ void __launch_bounds__(kBlkI, 7) k_backward_tasks(GridDev g) {
       __syncthreads();
       // the tile's chunk summaries (blocks of 32 from the tile start; the
       // projections are the sort's, as the lanes' d_i)
-      for (int bi = warp; skip_task && bi < ((len + 31) >> 5); bi += kBlkI / 32) {
+      for (int bi = warp; skip_task && bi < ((len + 31) >> 5); bi += BlkI / 32) {
         const int e = (bi << 5) + lane;
         float dmn = 3.0e38f, dmx = -3.0e38f, lmn = 3.0e38f, rmx = -3.0e38f;
         if (e < len) {
@@ -830,7 +831,7 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
               acc[4 * N + s] * ig, g_rho, g_D, g_pos, g_h, mscale);
     for (int q = 0; q < 5; q++) acc[q * N + s] = 0;
   };
-  // as the forward finalize: one warp per self-slot task (blocks of kBlkI
+  // as the forward finalize: one warp per self-slot task (blocks of g.task_blk
   // cell-local indices), or one block per task cell when the self slot is
   // masked out
   if ((g.slot_mask >> kSelfSlot) & 1u) {
@@ -877,7 +878,11 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
   // (a plain launch: as a dependent of the persistent cell kernel, the task
   // kernel made the 4M clustered step 0.6 ms slower)
-  PV_LAUNCH_PLAIN(k_backward_tasks, num_sms * 8, kBlkI, 0, st, g);
+  switch (g.task_blk) {
+    case 64: PV_LAUNCH_PLAIN(k_backward_tasks<64>, num_sms * 16, 64, 0, st, g); break;
+    case 256: PV_LAUNCH_PLAIN(k_backward_tasks<256>, num_sms * 4, 256, 0, st, g); break;
+    default: PV_LAUNCH_PLAIN(k_backward_tasks<128>, num_sms * 8, 128, 0, st, g); break;
+  }
   PV_LAUNCH(k_bwd_finalize_t, num_sms * 8, 256, 0, st, g, g_rho, g_drho_dh, g_pos,
             g_h);
   return cudaSuccess;

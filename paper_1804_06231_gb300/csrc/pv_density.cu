@@ -37,7 +37,6 @@ namespace pv {
 
 namespace {
 
-constexpr int kBlkI = 128;       // particles of a per task (task path)
 constexpr int kTileJ = 512;      // particles of b per tile (task path)
 constexpr int kCellThreads = 256;
 // dynamic shared memory of k_density_cells for 1..4 resident CTAs per SM (the
@@ -149,7 +148,7 @@ __global__ void k_plan_slots(GridDev g, int wide) {
 // One thread per cell: route a cell of at most kTinyCell particles to the
 // warp-per-cell kernel, any other cell to the cell-centric kernel when its
 // staged windows fit `smem_budget`, else to the task kernel, reserving one
-// task of kBlkI particles per block of each slot (the first task's index goes
+// task of g.task_blk particles per block of each slot (the first task's index goes
 // to plan.w; k_plan_tasks fills the tasks in).  The list appends and the task
 // reservations are aggregated per warp (one atomic per warp and list instead
 // of one per cell: a clustered box has tens of thousands of cells).
@@ -174,7 +173,7 @@ __global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a,
       }
       fits = elem_j * (total + kPad + 4) + elem_a * na + elem_i * sum_i + 16 <= smem_budget;
       if (!fits)
-        for (int o = 0; o < kNSlot; o++) nblk_tot += (pl[o].x + kBlkI - 1) / kBlkI;
+        for (int o = 0; o < kNSlot; o++) nblk_tot += (pl[o].x + g.task_blk - 1) / g.task_blk;
     }
   }
   const bool task = na > 0 && !tiny && !fits;
@@ -211,11 +210,11 @@ __global__ void k_plan_cells(GridDev g, int smem_budget, int elem_j, int elem_a,
     const int nI = pl[o].x;
     if (nI == 0) continue;
     pl[o].w = base;
-    base += (nI + kBlkI - 1) / kBlkI;
+    base += (nI + g.task_blk - 1) / g.task_blk;
   }
 }
 
-// One warp per (task cell, slot), lanes over its blocks of kBlkI particles:
+// One warp per (task cell, slot), lanes over its blocks of g.task_blk particles:
 // each task gets its particles [p0, p1) of a in the slot's order and the
 // window [j0, j1) of b that they can reach.
 __global__ void k_plan_tasks(GridDev g, int wide) {
@@ -239,9 +238,9 @@ __global__ void k_plan_tasks(GridDev g, int wide) {
     if (wide) reach = fmaxf(reach, g.cell_Hmax[b]);
     reach += window_pad(g, B, g.cell_box[a]);
     const float off = sl.v2 ? vnorm(sl.v2) * B.edge_f : 0.0f;
-    const int nblk = (nI + kBlkI - 1) / kBlkI;
+    const int nblk = (nI + g.task_blk - 1) / g.task_blk;
     for (int bk = lane; bk < nblk; bk += 32) {
-      const int p0 = bk * kBlkI, p1 = min(nI, p0 + kBlkI);
+      const int p0 = bk * g.task_blk, p1 = min(nI, p0 + g.task_blk);
       int j0, j1;
       if (o == kSelfSlot) {
         // upper bound of d[p0] - reach and lower bound of d[p1 - 1] + reach,
@@ -695,7 +694,8 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
     int* acc_n = reinterpret_cast<int*>(acc_d + na);                   // [na]
     uint16_t* SI = reinterpret_cast<uint16_t*>(acc_n + na);            // [sumI]
     // stage the 27 windows in sorted order (synchronous loads, three lookups
-    // in flight per thread), the slots' particle lists of a, and cell a
+    // in flight per thread: more would spill at this kernel's 64 registers),
+    // the slots' particle lists of a, and cell a
     stage_flat<3>(
         cs.off, total, tid, kCellThreads,
         [&](int f, int q) {
@@ -819,7 +819,9 @@ __global__ void __launch_bounds__(kCellThreads, 4) k_density_cells(GridDev g, fl
 
 // ---- task kernel (cells too dense for the cell-centric kernel) ---------------------
 
-__global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
+// BlkI particles (and threads) per task; 1024 threads per SM for every BlkI.
+template <int BlkI>
+__global__ void __launch_bounds__(BlkI, 1024 / BlkI) k_density_tasks(GridDev g) {
   pdl_enter();
   __shared__ __align__(16) float s_S[staged_floats(kTileJ)];
   __shared__ float s_d[kTileJ];
@@ -897,7 +899,7 @@ __global__ void __launch_bounds__(kBlkI, 8) k_density_tasks(GridDev g) {
 }
 
 // Fixed point -> caller order for the particles of the task-path cells.  The
-// self-slot tasks of a cell cover its positions [0, na) in blocks of kBlkI,
+// self-slot tasks of a cell cover its positions [0, na) in blocks of g.task_blk,
 // so one warp per self-slot task finalises cell-local indices [p0, p1): big
 // cells are spread over many warps.  (A pass whose slot mask leaves out the
 // self slot has no such tasks: one block per task cell then.)
@@ -1120,7 +1122,7 @@ cudaError_t launch_plan(const GridDev& g, int wide, int smem_budget, int elem_j,
 }
 
 int64_t max_tasks_for(int64_t n, int64_t ncell) {
-  return (int64_t)kNSlot * (n / kBlkI + ncell) + 64;
+  return (int64_t)kNSlot * (n / kTaskBlkMin + ncell) + 64;
 }
 
 cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t* n_ngb,
@@ -1140,7 +1142,11 @@ cudaError_t launch_density(const GridDev& g, float* rho, float* drho_dh, int32_t
   if (t1 && (e = cudaEventRecord(t1, st)) != cudaSuccess) return e;
   // (a plain launch: as a dependent of the persistent cell kernel, the task
   // kernel made the 4M clustered step 0.6 ms slower)
-  PV_LAUNCH_PLAIN(k_density_tasks, num_sms * 8, kBlkI, 0, st, g);
+  switch (g.task_blk) {
+    case 64: PV_LAUNCH_PLAIN(k_density_tasks<64>, num_sms * 16, 64, 0, st, g); break;
+    case 256: PV_LAUNCH_PLAIN(k_density_tasks<256>, num_sms * 4, 256, 0, st, g); break;
+    default: PV_LAUNCH_PLAIN(k_density_tasks<128>, num_sms * 8, 128, 0, st, g); break;
+  }
   PV_LAUNCH(k_finalize_t, num_sms * 8, 256, 0, st, g, rho, drho_dh, n_ngb);
   return cudaSuccess;
 }

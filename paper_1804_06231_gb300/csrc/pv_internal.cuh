@@ -107,6 +107,7 @@ struct GridDev {
   int32_t* ntask;
   int32_t* task_next;
   int32_t max_tasks;
+  int32_t task_blk;    // particles of a per task of the pass (64, 128 or 256)
   uint32_t slot_mask;  // neighbour slots the sweeps visit (bit o of slot o; all 27 normally)
   int32_t moved;       // positions updated since the sort: windows use the stored projections
   // scalars
@@ -491,6 +492,9 @@ cudaError_t launch_backward(const GridDev& g, const float* g_rho, const float* g
                             float* g_pos, float* g_h, int num_sms, int ctas_per_sm,
                             cudaStream_t st, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 constexpr int kDensityCtasDefault = 3, kBackwardCtasDefault = 3;
+// particles per task of the task path: the default and the smallest (which
+// sizes the task array)
+constexpr int kTaskBlkDefault = 128, kTaskBlkMin = 64;
 
 // Warp-wide min / max of a float by one integer reduction (redux.sync): the
 // map below is monotone from floats (no NaN) to signed integers and its own

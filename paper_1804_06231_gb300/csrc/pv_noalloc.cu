@@ -39,7 +39,7 @@ constexpr size_t scratch_bytes(int64_t n, int64_t c) {
          align_up(N * sizeof(int32_t)) + align_up(3 * N * sizeof(double)) +
          align_up(pv::kNDir * N * sizeof(uint16_t)) + align_up(pv::kNDir * N * sizeof(float)) +
          align_up(3 * N * sizeof(long long)) +
-         align_up((size_t)((int64_t)pv::kNSlot * (n / 128 + c) + 64) * sizeof(int4)) +
+         align_up((size_t)((int64_t)pv::kNSlot * (n / pv::kTaskBlkMin + c) + 64) * sizeof(int4)) +
          align_up(16 * sizeof(int32_t)) + align_up(16 * sizeof(unsigned long long));
 }
 
@@ -131,6 +131,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.dist = carve<float>(cur, pv::kNDir * N);
   d.acc = carve<long long>(cur, 3 * N);
   d.max_tasks = (int32_t)pv::max_tasks_for(n, ncell);
+  d.task_blk = pv::kTaskBlkDefault;
   d.slot_mask = pv::kAllSlots;
   d.moved = 0;
   d.tasks = carve<int4>(cur, (size_t)d.max_tasks);

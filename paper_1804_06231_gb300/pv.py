@@ -68,7 +68,8 @@ class pv_stats(ctypes.Structure):
 
 class pv_tuning(ctypes.Structure):
     _fields_ = [("density_ctas_per_sm", ctypes.c_int32), ("backward_ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("density_task_block", ctypes.c_int32), ("backward_task_block", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -190,16 +191,19 @@ def pv_density_static(pos: int, h: int, m: int | None, m_uniform: float, n: int,
                                             n_ngb, flags_out, stream), "pv_density_static")
 
 
-def pv_grid_set_tuning(grid: int, density_ctas_per_sm: int = 0,
-                       backward_ctas_per_sm: int = 0) -> None:
-    t = pv_tuning(int(density_ctas_per_sm), int(backward_ctas_per_sm))
+def pv_grid_set_tuning(grid: int, density_ctas_per_sm: int = 0, backward_ctas_per_sm: int = 0,
+                       density_task_block: int = 0, backward_task_block: int = 0) -> None:
+    t = pv_tuning(int(density_ctas_per_sm), int(backward_ctas_per_sm), int(density_task_block),
+                  int(backward_task_block))
     _check(load_library().pv_grid_set_tuning(grid, ctypes.byref(t)), "pv_grid_set_tuning")
 
 
-def pv_grid_get_tuning(grid: int) -> tuple[int, int]:
+def pv_grid_get_tuning(grid: int) -> tuple[int, int, int, int]:
+    """(density CTAs per SM, adjoint CTAs per SM, density task block, adjoint task block)"""
     t = pv_tuning()
     _check(load_library().pv_grid_get_tuning(grid, ctypes.byref(t)), "pv_grid_get_tuning")
-    return t.density_ctas_per_sm, t.backward_ctas_per_sm
+    return (t.density_ctas_per_sm, t.backward_ctas_per_sm, t.density_task_block,
+            t.backward_task_block)
 
 
 SLOT_MASK_ALL = (1 << 27) - 1
@@ -403,11 +407,20 @@ class Grid:
     def sync(self, stream=None) -> None:
         pv_grid_sync(self.handle, self._stream(stream))
 
-    def set_tuning(self, density_ctas_per_sm: int = 0, backward_ctas_per_sm: int = 0) -> None:
-        """CTAs per SM of the two cell-centric sweep kernels (0 = default)."""
-        pv_grid_set_tuning(self.handle, density_ctas_per_sm, backward_ctas_per_sm)
+    def set_tuning(self, density_ctas_per_sm: int = 0, backward_ctas_per_sm: int = 0,
+                   density_task_block: int | None = None,
+                   backward_task_block: int | None = None) -> None:
+        """CTAs per SM of the two cell-centric sweep kernels (0 = default) and
+        particles per task of the two task kernels (64, 128 or 256; 0 =
+        default, None = keep the current value)."""
+        cur = self.tuning()
+        pv_grid_set_tuning(self.handle, density_ctas_per_sm, backward_ctas_per_sm,
+                           cur[2] if density_task_block is None else density_task_block,
+                           cur[3] if backward_task_block is None else backward_task_block)
 
-    def tuning(self) -> tuple[int, int]:
+    def tuning(self) -> tuple[int, int, int, int]:
+        """(density CTAs per SM, adjoint CTAs per SM, density task block,
+        adjoint task block)"""
         return pv_grid_get_tuning(self.handle)
 
     def set_slot_mask(self, mask: int = SLOT_MASK_ALL) -> None:

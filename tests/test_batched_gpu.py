@@ -153,9 +153,11 @@ def test_cuda_graph_replay_matches_eager():
 
 
 def test_launch_shapes_meet_parity_and_autotune(oracle_lib, tmp_path):
-    """Every launch shape of the sweep kernels (which moves dense cells between
-    the cell-centric and the task kernels) meets the parity bar against the
-    oracle; the autotuner picks one of them, sets it and caches it."""
+    """Launch shapes of the sweeps (CTAs per SM of the cell kernels, which
+    moves dense cells between the cell-centric and the task kernels, and
+    particles per task of the task kernels) meet the parity bar against the
+    oracle, out-of-range shapes are refused, and the autotuner picks a shape,
+    sets it and caches it."""
     import torch
     from paper_1804_06231_gb300 import tune
     from paper_1804_06231_gb300.pv import Grid
@@ -174,10 +176,11 @@ def test_launch_shapes_meet_parity_and_autotune(oracle_lib, tmp_path):
     rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
     with Grid((box.n, box.L, box.nc)) as g:
         g.sort(pos, h, m)
-        assert g.tuning() == tune.DEFAULT
-        for d, b in ((2, 1), (3, 2), (4, 3), (4, 1)):
-            g.set_tuning(d, b)
-            assert g.tuning() == (d, b)
+        assert g.tuning() == (*tune.DEFAULT, tune.DEFAULT_TASK, tune.DEFAULT_TASK)
+        for d, b, td, tb in ((2, 1, 64, 256), (3, 2, 128, 64), (4, 3, 256, 128), (4, 1, 64, 64),
+                             (2, 1, 256, 256)):
+            g.set_tuning(d, b, td, tb)
+            assert g.tuning() == (d, b, td, tb)
             rho, D, n = g.density()
             gp, gh = g.backward(gr, gd)
             g.sync()
@@ -190,9 +193,14 @@ def test_launch_shapes_meet_parity_and_autotune(oracle_lib, tmp_path):
             g.set_tuning(5, 2)
         with pytest.raises(PvError):
             g.set_tuning(3, 4)
+        with pytest.raises(PvError):
+            g.set_tuning(3, 3, 96, 128)
+        with pytest.raises(PvError):
+            g.set_tuning(3, 3, 128, 512)
         path = str(tmp_path / "tuning.json")
         r1 = tune.autotune(g, gr, gd, reps=2, cache_path=path)
         assert r1["source"] == "timed"
-        assert g.tuning() == (r1["density_ctas_per_sm"], r1["backward_ctas_per_sm"])
+        assert g.tuning() == (r1["density_ctas_per_sm"], r1["backward_ctas_per_sm"],
+                              r1["density_task_block"], r1["backward_task_block"])
         r2 = tune.autotune(g, gr, gd, reps=2, cache_path=path)
         assert r2["source"] == "cache" and r2["signature"] == r1["signature"]
