@@ -321,7 +321,8 @@ def workload_extras(dev, flush, probe: dict, peak_derived: float, K: int = 5) ->
             "roofline_density_pass": sweep_roofline("pv_density (all its kernels)", fw[0], fw[1],
                                                     t_dens, probe, peak_derived),
             "roofline_adjoint_pass": sweep_roofline("pv_density_backward (all its kernels)",
-                                                    bw[0], bw[1], t_bwd, probe, peak_derived)}
+                                                    bw[0], bw[1], t_bwd, probe, peak_derived),
+            "roofline_sort": sort_roofline(box.n, t_sort, measured_peaks())}
     del pos, h, m, gr, gd, rho, D, nn, gp, gh
     torch.cuda.empty_cache()
 
@@ -434,6 +435,24 @@ def sweep_roofline(kernel: str, flops: float, insts: float, ms: float, probe: di
             "peak_derived_tflops": derived_tflops,
             "instructions": {"achieved": ai, "peak": pi, "unit": "T FP32 inst/s",
                              "frac": ai / pi, "inst_per_launch": insts}}
+
+
+# Algorithmic HBM bytes per particle of pv_sort_cells: the grid build reads
+# position, h and mass (32 B) and writes the cell-order record and h (24 B);
+# the 13-axis sort reads the record (16 B) and writes 13 16-bit indices (26 B).
+SORT_BYTES_PER_PARTICLE = 32 + 24 + 16 + 26
+
+
+def sort_roofline(n: int, ms: float, peaks: dict) -> dict:
+    """HBM roofline of pv_sort_cells (all its kernels): algorithmic bytes per
+    sort over its CUDA-event time, against the measured copy bandwidth."""
+    b = SORT_BYTES_PER_PARTICLE * n
+    a = b / (ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs")
+    return {"bound": "hbm", "kernel": "pv_sort_cells (all its kernels)", "achieved": a,
+            "peak": peak, "unit": "GB/s", "frac": a / peak if peak else None, "traffic": None,
+            "bytes_per_launch": b, "ms_per_launch": ms,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
 
 def raw_ceiling(dev, props, peak_tflops: float) -> dict:
@@ -857,6 +876,7 @@ def main():
             "gpu_launches": launches,
             "roofline": roofline,
             "roofline_forward": roofline_fwd,
+            "roofline_sort": sort_roofline(n, t_sort, peaks),
             "cpu_baseline": cpu,
             "clocks": clk,
             "breakdown_ms": {"sort": t_sort, "density": t_dens, "backward": t_bwd,
