@@ -167,6 +167,8 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_TRY(dev_alloc(g, &d.cell_box, C));
   PV_TRY(dev_alloc(g, &d.cell_Hmax, C));
   PV_TRY(dev_alloc(g, &d.big_cells, C));
+  PV_TRY(dev_alloc(g, &d.small_cells, C));
+  PV_TRY(dev_alloc(g, &d.tile_sum, (size_t)pv::scan_tiles(ncell)));
   PV_TRY(dev_alloc(g, &d.pcell, N));
   PV_TRY(dev_alloc(g, &d.prank, N));
   PV_TRY(dev_alloc(g, &d.xm, N));
@@ -202,6 +204,9 @@ pv_status build(pv_grid* g, const pv_grid_desc* desc) {
   PV_CUDA(cudaMemset(d.box_disp, 0, hb.size() * sizeof(float)));
   d.max_count = sc + 2;
   d.n_big = sc + 3;
+  d.n_small = sc + 12;
+  d.n_large = sc + 13;
+  d.n_huge = sc + 14;
   d.ntask = sc + 4;
   d.task_next = sc + 5;
   d.n_ccells = sc + 6;
@@ -286,7 +291,7 @@ pv_status pv_sort_cells(pv_grid* g, const double* pos, const float* h, const flo
   PV_CUDA(pv::launch_scatter(d, st));
   PV_CUDA(pv::launch_sort(d, pos, h, m, m_uniform, st));
   d.moved = 0;
-  g->launches += g->n > 0 ? 8 : 4;  // clear, bin, scan, scatter, cell sorts (x2), big-cell sorts (x2)
+  g->launches += g->n > 0 ? 11 : 3;  // clear, bin, scan (x2), scatter, gather, cell sorts (x2), big-cell sorts (x3)
   g->sorted = true;
   return PV_OK;
 }

@@ -8,22 +8,23 @@
 // frame in double precision and only then converted to single precision.
 //
 // Kernels (all HBM-bound except the sort, which is shared-memory bound):
-//   k_clear    zeroes the occupancies and the per-sort scalars
+//   k_clear    zeroes the occupancies, cell maxima and the per-sort scalars
 //   k_bin      particle -> cell id, occupancy histogram, box m_max, input
 //              checks (latched flags)
-//   k_scan     exclusive scan of the occupancies, list of big cells
+//   k_scan_tile, k_scan_add  exclusive scan of the occupancies (two passes
+//              over tiles of cells), the cell lists of the sort paths
 //   k_scatter  caller index of every cell-order slot
-//   k_cell_sort   one CTA per cell of more than 64 particles: gathers the
-//              cell's particles into cell order (FP32 offsets + normalised
-//              mass, h, wrapped FP64 position) with coalesced writes, the
-//              cell's H_max, and, for a cell of <= 384 particles, the 13
-//              sorts, one warp per axis: bucket (counting) sort in shared
-//              memory, exact order inside a bucket by (projection, caller
-//              index)
-//   k_cell_sort_tiny  the same for cells of <= 64 particles, one warp per
-//              cell (the 13 axes in turn)
-//   k_sort_big    one CTA per (larger cell, axis), the same algorithm with up
-//              to 8192 buckets in shared memory
+//   k_gather   one thread per slot of the cells outside k_cell_sort: the
+//              particle's FP32 offset from its cell centre + normalised mass,
+//              h, the wrapped FP64 position, and the cell's H_max
+//   k_cell_sort_tiny  cells of <= 64 particles, one warp per cell: rank
+//              counting over (axis, particle) pairs for <= 32, else the 13
+//              axes in turn with a warp bucket (counting) sort, exact order
+//              inside a bucket by (projection, caller index)
+//   k_cell_sort   cells of 65..384 particles, one CTA per cell, one warp per
+//              axis, the same warp bucket sort
+//   k_sort_big    one CTA per (larger cell, axis), the same algorithm with
+//              up to 16384 buckets in shared memory
 //   k_update, k_update_check  new positions on a kept sort (pv_update_positions)
 #include <cuda_runtime.h>
 
@@ -33,13 +34,13 @@ namespace pv {
 
 namespace {
 
-// cells of up to kSortTinyMax particles are gathered and sorted by one warp
-// (all 13 axes in turn), cells of up to kSortSmallMax particles by one CTA
-// (74 KB of shared memory, three CTAs per SM, one warp per axis); larger
-// ones are gathered by that CTA and sorted with one CTA per (cell, axis)
+// cells of up to kSortTinyMax particles are sorted by one warp, cells of up
+// to kSortSmallMax particles by one CTA (74 KB of shared memory, three CTAs
+// per SM, one warp per axis), larger ones with one CTA per (cell, axis)
 constexpr int kSortTinyMax = 64;
-constexpr int kSortTinyWarps = 8;
 constexpr int kSortSmallMax = 384;
+constexpr int kSortMidMax = 1536;    // larger cells: one CTA per (cell, axis)
+constexpr int kSortLargeMax = 6144;
 static_assert(kSortSmallMax % 32 == 0, "whole particles per lane in the cell sort");
 constexpr int kSortThreads = kNDir * 32;
 
@@ -68,7 +69,10 @@ __device__ __forceinline__ double wrap_coord(double x, double L) {
 __global__ void k_clear(GridDev g) {
   pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < g.ncell) g.cell_count[i] = 0;
+  if (i < g.ncell) {
+    g.cell_count[i] = 0;
+    g.cell_Hmax[i] = 0.0f;
+  }
   if (i < g.n_boxes) {
     g.m_max[i] = 0.0f;
     g.box_disp[i] = 0.0f;
@@ -77,6 +81,9 @@ __global__ void k_clear(GridDev g) {
     *g.flags = 0u;
     *g.max_count = 0;
     *g.n_big = 0;
+    *g.n_large = 0;
+    *g.n_small = 0;
+    *g.n_huge = 0;
   }
 }
 
@@ -120,52 +127,73 @@ __global__ void k_bin(GridDev g, const double* __restrict__ pos, const float* __
   }
 }
 
-// Single-CTA exclusive scan of the cell occupancies (C is at most a few
-// million; each thread scans a contiguous chunk).
-__global__ void __launch_bounds__(1024) k_scan(GridDev g) {
-  pdl_enter();
-  __shared__ int s_part[1024];
-  __shared__ int s_max[32];
-  const int C = g.ncell, T = blockDim.x, t = threadIdx.x;
-  const int per = (C + T - 1) / T;
-  const int c0 = min(C, t * per), c1 = min(C, c0 + per);
-  int sum = 0, mx = 0;
-  for (int c = c0; c < c1; c++) {
-    int v = g.cell_count[c];
-    sum += v;
-    mx = max(mx, v);
-  }
-  s_part[t] = sum;
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((t & 31) == 0) s_max[t >> 5] = mx;
-  __syncthreads();
-  // Hillis-Steele inclusive scan of the chunk sums
-  for (int o = 1; o < T; o <<= 1) {
-    int v = t >= o ? s_part[t - o] : 0;
-    __syncthreads();
-    s_part[t] += v;
-    __syncthreads();
-  }
-  int run = s_part[t] - sum;
-  for (int c = c0; c < c1; c++) {
-    int v = g.cell_count[c];
-    g.cell_start[c] = run;
-    run += v;
-    if (v > kSortSmallMax) g.big_cells[atomicAdd(g.n_big, 1)] = c;
-  }
-  if (t == T - 1) g.cell_start[C] = s_part[T - 1];
-  if (t == 0) {
-    int m = 0;
-    for (int w = 0; w < T / 32; w++) m = max(m, s_max[w]);
-    *g.max_count = m;
-    if (m > PV_MAX_CELL_COUNT) atomicOr(g.flags, PV_FLAG_CELL_OVERFLOW);
-  }
-}
-
 __global__ void k_scatter(GridDev g) {
   pdl_enter();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < g.n) g.orig[g.cell_start[g.pcell[p]] + g.prank[p]] = p;
+}
+
+// Gathers the particle p of cell-order slot s of a cell of box B centred at
+// -ctr (in units of the edge): the FP32 offset from the cell centre (Section
+// 3.2: shifted in FP64, then rounded) with the normalised mass, h, the copy
+// kept for pv_update_positions and the wrapped FP64 position.  Returns the
+// staged record; hm is gamma h, or 0 for an invalid h or mass.
+__device__ __forceinline__ float4 gather_slot(const GridDev& g, int s, int p, const BoxDev& B,
+                                              const double (&ctr)[3], float mmax,
+                                              const double* __restrict__ pos,
+                                              const float* __restrict__ h,
+                                              const float* __restrict__ m, float m_uniform,
+                                              float& hm) {
+  float off[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    double x = pos[3 * (size_t)p + k];
+    if (!finite_bits(x)) x = 0.0;
+    if (!in_box_bits(x, B.L)) x = wrap_coord(x, B.L);
+    off[k] = (float)fma(ctr[k], B.edge, x);
+    g.pos64[3 * (size_t)s + k] = x;
+  }
+  const float mv = m ? m[p] : m_uniform;
+  const float hv = h[p];
+  const float4 xm = make_float4(off[0], off[1], off[2], mmax > 0.0f ? mv / mmax : 0.0f);
+  g.xm[s] = xm;
+  g.xm_ref[s] = xm;
+  g.hs[s] = hv;
+  hm = valid_h_m(hv, mv) ? g.gamma * hv : 0.0f;
+  return xm;
+}
+
+__device__ __forceinline__ void cell_centre(const BoxDev& B, int c, double (&ctr)[3]) {
+  const int loc = c - B.cell_base;
+  ctr[0] = -((loc / (B.nc * B.nc)) + 0.5);
+  ctr[1] = -(((loc / B.nc) % B.nc) + 0.5);
+  ctr[2] = -((loc % B.nc) + 0.5);
+}
+
+// One thread per cell-order slot s: gathers the slot's particle and raises its
+// cell's H_max (cleared by k_clear), one atomic per run of equal cells in the
+// warp.  Every slot is independent, so the random reads of the caller's
+// arrays all overlap.
+__global__ void k_gather(GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
+                         const float* __restrict__ m, float m_uniform) {
+  pdl_enter();
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int cell = -1;
+  float hm = 0.0f;
+  if (s < g.n) {
+    const int p = g.orig[s];
+    cell = g.pcell[p];
+    const int bx = g.cell_box[cell];
+    const BoxDev& B = g.boxes[bx];
+    double ctr[3];
+    cell_centre(B, cell, ctr);
+    gather_slot(g, s, p, B, ctr, g.m_max[bx], pos, h, m, m_uniform, hm);
+  }
+  // H_max >= 0: the float order is the order of the bit patterns
+  const unsigned grp = __match_any_sync(0xffffffffu, cell);
+  const unsigned hb = __reduce_max_sync(grp, __float_as_uint(hm));
+  if (cell >= 0 && hb != 0u && (int)(threadIdx.x & 31) == __ffs(grp) - 1)
+    atomicMax(reinterpret_cast<unsigned int*>(&g.cell_Hmax[cell]), hb);
 }
 
 // New positions and smoothing lengths for the sorted grid (pv_update_positions):
@@ -269,6 +297,60 @@ __device__ __forceinline__ int group_exclusive_scan(int v, int rank, int* scratc
   return r;
 }
 
+// Appends val to list (at the front, or from the back when back) for every
+// lane with pred: one atomic per warp.  All 32 lanes take part.
+__device__ __forceinline__ void warp_push(bool pred, int32_t* list, int32_t* n, int val,
+                                          bool back, int len) {
+  const unsigned b = __ballot_sync(0xffffffffu, pred);
+  if (!b) return;
+  const int lane = threadIdx.x & 31, lead = __ffs(b) - 1;
+  int base = 0;
+  if (lane == lead) base = atomicAdd(n, __popc(b));
+  base = __shfl_sync(0xffffffffu, base, lead);
+  const int at = base + __popc(b & ((1u << lane) - 1u));
+  if (pred) list[back ? len - 1 - at : at] = val;
+}
+
+// Exclusive scan of the cell occupancies in two passes over tiles of
+// kScanTile cells.  k_scan_tile: the scan inside each tile (its total in
+// tile_sum), the largest occupancy and the cell lists of the sort paths.
+__global__ void __launch_bounds__(kScanTile) k_scan_tile(GridDev g) {
+  pdl_enter();
+  __shared__ int s_w[32];
+  const int c = blockIdx.x * kScanTile + threadIdx.x;
+  const int v = c < g.ncell ? g.cell_count[c] : 0;
+  const int ex = group_exclusive_scan<true>(v, threadIdx.x, s_w);
+  if (c < g.ncell) g.cell_start[c] = ex;
+  if (threadIdx.x == kScanTile - 1) g.tile_sum[blockIdx.x] = ex + v;
+  const int mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)v);
+  if ((threadIdx.x & 31) == 0 && mx > 0) {
+    atomicMax(g.max_count, mx);
+    if (mx > PV_MAX_CELL_COUNT) atomicOr(g.flags, PV_FLAG_CELL_OVERFLOW);
+  }
+  warp_push(v > kSortTinyMax && v <= kSortSmallMax, g.small_cells, g.n_small, c, false, g.ncell);
+  warp_push(v > kSortLargeMax, g.small_cells, g.n_huge, c, true, g.ncell);
+  warp_push(v > kSortSmallMax && v <= kSortMidMax, g.big_cells, g.n_big, c, false, g.ncell);
+  warp_push(v > kSortMidMax && v <= kSortLargeMax, g.big_cells, g.n_large, c, true, g.ncell);
+}
+
+// k_scan_add: each tile adds the totals of the tiles before it; the last one
+// also writes cell_start[C], the particle count.
+__global__ void __launch_bounds__(kScanTile) k_scan_add(GridDev g) {
+  pdl_enter();
+  __shared__ int s_w[32];
+  int p = 0;
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += kScanTile) p += g.tile_sum[t];
+  p = (int)__reduce_add_sync(0xffffffffu, (unsigned)p);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = p;
+  __syncthreads();
+  p = 0;
+  for (int w = 0; w < kScanTile / 32; w++) p += s_w[w];
+  const int c = blockIdx.x * kScanTile + threadIdx.x;
+  if (c < g.ncell) g.cell_start[c] += p;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+    g.cell_start[g.ncell] = p + g.tile_sum[blockIdx.x];
+}
+
 // Bucket b of a scan in which each of nthr threads owns per = nb / nthr
 // consecutive buckets sits at b + b / per (sh = log2 per): one pad word per
 // chunk puts the chunks' i-th buckets in distinct shared-memory banks.
@@ -355,191 +437,90 @@ constexpr size_t sort_small_smem() {
                           (sort_small_buckets<kMax>() + 32) * sizeof(int));
 }
 
-// One CTA per cell.  All threads gather the cell's particles (caller indices
-// in orig) into cell order with coalesced writes: FP32 offsets from the cell
-// centre (Section 3.2: shifted in FP64, then rounded) with the normalised
-// mass, h, the copy kept for pv_update_positions and the wrapped FP64
-// position; the cell's H_max is reduced on the way.  A cell of at most kMax
-// particles is then sorted along the 13 axes from the staged copy, one warp
-// per axis; larger cells are left to k_sort_big.
-template <int kMax>
-__global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g,
-                                                            const double* __restrict__ pos,
-                                                            const float* __restrict__ h,
-                                                            const float* __restrict__ m,
-                                                            float m_uniform) {
-  pdl_enter();
-  constexpr int kB = sort_small_buckets<kMax>();
-  extern __shared__ float4 smem4[];
-  __shared__ unsigned int s_hmax;
-  float4* s_x = smem4;                                           // [kMax]
-  int* s_orig = reinterpret_cast<int*>(s_x + kMax);              // [kMax]
-  float* s_key = reinterpret_cast<float*>(s_orig + kMax);        // [13][kMax]
-  int* s_bkt = reinterpret_cast<int*>(s_key + kNDir * kMax);     // [13][kB + 32]
-  uint16_t* s_out = reinterpret_cast<uint16_t*>(s_bkt + kNDir * (kB + 32));  // [13][kMax]
-  uint16_t* s_tmp = s_out + kNDir * kMax;                        // [13][kMax]
-  const int c = blockIdx.x;
-  const int cnt = g.cell_count[c];
-  if (cnt <= kSortTinyMax) return;  // k_cell_sort_tiny's
-  const int cs = g.cell_start[c];
-  const int bx = g.cell_box[c];
-  const BoxDev B = g.boxes[bx];
-  const int loc = c - B.cell_base;
-  const double ctr[3] = {-((loc / (B.nc * B.nc)) + 0.5), -(((loc / B.nc) % B.nc) + 0.5),
-                         -((loc % B.nc) + 0.5)};
-  const float mmax = g.m_max[bx];
-  if (threadIdx.x == 0) s_hmax = 0u;
-  __syncthreads();
-  float hmax = 0.0f;
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    const int p = g.orig[cs + t];
-    const size_t s = (size_t)cs + t;
-    float off[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      double x = pos[3 * (size_t)p + k];
-      if (!finite_bits(x)) x = 0.0;
-      if (!in_box_bits(x, B.L)) x = wrap_coord(x, B.L);
-      off[k] = (float)fma(ctr[k], B.edge, x);
-      g.pos64[3 * s + k] = x;
-    }
-    const float mv = m ? m[p] : m_uniform;
-    const float hv = h[p];
-    const float4 xm = make_float4(off[0], off[1], off[2], mmax > 0.0f ? mv / mmax : 0.0f);
-    g.xm[s] = xm;
-    g.xm_ref[s] = xm;
-    g.hs[s] = hv;
-    if (valid_h_m(hv, mv)) hmax = fmaxf(hmax, g.gamma * hv);
-    if (cnt <= kMax) {
-      s_x[t] = xm;
-      s_orig[t] = p;
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-  if ((threadIdx.x & 31) == 0 && hmax > 0.0f) atomicMax(&s_hmax, __float_as_uint(hmax));
-  __syncthreads();
-  if (threadIdx.x == 0) g.cell_Hmax[c] = __uint_as_float(s_hmax);
-  if (cnt > kMax) return;
-  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float ux, uy, uz;
-  axis_u(k, ux, uy, uz);
-  float* key = s_key + k * kMax;
-  uint16_t* out = s_out + k * kMax;
-  uint16_t* tmp = s_tmp + k * kMax;
-  int* bkt = s_bkt + k * (kB + 32);
-  constexpr int kPer = kMax / 32;
-  float kr[kPer];
-  float kmin = 3.0e38f, kmax = -3.0e38f;
-#pragma unroll
-  for (int j = 0; j < kPer; j++) {
-    const int t = lane + 32 * j;
-    kr[j] = 0.0f;
-    if (t < cnt) {
-      const float d = project(s_x[t], ux, uy, uz);
-      key[t] = d;
-      kr[j] = d;
-      kmin = fminf(kmin, d);
-      kmax = fmaxf(kmax, d);
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-    kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-  }
-  int nb = 32;
-  while (nb < cnt) nb <<= 1;
-  warp_sort_axis<kPer>(cnt, kr, key, s_orig, tmp, out, bkt, nb, lane, kmin, kmax);
-  const size_t base = (size_t)k * g.n + cs;
-#pragma unroll
-  for (int j = 0; j < kPer; j++) {
-    const int t = lane + 32 * j;
-    if (t < cnt) {
-      const int v = out[t];
-      g.perm[base + t] = (uint16_t)v;
-      g.dist[base + t] = key[v];
-    }
-  }
+// (projection, caller index) as one unsigned integer of the same order: the
+// FP32 order of d (-0 and +0 equal) in the high word, the index o >= 0 below
+__device__ __forceinline__ unsigned long long sort_key64(float d, int o) {
+  const unsigned b = __float_as_uint(d == 0.0f ? 0.0f : d);
+  const unsigned u = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+  return ((unsigned long long)u << 32) | (unsigned)o;
 }
 
-// One warp per cell of at most kSortTinyMax particles (a clustered box has
-// tens of thousands of them, which k_cell_sort's one CTA per cell handles
-// poorly): the same gather into cell order and H_max, then the 13 axes in
-// turn with the same warp bucket sort, from a per-warp copy of the keys.
-__global__ void __launch_bounds__(kSortTinyWarps * 32) k_cell_sort_tiny(
-    GridDev g, const double* __restrict__ pos, const float* __restrict__ h,
-    const float* __restrict__ m, float m_uniform) {
-  pdl_enter();
+// Cells of at most kSortTinyMax particles, one warp per cell (a clustered box
+// has tens of thousands of them, which a CTA per cell handles poorly): the
+// cell's staged offsets and caller indices are loaded into the warp's shared
+// memory, then
+// * cells of at most 32: the lanes take the 13 cnt (axis, particle) pairs in
+//   turn; the rank of a key is the count of keys before it in (projection,
+//   caller index) order, read from a row of 33 words per axis (broadcasts,
+//   and lanes on different axes in different banks);
+// * larger cells: the 13 axes in turn with the warp bucket sort.
+constexpr int kTinyRow = 33;
+struct TinyBuf {  // one warp's shared memory
+  float4 x[kSortTinyMax];
+  int orig[kSortTinyMax];
+  // the 64-bit keys of the <= 32 path, or the bucket sort's arrays
+  unsigned long long u[kNDir * kTinyRow];
+};
+static_assert(kSortTinyMax * (sizeof(float) + 2 * sizeof(uint16_t)) +
+                      (kSortTinyMax + 32) * sizeof(int) <=
+                  sizeof(TinyBuf::u),
+              "the bucket sort's arrays fit the key rows");
+
+// The warp with index w0 of nw takes cells w0, w0 + nw, ...
+__device__ __forceinline__ void sort_tiny_cells(const GridDev& g, TinyBuf& tb, int lane, int w0,
+                                                int nw) {
   constexpr int kPer = kSortTinyMax / 32;
-  __shared__ float4 s_x[kSortTinyWarps][kSortTinyMax];
-  __shared__ float s_key[kSortTinyWarps][kSortTinyMax];
-  __shared__ int s_orig[kSortTinyWarps][kSortTinyMax];
-  __shared__ uint16_t s_tmp[kSortTinyWarps][kSortTinyMax];
-  __shared__ uint16_t s_out[kSortTinyWarps][kSortTinyMax];
-  __shared__ int s_bkt[kSortTinyWarps][kSortTinyMax + 32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float4* wx = s_x[warp];
-  float* key = s_key[warp];
-  int* orig = s_orig[warp];
-  for (int c = blockIdx.x * kSortTinyWarps + warp; c < g.ncell;
-       c += gridDim.x * kSortTinyWarps) {
+  float4* wx = tb.x;
+  int* orig = tb.orig;
+  unsigned long long* kk = tb.u;
+  float* key = reinterpret_cast<float*>(kk);
+  uint16_t* tmp = reinterpret_cast<uint16_t*>(key + kSortTinyMax);
+  uint16_t* out = tmp + kSortTinyMax;
+  int* bkt = reinterpret_cast<int*>(out + kSortTinyMax);
+  for (int c = w0; c < g.ncell; c += nw) {
     const int cnt = g.cell_count[c];
-    if (cnt > kSortTinyMax) continue;
+    if (cnt > kSortTinyMax || cnt == 0) continue;
     const int cs = g.cell_start[c];
-    const int bx = g.cell_box[c];
-    const BoxDev& B = g.boxes[bx];
-    const int loc = c - B.cell_base;
-    const double ctr[3] = {-((loc / (B.nc * B.nc)) + 0.5), -(((loc / B.nc) % B.nc) + 0.5),
-                           -((loc % B.nc) + 0.5)};
-    const float mmax = g.m_max[bx];
-    float hmax = 0.0f;
     for (int t = lane; t < cnt; t += 32) {
-      const int p = g.orig[cs + t];
-      const size_t s = (size_t)cs + t;
-      float off[3];
-#pragma unroll
-      for (int k = 0; k < 3; k++) {
-        double x = pos[3 * (size_t)p + k];
-        if (!finite_bits(x)) x = 0.0;
-        if (!in_box_bits(x, B.L)) x = wrap_coord(x, B.L);
-        off[k] = (float)fma(ctr[k], B.edge, x);
-        g.pos64[3 * s + k] = x;
-      }
-      const float mv = m ? m[p] : m_uniform;
-      const float hv = h[p];
-      const float4 xm = make_float4(off[0], off[1], off[2], mmax > 0.0f ? mv / mmax : 0.0f);
-      g.xm[s] = xm;
-      g.xm_ref[s] = xm;
-      g.hs[s] = hv;
-      if (valid_h_m(hv, mv)) hmax = fmaxf(hmax, g.gamma * hv);
-      wx[t] = xm;
-      orig[t] = p;
+      wx[t] = g.xm[cs + t];
+      orig[t] = g.orig[cs + t];
     }
-    for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-    if (lane == 0) g.cell_Hmax[c] = hmax;
-    if (cnt == 0) continue;
     __syncwarp();
     if (cnt <= 32) {
-      // one key per lane: its rank is the number of keys before it in
-      // (projection, caller index) order, counted over shuffles (the order
-      // of the bucket sort below, without its buckets)
-      const float4 xl = lane < cnt ? wx[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      const int ol = lane < cnt ? orig[lane] : 0;
-      for (int k = 0; k < kNDir; k++) {
-        float ux, uy, uz;
-        axis_u(k, ux, uy, uz);
-        const float kl = project(xl, ux, uy, uz);
-        int r = 0;
-        for (int u = 0; u < cnt; u++) {
-          const float ku = __shfl_sync(0xffffffffu, kl, u);
-          const int ou = __shfl_sync(0xffffffffu, ol, u);
-          r += key_less(ku, ou, kl, ol) ? 1 : 0;
-        }
-        if (lane < cnt) {
-          const size_t base = (size_t)k * g.n + cs;
-          g.perm[base + r] = (uint16_t)lane;
-          g.dist[base + r] = kl;
+      const int npair = kNDir * cnt;
+      // pair q = (axis k, particle t) with k = q / cnt: (q + 1/2) / cnt in
+      // FP32 is at least 1 / (2 cnt) from an integer, far above its rounding
+      const float inv = 1.0f / (float)cnt;
+      float kf[kNDir];
+#pragma unroll
+      for (int j = 0; j < kNDir; j++) {
+        const int q = lane + 32 * j;
+        kf[j] = 0.0f;
+        if (q < npair) {
+          const int k = (int)(((float)q + 0.5f) * inv), t = q - k * cnt;
+          float ux, uy, uz;
+          axis_u(k, ux, uy, uz);
+          kf[j] = project(wx[t], ux, uy, uz);
+          kk[k * kTinyRow + t] = sort_key64(kf[j], orig[t]);
         }
       }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < kNDir; j++) {
+        const int q = lane + 32 * j;
+        if (q < npair) {
+          const int k = (int)(((float)q + 0.5f) * inv), t = q - k * cnt;
+          const unsigned long long* row = kk + k * kTinyRow;
+          const unsigned long long me = row[t];
+          int r = 0;
+#pragma unroll 4
+          for (int u = 0; u < cnt; u++) r += row[u] < me ? 1 : 0;
+          const size_t base = (size_t)k * g.n + cs;
+          g.perm[base + r] = (uint16_t)t;
+          g.dist[base + r] = kf[j];
+        }
+      }
+      __syncwarp();  // the rows are rewritten by the next cell
       continue;
     }
     int nb = 32;
@@ -561,19 +542,16 @@ __global__ void __launch_bounds__(kSortTinyWarps * 32) k_cell_sort_tiny(
           kmax = fmaxf(kmax, d);
         }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-        kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-      }
+      kmin = warp_min_f(kmin);
+      kmax = warp_max_f(kmax);
       __syncwarp();
-      warp_sort_axis<kPer>(cnt, kr, key, orig, s_tmp[warp], s_out[warp], s_bkt[warp], nb, lane,
-                           kmin, kmax);
+      warp_sort_axis<kPer>(cnt, kr, key, orig, tmp, out, bkt, nb, lane, kmin, kmax);
       const size_t base = (size_t)k * g.n + cs;
 #pragma unroll
       for (int j = 0; j < kPer; j++) {
         const int t = lane + 32 * j;
         if (t < cnt) {
-          const int v = s_out[warp][t];
+          const int v = out[t];
           g.perm[base + t] = (uint16_t)v;
           g.dist[base + t] = key[v];
         }
@@ -583,41 +561,144 @@ __global__ void __launch_bounds__(kSortTinyWarps * 32) k_cell_sort_tiny(
   }
 }
 
-// One CTA per (cell of more than kSortSmallMax particles, axis), the same
-// bucket sort with the buckets in shared memory.  For a cell of at most
-// kSortBigSmem particles the keys, caller indices and bucket-grouped indices
-// are staged in shared memory too (keys computed once); larger cells need no
-// scratch beyond the axis's own outputs: the bucket-grouped indices go into
-// dist[k] (as int bits) until the exact ranks have been written to perm[k],
-// then dist[k] receives the keys, which are recomputed from xm wherever they
-// are needed (the same FP32 expression each time, so the same values).
-constexpr int kSortBigThreads = 1024;
-constexpr int kSortBigBuckets = 8192;
-constexpr int kSortBigSmem = 6144;
-constexpr size_t kSortBigDynSmem =
-    (size_t)kSortBigSmem * (sizeof(float) + sizeof(int) + sizeof(uint16_t));
+// One warp's axis k of a staged cell of cnt <= 32 kPer particles (the keys,
+// bucket sort and the axis's outputs).
+template <int kPer>
+__device__ __forceinline__ void cell_sort_axis(const GridDev& g, int k, int lane, int cnt, int cs,
+                                               const float4* s_x, const int* s_orig, float* key,
+                                               uint16_t* tmp, uint16_t* out, int* bkt) {
+  float ux, uy, uz;
+  axis_u(k, ux, uy, uz);
+  float kr[kPer];
+  float kmin = 3.0e38f, kmax = -3.0e38f;
+#pragma unroll
+  for (int j = 0; j < kPer; j++) {
+    const int t = lane + 32 * j;
+    kr[j] = 0.0f;
+    if (t < cnt) {
+      const float d = project(s_x[t], ux, uy, uz);
+      key[t] = d;
+      kr[j] = d;
+      kmin = fminf(kmin, d);
+      kmax = fmaxf(kmax, d);
+    }
+  }
+  kmin = warp_min_f(kmin);
+  kmax = warp_max_f(kmax);
+  int nb = 32;
+  while (nb < cnt) nb <<= 1;
+  warp_sort_axis<kPer>(cnt, kr, key, s_orig, tmp, out, bkt, nb, lane, kmin, kmax);
+  const size_t base = (size_t)k * g.n + cs;
+#pragma unroll
+  for (int j = 0; j < kPer; j++) {
+    const int t = lane + 32 * j;
+    if (t < cnt) {
+      const int v = out[t];
+      g.perm[base + t] = (uint16_t)v;
+      g.dist[base + t] = key[v];
+    }
+  }
+}
 
-template <bool kStaged>
-__global__ void __launch_bounds__(kSortBigThreads, kStaged ? 2 : 1) k_sort_big(GridDev g) {
+// One CTA per cell of kSortTinyMax < count <= kMax (entry blockIdx.x of the
+// small_cells list; the grid covers every cell, the CTAs past the list's end
+// exit at once): the cell's staged offsets and caller indices are loaded
+// (coalesced) into shared memory, then the 13 axes are sorted one warp each.
+template <int kMax>
+__global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g) {
   pdl_enter();
-  __shared__ int s_bkt[kSortBigBuckets + kSortBigThreads];  // bucket b at bucket_slot(b, sh)
-  __shared__ float s_red[2][32];
+  constexpr int kB = sort_small_buckets<kMax>();
+  extern __shared__ float4 smem4[];
+  float4* s_x = smem4;                                           // [kMax]
+  int* s_orig = reinterpret_cast<int*>(s_x + kMax);              // [kMax]
+  float* s_key = reinterpret_cast<float*>(s_orig + kMax);        // [13][kMax]
+  int* s_bkt = reinterpret_cast<int*>(s_key + kNDir * kMax);     // [13][kB + 32]
+  uint16_t* s_out = reinterpret_cast<uint16_t*>(s_bkt + kNDir * (kB + 32));  // [13][kMax]
+  uint16_t* s_tmp = s_out + kNDir * kMax;                        // [13][kMax]
+  const int i = blockIdx.x;  // one CTA per listed cell (the grid covers every cell)
+  if (i >= *g.n_small) return;
+  const int c = g.small_cells[i];
+  const int cnt = min(g.cell_count[c], kMax);
+  const int cs = g.cell_start[c];
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    s_x[t] = g.xm[cs + t];
+    s_orig[t] = g.orig[cs + t];
+  }
+  __syncthreads();
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cell_sort_axis<kMax / 32>(g, k, lane, cnt, cs, s_x, s_orig, s_key + k * kMax, s_tmp + k * kMax,
+                            s_out + k * kMax, s_bkt + k * (kB + 32));
+}
+
+// One warp per cell of at most kSortTinyMax particles, over all cells.
+constexpr int kSortTinyWarps = 8;
+__global__ void __launch_bounds__(kSortTinyWarps * 32, 5) k_cell_sort_tiny(GridDev g) {
+  pdl_enter();
+  __shared__ TinyBuf s_tb[kSortTinyWarps];
+  const int warp = threadIdx.x >> 5;
+  sort_tiny_cells(g, s_tb[warp], threadIdx.x & 31, blockIdx.x * kSortTinyWarps + warp,
+                  gridDim.x * kSortTinyWarps);
+}
+
+// One CTA per (cell of more than kSortSmallMax particles, axis), persistent:
+// the same bucket sort with the buckets in shared memory and the keys
+// computed once into shared memory.  Three instances over three cell lists:
+//   mid   (<= kSortMidMax particles)   kSortMidThreads threads, six CTAs per SM
+//   large (<= kSortLargeMax)           kSortLargeThreads threads, two per SM
+//   huge  (the rest)                   kSortHugeThreads threads, one per SM
+// The mid and large instances stage the caller indices and the ranks too,
+// so that no phase waits on global memory.  The huge one stages only the
+// keys and the bucket-grouped indices, and a cell above kStage needs no
+// scratch beyond the axis's own outputs: the grouped indices go into dist[k]
+// (as int bits) until the exact ranks have been written to perm[k], then
+// dist[k] receives the keys, recomputed from xm wherever they are needed (the
+// same FP32 expression each time, so the same values).  Caller indices are
+// read only to order equal keys.
+constexpr int kSortMidThreads = 256;
+constexpr int kSortMidBuckets = 2048;  // >= kSortMidMax
+constexpr int kSortLargeThreads = 512;
+constexpr int kSortLargeBuckets = 8192;  // >= kSortLargeMax
+constexpr int kSortHugeThreads = 1024;
+constexpr int kSortHugeBuckets = 16384;
+constexpr int kSortHugeStage = 24576;
+enum SortList { kListMid = 0, kListLarge = 1, kListHuge = 2 };
+
+template <int kThreads, int kMaxB, int kStage, int kList>
+constexpr size_t sort_big_smem() {
+  return (size_t)(kMaxB + kThreads) * sizeof(int) +
+         (size_t)kStage * (kList == kListHuge ? sizeof(float) + sizeof(uint16_t)
+                                              : sizeof(float) + sizeof(int) + 2 * sizeof(uint16_t));
+}
+
+template <int kThreads, int kMaxB, int kStage, int kList>
+__global__ void __launch_bounds__(kThreads, kList == kListMid ? 6 : (kList == kListLarge ? 2 : 1))
+    k_sort_big(GridDev g) {
+  pdl_enter();
+  static_assert(kMaxB % kThreads == 0, "whole buckets per thread in the scan");
+  constexpr bool kFull = kList != kListHuge;  // every cell fits; indices and ranks staged
+  constexpr int kWarps = kThreads / 32;
+  extern __shared__ int s_dyn[];
+  int* s_bkt = s_dyn;                                                 // [kMaxB + kThreads]
+  float* s_key = reinterpret_cast<float*>(s_bkt + kMaxB + kThreads);  // [kStage]
+  int* s_org = reinterpret_cast<int*>(s_key + kStage);                // [kStage] (kFull)
+  uint16_t* s_grp = reinterpret_cast<uint16_t*>(kFull ? s_org + kStage : s_org);  // [kStage]
+  uint16_t* s_out = s_grp + kStage;                                   // [kStage] (kFull)
+  __shared__ float s_red[2][kWarps];
   __shared__ int s_scan[32];
-  extern __shared__ float s_key[];                                  // [kSortBigSmem]
-  int* s_org = reinterpret_cast<int*>(s_key + kSortBigSmem);        // [kSortBigSmem]
-  uint16_t* s_grp = reinterpret_cast<uint16_t*>(s_org + kSortBigSmem);  // [kSortBigSmem]
   if (*g.flags) return;
-  const int nbig = *g.n_big;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int idx = blockIdx.x; idx < nbig * kNDir; idx += gridDim.x) {
-    const int c = g.big_cells[idx / kNDir], k = idx % kNDir;
-    const int cnt = min(g.cell_count[c], PV_MAX_CELL_COUNT);
-    // cells of at most kSortBigSmem particles go to the staged instance
-    if ((cnt <= kSortBigSmem) != kStaged) continue;
+  const int nlist = kList == kListMid ? *g.n_big : (kList == kListLarge ? *g.n_large : *g.n_huge);
+  const int nitem = nlist * kNDir;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int idx = blockIdx.x; idx < nitem; idx += gridDim.x) {
+    const int e = idx / kNDir, k = idx - e * kNDir;
+    const int c = kList == kListMid     ? g.big_cells[e]
+                  : kList == kListLarge ? g.big_cells[g.ncell - 1 - e]
+                                        : g.small_cells[g.ncell - 1 - e];
+    const int cnt = min(g.cell_count[c], kFull ? kStage : PV_MAX_CELL_COUNT);
+    const bool staged = kFull || cnt <= kStage;
     const int cs = g.cell_start[c];
-    constexpr bool staged = kStaged;
-    int B = kSortBigThreads;
-    while (B < cnt && B < kSortBigBuckets) B <<= 1;
+    int B = kThreads;
+    while (B < cnt && B < kMaxB) B <<= 1;
     float ux, uy, uz;
     axis_u(k, ux, uy, uz);
     const float4* X = g.xm + cs;
@@ -626,40 +707,32 @@ __global__ void __launch_bounds__(kSortBigThreads, kStaged ? 2 : 1) k_sort_big(G
     int* tmp = reinterpret_cast<int*>(g.dist + base);
     uint16_t* out = g.perm + base;
     auto key_of = [&](int t) { return staged ? s_key[t] : project(X[t], ux, uy, uz); };
-    auto org_of = [&](int t) { return staged ? s_org[t] : O[t]; };
+    auto org_of = [&](int t) { return kFull ? s_org[t] : O[t]; };
     float kmin = 3.0e38f, kmax = -3.0e38f;
-    for (int t = tid; t < cnt; t += nthr) {
+    for (int t = tid; t < cnt; t += kThreads) {
       const float d = project(X[t], ux, uy, uz);
-      if (staged) {
-        s_key[t] = d;
-        s_org[t] = O[t];
-      }
+      if (staged) s_key[t] = d;
+      if (kFull) s_org[t] = O[t];
       kmin = fminf(kmin, d);
       kmax = fmaxf(kmax, d);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      kmin = fminf(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-      kmax = fmaxf(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    kmin = warp_min_f(kmin);
+    kmax = warp_max_f(kmax);
+    if (lane == 0) {
+      s_red[0][warp] = kmin;
+      s_red[1][warp] = kmax;
     }
-    if ((tid & 31) == 0) {
-      s_red[0][tid >> 5] = kmin;
-      s_red[1][tid >> 5] = kmax;
-    }
-    const int per = B / nthr, sh = __ffs(per) - 1;
-    for (int b = tid; b < B + nthr; b += nthr) s_bkt[b] = 0;
+    const int per = B / kThreads, sh = __ffs(per) - 1;
+    for (int b = tid; b < B + kThreads; b += kThreads) s_bkt[b] = 0;
     __syncthreads();
-    kmin = s_red[0][0];
-    kmax = s_red[1][0];
-    for (int w = 1; w < (nthr >> 5); w++) {
-      kmin = fminf(kmin, s_red[0][w]);
-      kmax = fmaxf(kmax, s_red[1][w]);
-    }
+    kmin = warp_min_f(lane < kWarps ? s_red[0][lane] : 3.0e38f);
+    kmax = warp_max_f(lane < kWarps ? s_red[1][lane] : -3.0e38f);
     const float scale = kmax > kmin ? (float)B / (kmax - kmin) : 0.0f;
     auto bucket_of = [&](float d) { return min(B - 1, max(0, (int)((d - kmin) * scale))); };
-    for (int t = tid; t < cnt; t += nthr)
+    for (int t = tid; t < cnt; t += kThreads)
       atomicAdd(&s_bkt[bucket_slot(bucket_of(key_of(t)), sh)], 1);
     __syncthreads();
-    // exclusive scan: each thread owns B / nthr consecutive buckets
+    // exclusive scan: each thread owns B / kThreads consecutive buckets
     const int p0 = bucket_slot(tid * per, sh);
     int sum = 0;
     for (int b = p0; b < p0 + per; b++) sum += s_bkt[b];
@@ -670,26 +743,35 @@ __global__ void __launch_bounds__(kSortBigThreads, kStaged ? 2 : 1) k_sort_big(G
       run += v;
     }
     __syncthreads();
-    for (int t = tid; t < cnt; t += nthr) {
+    for (int t = tid; t < cnt; t += kThreads) {
       const int at = atomicAdd(&s_bkt[bucket_slot(bucket_of(key_of(t)), sh)], 1);
       if (staged) s_grp[at] = (uint16_t)t; else tmp[at] = t;
     }
     __syncthreads();
-    // s_bkt[b] is now the end of bucket b; rank each particle inside its bucket
-    for (int t = tid; t < cnt; t += nthr) {
+    // s_bkt[b] is now the end of bucket b; rank each particle inside its
+    // bucket (caller indices only between equal keys)
+    for (int t = tid; t < cnt; t += kThreads) {
       const float kt = key_of(t);
       const int b = bucket_of(kt);
       const int s0 = b ? s_bkt[bucket_slot(b - 1, sh)] : 0, s1 = s_bkt[bucket_slot(b, sh)];
-      const int ot = org_of(t);
       int r = 0;
-      for (int u = s0; u < s1; u++) {
-        const int v = staged ? (int)s_grp[u] : tmp[u];
-        r += key_less(key_of(v), org_of(v), kt, ot) ? 1 : 0;
+      if (s1 - s0 > 1) {
+        const int ot = org_of(t);
+        for (int u = s0; u < s1; u++) {
+          const int v = staged ? (int)s_grp[u] : tmp[u];
+          const float kv = key_of(v);
+          if (kv < kt) r++;
+          else if (kv == kt && org_of(v) < ot) r++;
+        }
       }
-      out[s0 + r] = (uint16_t)t;
+      if (kFull) s_out[s0 + r] = (uint16_t)t; else out[s0 + r] = (uint16_t)t;
     }
     __syncthreads();
-    for (int t = tid; t < cnt; t += nthr) g.dist[base + t] = key_of(out[t]);
+    for (int t = tid; t < cnt; t += kThreads) {
+      const int v = kFull ? (int)s_out[t] : (int)out[t];
+      if (kFull) out[t] = (uint16_t)v;
+      g.dist[base + t] = key_of(v);
+    }
     __syncthreads();
   }
 }
@@ -704,7 +786,9 @@ cudaError_t launch_bin(const GridDev& g, const double* pos, const float* h, cons
 }
 
 cudaError_t launch_scan(const GridDev& g, cudaStream_t st) {
-  PV_LAUNCH(k_scan, 1, 1024, 0, st, g);
+  const int tiles = scan_tiles(g.ncell);
+  PV_LAUNCH(k_scan_tile, tiles, kScanTile, 0, st, g);
+  PV_LAUNCH(k_scan_add, tiles, kScanTile, 0, st, g);
   return cudaSuccess;
 }
 
@@ -729,26 +813,41 @@ cudaError_t launch_clear(const GridDev& g, cudaStream_t st) {
 
 cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, const float* m,
                         float m_uniform, cudaStream_t st) {
-  constexpr int smem = (int)sort_small_smem<kSortSmallMax>();
-  cudaError_t e =
-      set_max_dynamic_smem(reinterpret_cast<const void*>(&k_cell_sort<kSortSmallMax>), smem, st);
-  if (e != cudaSuccess) return e;
-  PV_LAUNCH(k_cell_sort<kSortSmallMax>, g.ncell, kSortThreads, smem, st, g, pos, h, m,
-            m_uniform);
-  PV_LAUNCH(k_cell_sort_tiny, (g.ncell + kSortTinyWarps - 1) / kSortTinyWarps,
-            kSortTinyWarps * 32, 0, st, g, pos, h, m, m_uniform);
   if (g.n == 0) return cudaSuccess;
-  if ((e = set_max_dynamic_smem(reinterpret_cast<const void*>(&k_sort_big<true>),
-                                (int)kSortBigDynSmem, st)) != cudaSuccess)
-    return e;
-  // persistent grids over (big cell, axis): two CTAs per SM for the staged
-  // instance, one for the rare cells above kSortBigSmem
   int dev = 0, sms = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  PV_LAUNCH_PLAIN(k_sort_big<true>, 2 * sms, kSortBigThreads, kSortBigDynSmem, st, g);
-  PV_LAUNCH_PLAIN(k_sort_big<false>, sms, kSortBigThreads, 0, st, g);
+  PV_LAUNCH(k_gather, (g.n + 255) / 256, 256, 0, st, g, pos, h, m, m_uniform);
+  PV_LAUNCH(k_cell_sort_tiny, (g.ncell + kSortTinyWarps - 1) / kSortTinyWarps,
+            kSortTinyWarps * 32, 0, st, g);
+  constexpr int smem = (int)sort_small_smem<kSortSmallMax>();
+  if ((e = set_max_dynamic_smem(reinterpret_cast<const void*>(&k_cell_sort<kSortSmallMax>), smem,
+                                st)) != cudaSuccess)
+    return e;
+  PV_LAUNCH(k_cell_sort<kSortSmallMax>, g.ncell, kSortThreads, smem, st, g);
+  // persistent grids over the (cell, axis) items of the larger cells: six
+  // CTAs per SM (mid), two (large) and one (huge)
+  constexpr size_t mid_smem =
+      sort_big_smem<kSortMidThreads, kSortMidBuckets, kSortMidMax, kListMid>();
+  constexpr size_t large_smem =
+      sort_big_smem<kSortLargeThreads, kSortLargeBuckets, kSortLargeMax, kListLarge>();
+  constexpr size_t huge_smem =
+      sort_big_smem<kSortHugeThreads, kSortHugeBuckets, kSortHugeStage, kListHuge>();
+  auto* mid = &k_sort_big<kSortMidThreads, kSortMidBuckets, kSortMidMax, kListMid>;
+  auto* large = &k_sort_big<kSortLargeThreads, kSortLargeBuckets, kSortLargeMax, kListLarge>;
+  auto* huge = &k_sort_big<kSortHugeThreads, kSortHugeBuckets, kSortHugeStage, kListHuge>;
+  if ((e = set_max_dynamic_smem(reinterpret_cast<const void*>(mid), (int)mid_smem, st)) !=
+          cudaSuccess ||
+      (e = set_max_dynamic_smem(reinterpret_cast<const void*>(large), (int)large_smem, st)) !=
+          cudaSuccess ||
+      (e = set_max_dynamic_smem(reinterpret_cast<const void*>(huge), (int)huge_smem, st)) !=
+          cudaSuccess)
+    return e;
+  PV_LAUNCH_PLAIN(huge, sms, kSortHugeThreads, huge_smem, st, g);
+  PV_LAUNCH_PLAIN(large, 2 * sms, kSortLargeThreads, large_smem, st, g);
+  PV_LAUNCH_PLAIN(mid, 6 * sms, kSortMidThreads, mid_smem, st, g);
   return cudaSuccess;
 }
 

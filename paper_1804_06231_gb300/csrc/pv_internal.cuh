@@ -69,8 +69,15 @@ struct GridDev {
   int32_t* cell_start;  // [C+1]
   int32_t* cell_box;    // [C]
   float* cell_Hmax;     // [C]
-  int32_t* big_cells;   // [C] list of cells sorted by the big-cell path
-  int32_t* n_big;       // [1]
+  // cell lists of the sort paths (two lists per array, one from each end)
+  int32_t* small_cells;  // [C] front: cells sorted by one CTA each; back: the largest
+  int32_t* n_small;      // [1] entries at the front
+  int32_t* n_huge;       // [1] entries at the back
+  int32_t* big_cells;    // [C] cells sorted one axis per CTA: mid-sized ones from the
+                         // front, large ones from the back
+  int32_t* n_big;        // [1] entries at the front
+  int32_t* n_large;      // [1] entries at the back
+  int32_t* tile_sum;     // [scan_tiles(C)] occupancy totals of the scan's tiles
   // per particle, caller order
   int32_t* pcell;
   int32_t* prank;
@@ -463,6 +470,9 @@ __device__ __forceinline__ int tiny_candidate(const GridDev& g, const TinySlots&
 cudaError_t launch_clear(const GridDev& g, cudaStream_t st);
 cudaError_t launch_bin(const GridDev& g, const double* pos, const float* h, const float* m,
                        float m_uniform, cudaStream_t st);
+// tiles of the occupancy scan
+constexpr int kScanTile = 1024;  // cells per CTA
+constexpr int scan_tiles(int64_t ncell) { return (int)((ncell + kScanTile - 1) / kScanTile); }
 cudaError_t launch_scan(const GridDev& g, cudaStream_t st);
 cudaError_t launch_scatter(const GridDev& g, cudaStream_t st);
 cudaError_t launch_sort(const GridDev& g, const double* pos, const float* h, const float* m,

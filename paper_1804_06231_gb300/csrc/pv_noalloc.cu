@@ -31,7 +31,8 @@ constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign;
 constexpr size_t scratch_bytes(int64_t n, int64_t c) {
   const size_t N = (size_t)n, C = (size_t)c;
   return align_up(sizeof(pv::BoxDev)) + align_up(sizeof(int64_t)) +
-         3 * align_up(C * sizeof(int32_t)) + align_up((C + 1) * sizeof(int32_t)) +
+         4 * align_up(C * sizeof(int32_t)) + align_up((C + 1) * sizeof(int32_t)) +
+         align_up((size_t)pv::scan_tiles(c) * sizeof(int32_t)) +
          align_up(C * sizeof(float)) +
          align_up(pv::kNSlot * C * sizeof(int4)) + 3 * align_up(C * sizeof(int32_t)) +  // plan
          2 * align_up(N * sizeof(int32_t)) +          // pcell, prank
@@ -114,6 +115,8 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.cell_count = carve<int32_t>(cur, C);
   d.cell_box = carve<int32_t>(cur, C);
   d.big_cells = carve<int32_t>(cur, C);
+  d.small_cells = carve<int32_t>(cur, C);
+  d.tile_sum = carve<int32_t>(cur, (size_t)pv::scan_tiles(ncell));
   d.cell_start = carve<int32_t>(cur, C + 1);
   d.cell_Hmax = carve<float>(cur, C);
   d.plan = carve<int4>(cur, pv::kNSlot * C);
@@ -143,6 +146,9 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   d.box_disp = reinterpret_cast<float*>(sc + 9);  // one box, zero (the scalars are cleared)
   d.max_count = sc + 2;
   d.n_big = sc + 3;
+  d.n_small = sc + 12;
+  d.n_large = sc + 13;
+  d.n_huge = sc + 14;
   d.ntask = sc + 4;
   d.task_next = sc + 5;
   d.n_ccells = sc + 6;
@@ -183,6 +189,7 @@ extern "C" pv_status pv_density_static(const double* pos, const float* h, const 
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_static_setup");
   if ((e = cudaMemsetAsync(d.cell_count, 0, C * sizeof(int32_t), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(sc, 0, 16 * sizeof(int32_t), st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(d.cell_Hmax, 0, C * sizeof(float), st)) != cudaSuccess ||
       (e = cudaMemsetAsync(d.counters, 0, 16 * sizeof(unsigned long long), st)) != cudaSuccess ||
       (N && (e = cudaMemsetAsync(d.acc, 0, 3 * N * sizeof(long long), st)) != cudaSuccess))
     return fail(e, "cudaMemsetAsync");
