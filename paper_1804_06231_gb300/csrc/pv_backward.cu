@@ -132,11 +132,13 @@ __device__ __forceinline__ float fix_scale_g64(float bn, float pairs) {
 constexpr float kTaskPairs = 27.0f * 65535.0f + 1.0f;
 constexpr double kFixS64 = 68719476736.0;  // 2^36
 
-// Bn of cell a: the largest per-cell bound over a and its 26 neighbours.
-__device__ __forceinline__ float nbhd_bound(const GridDev& g, int a) {
-  float bn = 0.0f;
-  for (int o = 0; o < kNSlot; o++) bn = fmaxf(bn, g.bwd_cmax[neighbour_cell(g, a, o)]);
-  return bn;
+// Bn of cell a: the largest per-cell bound over a and its 26 neighbours, the
+// warp's lanes taking one neighbour each (the whole warp calls it).  The
+// bounds are non-negative, so their order is that of the bit patterns
+// (fmaxf with 0 also drops a NaN, as a running fmaxf would).
+__device__ __forceinline__ float nbhd_bound(const GridDev& g, int a, int lane) {
+  const float v = lane < kNSlot ? fmaxf(g.bwd_cmax[neighbour_cell(g, a, lane)], 0.0f) : 0.0f;
+  return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
 }
 
 // Half-scaled kernel factors of the adjoint, without branches.  With
@@ -799,13 +801,14 @@ __global__ void __launch_bounds__(BlkI, 896 / BlkI) k_backward_tasks(GridDev g) 
       __syncthreads();
     }
     laneb_fold(L);
+    const float bn = nbhd_bound(g, a, lane);
     if (valid && (L.Sth != 0.0f || L.Suh != 0.0f || L.gx != 0.0f || L.gy != 0.0f ||
                   L.gz != 0.0f)) {
       // 64-bit fixed point: the sum does not depend on the order of the tasks
       unsigned long long* acc = reinterpret_cast<unsigned long long*>(g.gacc);
       const size_t N = (size_t)g.n;
       const float ks = (float)kFixS64;
-      const float kg = fix_scale_g64(nbhd_bound(g, a), kTaskPairs);
+      const float kg = fix_scale_g64(bn, kTaskPairs);
       atomicAdd(&acc[L.si], (unsigned long long)__float2ll_rn(L.Sth * ks));
       atomicAdd(&acc[N + L.si], (unsigned long long)__float2ll_rn(L.Suh * ks));
       atomicAdd(&acc[2 * N + L.si], (unsigned long long)__float2ll_rn(L.gx * kg));
@@ -815,6 +818,7 @@ __global__ void __launch_bounds__(BlkI, 896 / BlkI) k_backward_tasks(GridDev g) 
   }
 }
 
+constexpr int kFinBatchB = 4;  // particles per thread in flight in the task-path finalize
 __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
                                  const float* __restrict__ g_D, float* __restrict__ g_pos,
                                  float* __restrict__ g_h) {
@@ -825,11 +829,37 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
   const size_t N = (size_t)g.n;
   const int lane = threadIdx.x & 31;
   // units as in k_backward_tasks (the float rounding of the scale is the same)
-  auto fin = [&](int s, float ig, float mscale) {
+  // The slots ca + t0 + k stride (k < kFinBatchB, below t1) of one thread:
+  // every load first, so that the batch's random accesses are in flight
+  // together, then the outputs, then the clears.
+  auto fin = [&](int ca, int t0, int stride, int t1, float ig, float mscale) {
     const double is = 1.0 / (double)(float)kFixS64;
-    write_bwd(g, s, acc[s] * is, acc[N + s] * is, acc[2 * N + s] * ig, acc[3 * N + s] * ig,
-              acc[4 * N + s] * ig, g_rho, g_D, g_pos, g_h, mscale);
-    for (int q = 0; q < 5; q++) acc[q * N + s] = 0;
+    long long v[kFinBatchB][5];
+#pragma unroll
+    for (int k = 0; k < kFinBatchB; k++) {
+      const int t = t0 + k * stride;
+      if (t < t1) {
+        const size_t s = (size_t)ca + t;
+#pragma unroll
+        for (int q = 0; q < 5; q++) v[k][q] = acc[q * N + s];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kFinBatchB; k++) {
+      const int t = t0 + k * stride;
+      if (t < t1)
+        write_bwd(g, ca + t, v[k][0] * is, v[k][1] * is, v[k][2] * ig, v[k][3] * ig,
+                  v[k][4] * ig, g_rho, g_D, g_pos, g_h, mscale);
+    }
+#pragma unroll
+    for (int k = 0; k < kFinBatchB; k++) {
+      const int t = t0 + k * stride;
+      if (t < t1) {
+        const size_t s = (size_t)ca + t;
+#pragma unroll
+        for (int q = 0; q < 5; q++) acc[q * N + s] = 0;
+      }
+    }
   };
   // as the forward finalize: one warp per self-slot task (blocks of g.task_blk
   // cell-local indices), or one block per task cell when the self slot is
@@ -842,8 +872,9 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
       if (tk.o != kSelfSlot) continue;
       const int ca = g.cell_start[tk.a];
       const float mscale = munit * g.m_max[g.cell_box[tk.a]];
-      const float ig = 1.0f / fix_scale_g64(nbhd_bound(g, tk.a), kTaskPairs);
-      for (int t = tk.p0 + lane; t < tk.p1; t += 32) fin(ca + t, ig, mscale);
+      const float ig = 1.0f / fix_scale_g64(nbhd_bound(g, tk.a, lane), kTaskPairs);
+      for (int t0 = tk.p0 + lane; t0 < tk.p1; t0 += 32 * kFinBatchB)
+        fin(ca, t0, 32, tk.p1, ig, mscale);
     }
   } else {
     const int nt = *g.n_tcells;
@@ -851,8 +882,9 @@ __global__ void k_bwd_finalize_t(GridDev g, const float* __restrict__ g_rho,
       const int a = g.tcells[c];
       const int ca = g.cell_start[a], na = g.cell_count[a];
       const float mscale = munit * g.m_max[g.cell_box[a]];
-      const float ig = 1.0f / fix_scale_g64(nbhd_bound(g, a), kTaskPairs);
-      for (int t = threadIdx.x; t < na; t += blockDim.x) fin(ca + t, ig, mscale);
+      const float ig = 1.0f / fix_scale_g64(nbhd_bound(g, a, lane), kTaskPairs);
+      for (int t0 = threadIdx.x; t0 < na; t0 += blockDim.x * kFinBatchB)
+        fin(ca, t0, blockDim.x, na, ig, mscale);
     }
   }
 }

@@ -903,6 +903,7 @@ __global__ void __launch_bounds__(BlkI, 1024 / BlkI) k_density_tasks(GridDev g) 
 // so one warp per self-slot task finalises cell-local indices [p0, p1): big
 // cells are spread over many warps.  (A pass whose slot mask leaves out the
 // self slot has no such tasks: one block per task cell then.)
+constexpr int kFinBatch = 4;  // particles per thread in flight in the task-path finalize
 __global__ void k_finalize_t(GridDev g, float* __restrict__ rho, float* __restrict__ drho_dh,
                              int32_t* __restrict__ n_ngb) {
   pdl_enter();
@@ -911,13 +912,39 @@ __global__ void k_finalize_t(GridDev g, float* __restrict__ rho, float* __restri
   const float munit = (float)(16.0 / 3.14159265358979323846 * kFixInv);
   unsigned long long inter = 0;
   const size_t N = (size_t)g.n;
-  auto fin = [&](int s, float mscale) {
-    const long long an = g.acc[2 * N + s];
-    write_out(g, s, g.acc[s], g.acc[N + s], (int)an, rho, drho_dh, n_ngb, mscale);
-    inter += (unsigned long long)(an - 1);
-    g.acc[s] = 0;
-    g.acc[N + s] = 0;
-    g.acc[2 * N + s] = 0;
+  // The slots ca + t0 + k stride (k < kFinBatch, below t1) of one thread: every
+  // load first, so that the batch's random accesses are in flight together,
+  // then the outputs, then the clears.
+  auto fin = [&](int ca, int t0, int stride, int t1, float mscale) {
+    long long ar[kFinBatch], ad[kFinBatch], an[kFinBatch];
+#pragma unroll
+    for (int k = 0; k < kFinBatch; k++) {
+      const int t = t0 + k * stride;
+      if (t < t1) {
+        const size_t s = (size_t)ca + t;
+        ar[k] = g.acc[s];
+        ad[k] = g.acc[N + s];
+        an[k] = g.acc[2 * N + s];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kFinBatch; k++) {
+      const int t = t0 + k * stride;
+      if (t < t1) {
+        write_out(g, ca + t, ar[k], ad[k], (int)an[k], rho, drho_dh, n_ngb, mscale);
+        inter += (unsigned long long)(an[k] - 1);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kFinBatch; k++) {
+      const int t = t0 + k * stride;
+      if (t < t1) {
+        const size_t s = (size_t)ca + t;
+        g.acc[s] = 0;
+        g.acc[N + s] = 0;
+        g.acc[2 * N + s] = 0;
+      }
+    }
   };
   if ((g.slot_mask >> kSelfSlot) & 1u) {
     const int ntask = *g.ntask;
@@ -927,7 +954,7 @@ __global__ void k_finalize_t(GridDev g, float* __restrict__ rho, float* __restri
       if (tk.o != kSelfSlot) continue;
       const int ca = g.cell_start[tk.a];
       const float mscale = munit * g.m_max[g.cell_box[tk.a]];
-      for (int t = tk.p0 + lane; t < tk.p1; t += 32) fin(ca + t, mscale);
+      for (int t0 = tk.p0 + lane; t0 < tk.p1; t0 += 32 * kFinBatch) fin(ca, t0, 32, tk.p1, mscale);
     }
   } else {
     const int nt = *g.n_tcells;
@@ -935,7 +962,8 @@ __global__ void k_finalize_t(GridDev g, float* __restrict__ rho, float* __restri
       const int a = g.tcells[c];
       const int ca = g.cell_start[a], na = g.cell_count[a];
       const float mscale = munit * g.m_max[g.cell_box[a]];
-      for (int t = threadIdx.x; t < na; t += blockDim.x) fin(ca + t, mscale);
+      for (int t0 = threadIdx.x; t0 < na; t0 += blockDim.x * kFinBatch)
+        fin(ca, t0, blockDim.x, na, mscale);
     }
   }
   for (int s = 16; s > 0; s >>= 1) inter += __shfl_xor_sync(0xffffffffu, inter, s);
