@@ -53,6 +53,29 @@ def test_large_cells_vs_oracle(oracle_lib):
     check_density(rho, D, n, ref)
 
 
+def test_every_sort_path_vs_oracle(oracle_lib):
+    """One cell of each size class of pv_sort_cells on a 3^3 grid: 26,000
+    particles (above what the largest sort instance stages in shared memory,
+    so its global-memory path), 8,000 (the staged largest instance), 3,000,
+    1,000, 200, 40 and 10 particles, empty cells, and 100 in each of the
+    rest.  A wrong order along any axis would drop pairs from the windows."""
+    rng = np.random.default_rng(23)
+    counts = [26000, 8000, 3000, 1000, 200, 40, 10, 0, 0] + [100] * 18
+    cells = np.stack(np.meshgrid(np.arange(3), np.arange(3), np.arange(3),
+                                 indexing="ij"), -1).reshape(-1, 3)
+    pos = np.concatenate([(cells[c] + rng.random((k, 3))) / 3.0
+                          for c, k in enumerate(counts) if k])
+    pos = np.ascontiguousarray(pos[rng.permutation(len(pos))])
+    n = len(pos)
+    h = np.full(n, 0.012, dtype=np.float32) * rng.uniform(0.9, 1.1, n).astype(np.float32)
+    m = np.full(n, 1.0 / n, dtype=np.float32)
+    box = I.Box(pos, h, m, 1.0, 3, "sort-classes")
+    rho, D, n_ngb, st, _ = run_density(box)
+    assert st.max_cell_count == 26000
+    ref = oracle_lib.density_pv(box.pos, box.h, box.m, 1.0, 3)
+    check_density(rho, D, n_ngb, ref)
+
+
 def test_masses_vary(oracle_lib):
     box = I.uniform(20000, 9)
     rng = np.random.default_rng(1)
