@@ -304,7 +304,7 @@ pv_status pv_grid_sweep_times(pv_grid* g, double* ms, int64_t* launches);
    NULL, is a device uint32 that receives the PV_FLAG_* bits the kernels
    latched (0 = inputs valid; outputs are not written otherwise).
    Memory: every intermediate array lives in one fixed device array inside
-   this library (about 14 MB, sized for the limits below) that each GPU
+   this library (about 15 MB, sized for the limits below) that each GPU
    loading the library keeps until the process exits; nothing is allocated
    or freed, by this library or by any library it calls.
    Limits: n <= PV_STATIC_MAX_PARTICLES and nc^3 <= PV_STATIC_MAX_CELLS;
