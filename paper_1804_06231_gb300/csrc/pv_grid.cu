@@ -14,9 +14,9 @@
 //   k_scan_tile, k_scan_add  exclusive scan of the occupancies (two passes
 //              over tiles of cells), the cell lists of the sort paths
 //   k_scatter  caller index of every cell-order slot
-//   k_gather   one thread per slot of the cells outside k_cell_sort: the
-//              particle's FP32 offset from its cell centre + normalised mass,
-//              h, the wrapped FP64 position, and the cell's H_max
+//   k_gather   one thread per cell-order slot: the particle's FP32 offset
+//              from its cell centre + normalised mass, h, the wrapped FP64
+//              position, and the cell's H_max
 //   k_cell_sort_tiny  cells of <= 64 particles, one warp per cell: rank
 //              counting over (axis, particle) pairs for <= 32, else the 13
 //              axes in turn with a warp bucket (counting) sort, exact order
@@ -24,7 +24,7 @@
 //   k_cell_sort   cells of 65..384 particles, one CTA per cell, one warp per
 //              axis, the same warp bucket sort
 //   k_sort_big    one CTA per (larger cell, axis), the same algorithm with
-//              up to 16384 buckets in shared memory
+//              up to 16384 buckets in shared memory (three instances by size)
 //   k_update, k_update_check  new positions on a kept sort (pv_update_positions)
 #include <cuda_runtime.h>
 
@@ -163,6 +163,7 @@ __device__ __forceinline__ float4 gather_slot(const GridDev& g, int s, int p, co
   return xm;
 }
 
+// The centre of cell c of box B, negated, in units of the edge.
 __device__ __forceinline__ void cell_centre(const BoxDev& B, int c, double (&ctr)[3]) {
   const int loc = c - B.cell_base;
   ctr[0] = -((loc / (B.nc * B.nc)) + 0.5);
