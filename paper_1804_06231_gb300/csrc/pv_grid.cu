@@ -632,8 +632,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_cell_sort(GridDev g) {
 }
 
 // One warp per cell of at most kSortTinyMax particles, over all cells.
-constexpr int kSortTinyWarps = 8;
-__global__ void __launch_bounds__(kSortTinyWarps * 32, 5) k_cell_sort_tiny(GridDev g) {
+constexpr int kSortTinyWarps = 4;  // (small CTAs: one retires when its four cells are done)
+__global__ void __launch_bounds__(kSortTinyWarps * 32, 10) k_cell_sort_tiny(GridDev g) {
   pdl_enter();
   __shared__ TinyBuf s_tb[kSortTinyWarps];
   const int warp = threadIdx.x >> 5;
