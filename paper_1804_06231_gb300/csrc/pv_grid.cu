@@ -686,12 +686,31 @@ __global__ void __launch_bounds__(kThreads, kList == kListMid ? 6 : (kList == kL
   uint16_t* s_out = s_grp + kStage;                                   // [kStage] (kFull)
   __shared__ float s_red[2][kWarps];
   __shared__ int s_scan[32];
+  // huge instance: a list of at most kOrderMax cells is taken largest first,
+  // so that the items of the last round are the shortest
+  constexpr int kOrderMax = 256;
+  __shared__ int s_order[kList == kListHuge ? kOrderMax : 1];
   if (*g.flags) return;
   const int nlist = kList == kListMid ? *g.n_big : (kList == kListLarge ? *g.n_large : *g.n_huge);
   const int nitem = nlist * kNDir;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool ordered = kList == kListHuge && nlist <= kOrderMax;  // (the same in every thread)
+  if (ordered) {
+    auto count_of = [&](int e) { return g.cell_count[g.small_cells[g.ncell - 1 - e]]; };
+    for (int e = tid; e < nlist; e += kThreads) {
+      const int ne = count_of(e);
+      int r = 0;  // entries before e: larger, or as large and earlier in the list
+      for (int f = 0; f < nlist; f++) {
+        const int nf = count_of(f);
+        r += (nf > ne || (nf == ne && f < e)) ? 1 : 0;
+      }
+      s_order[r] = e;
+    }
+    __syncthreads();
+  }
   for (int idx = blockIdx.x; idx < nitem; idx += gridDim.x) {
-    const int e = idx / kNDir, k = idx - e * kNDir;
+    const int e0 = idx / kNDir, k = idx - e0 * kNDir;
+    const int e = ordered ? s_order[e0] : e0;
     const int c = kList == kListMid     ? g.big_cells[e]
                   : kList == kListLarge ? g.big_cells[g.ncell - 1 - e]
                                         : g.small_cells[g.ncell - 1 - e];
